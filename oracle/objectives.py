@@ -1,0 +1,99 @@
+"""Objective families in FP64 (oracle side): value, analytic gradient, Hessian.
+
+* Gaussian mixture log-density (Appendix D "Gaussian mixture", generalised to
+  per-component weights and diagonal or full covariances):
+      f(x) = log sum_k w_k N(x; mu_k, Sigma_k)
+  computed as a log-sum-exp over the component log-densities.
+* Rotated quadratic f(x) = -(x-c)^T Q^T Lambda Q (x-c) (a log-concave target
+  with the single mode c, the setting of Proposition 1).
+
+The optional additive noise of Section 5.6 (f~ = f + eps, eps ~ N(0, s^2)) is
+applied by ``method.evaluate``, which knows the evaluation's stream position.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+OBJ_MIXTURE_DIAG = 1
+OBJ_MIXTURE_FULL = 2
+OBJ_QUADRATIC = 3
+
+LOG2PI = np.log(2.0 * np.pi)
+
+
+def _component_logdens(obj, X):
+    """log w_k + log N(x; mu_k, Sigma_k) for all samples and components -> (N, K),
+    plus the per-component score a_k(x) = grad_x log N_k(x) -> (N, K, d)."""
+    A = obj.arrays
+    w, mu = A["weights"], A["means"]
+    K, d = mu.shape
+    R = X[:, None, :] - mu[None, :, :]                     # (N, K, d)
+    if obj.kind == OBJ_MIXTURE_DIAG:
+        sig = A["sigmas"]
+        Z = R / sig[None]
+        logdet = np.log(sig).sum(axis=1)                   # log |Sigma_k|^(1/2)
+        score = -R / (sig[None] ** 2)
+    else:
+        L = A["chol"]
+        Z = np.empty_like(R)
+        score = np.empty_like(R)
+        for k in range(K):
+            zk = solve_triangular(L[k], R[:, k, :].T, lower=True)          # L^-1 (x - mu)
+            Z[:, k, :] = zk.T
+            score[:, k, :] = -solve_triangular(L[k], zk, lower=True, trans="T").T   # -Sigma^-1 (x-mu)
+        logdet = np.log(np.abs(np.einsum("kii->ki", L))).sum(axis=1)
+    lc = np.log(w)[None, :] - 0.5 * np.einsum("nkd,nkd->nk", Z, Z) - logdet[None, :] - 0.5 * d * LOG2PI
+    return lc, score
+
+
+def _lse(lc):
+    m = lc.max(axis=1, keepdims=True)
+    return (m + np.log(np.exp(lc - m).sum(axis=1, keepdims=True)))[:, 0]
+
+
+def value(obj, X):
+    X = np.asarray(X, dtype=np.float64)
+    if obj.kind == OBJ_QUADRATIC:
+        A = obj.arrays
+        Z = (X - A["center"][None, :]) @ A["Q"].T
+        return -(Z * Z * A["lam"][None, :]).sum(axis=1)
+    lc, _ = _component_logdens(obj, X)
+    return _lse(lc)
+
+
+def grad(obj, X):
+    """Analytic gradient of f (the exact gradient the adjoint path computes)."""
+    X = np.asarray(X, dtype=np.float64)
+    if obj.kind == OBJ_QUADRATIC:
+        A = obj.arrays
+        Q, lam = A["Q"], A["lam"]
+        Z = (X - A["center"][None, :]) @ Q.T
+        return -2.0 * (Z * lam[None, :]) @ Q
+    lc, score = _component_logdens(obj, X)
+    r = np.exp(lc - _lse(lc)[:, None])                      # responsibilities
+    return np.einsum("nk,nkd->nd", r, score)
+
+
+def hessian(obj, x):
+    """Hessian of f at one point x (d,), for the Newton mode finder."""
+    x = np.asarray(x, dtype=np.float64)[None, :]
+    if obj.kind == OBJ_QUADRATIC:
+        A = obj.arrays
+        Q, lam = A["Q"], A["lam"]
+        return -2.0 * Q.T @ np.diag(lam) @ Q
+    lc, score = _component_logdens(obj, x)
+    r = np.exp(lc - _lse(lc)[:, None])[0]
+    a = score[0]                                            # (K, d)
+    A = obj.arrays
+    K, d = A["means"].shape
+    H = np.zeros((d, d))
+    for k in range(K):
+        if obj.kind == OBJ_MIXTURE_DIAG:
+            prec = np.diag(1.0 / A["sigmas"][k] ** 2)
+        else:
+            Linv = np.linalg.inv(A["chol"][k])
+            prec = Linv.T @ Linv
+        H += r[k] * (-prec + np.outer(a[k], a[k]))
+    gbar = r @ a
+    return H - np.outer(gbar, gbar)

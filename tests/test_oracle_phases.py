@@ -1,0 +1,246 @@
+"""Pins for the oracle's Phases 2-6 (freeze, dedup, reseed, HLC, anti-convergence)."""
+import numpy as np
+import pytest
+
+from oracle import method as M
+from oracle import philox as PX
+from paper_2606_26164_gb300 import inputs as I
+
+
+# --------------------------------------------------------------------- Phase 2 (Eq. 3)
+
+def test_freeze_hand_case():
+    f = np.array([0.0, -1.0, -2.5, -2.0, 0.0])
+    g = np.array([[1e-7, 0.0], [0.0, -5e-7], [1e-8, 0.0], [2e-6, 0.0], [1e-6, 0.0]])
+    stuck, fmax = M.freeze(f, g, 1e-6, 0.1)
+    # thr = 0 + log 0.1 = -2.3026: sample 2 fails the quality gate, 3 and 4 the gradient gate
+    assert fmax == 0.0
+    assert list(stuck) == [True, True, False, False, False]
+
+
+def test_freeze_binary32_threshold_rounding():
+    """The FP32 decision uses thr = fl32(fl32(f_max) + fl32(log delta)); a value
+    equal to that rounded threshold sticks, its predecessor does not."""
+    f32 = np.array([10.0, 0.0, 0.0], dtype=np.float32)
+    thr = np.float32(np.float32(10.0) + np.float32(np.log(0.1)))
+    f32[1] = thr
+    f32[2] = np.nextafter(thr, np.float32(-np.inf))
+    g32 = np.zeros((3, 2), np.float32)
+    stuck, _ = M.freeze(f32, g32, 1e-6, 0.1, dtype=np.float32)
+    assert list(stuck) == [True, True, False]
+
+
+def test_freeze_excludes_nonfinite_from_fmax():
+    f = np.array([np.nan, -1.0, -1.5])
+    stuck, fmax = M.freeze(f, np.zeros((3, 1)), 1.0, 0.1)
+    assert fmax == -1.0 and list(stuck) == [False, True, True]
+
+
+# --------------------------------------------------------------------- Phase 3 (Eq. 4)
+
+def test_dedup_chain_literal_reading():
+    """A ~ B and B ~ C but A !~ C, f_A > f_B > f_C: B is removed by A and C by B
+    (B counts although it is itself removed)."""
+    x = np.array([[0.0], [0.0008], [0.0016], [5.0]])
+    f = np.array([3.0, 2.0, 1.0, 0.0])
+    stuck = np.array([True, True, True, False])
+    rem = M.dedup(x, f, stuck, 1e-3)
+    assert list(rem) == [False, True, True, False]
+
+
+def test_dedup_ties_keep_lower_index_and_ignore_unstuck():
+    x = np.array([[1.0, 1.0], [1.0, 1.0005], [1.0, 1.0], [1.0, 1.0]])
+    f = np.array([2.0, 2.0, 5.0, 2.0])
+    stuck = np.array([True, True, False, True])
+    rem = M.dedup(x, f, stuck, 1e-3)
+    assert list(rem) == [False, True, False, True]
+
+
+def test_dedup_strict_distance():
+    x = np.array([[0.0], [0.5]])                        # |dx| = eps exactly: not a duplicate
+    rem = M.dedup(x, np.array([1.0, 0.0]), np.array([True, True]), 0.5)
+    assert not rem.any()
+
+
+def test_dedup_invariants_random():
+    rng = np.random.default_rng(3)
+    x = np.round(rng.uniform(0, 0.02, size=(300, 2)), 4)
+    f = np.round(rng.uniform(0, 1, size=300), 2)
+    stuck = rng.random(300) < 0.8
+    rem = M.dedup(x, f, stuck, 1e-3)
+    surv = np.flatnonzero(stuck & ~rem)
+    # survivors are pairwise at L-inf distance >= eps
+    D = np.abs(x[surv][:, None] - x[surv][None]).max(axis=2)
+    assert (D[~np.eye(surv.size, dtype=bool)] >= 1e-3).all()
+    # every removed sample has a higher-ranked stuck neighbour within eps
+    st_idx = np.flatnonzero(stuck)
+    for j in np.flatnonzero(rem):
+        d = np.abs(x[st_idx] - x[j]).max(axis=1)
+        above = (f[st_idx] > f[j]) | ((f[st_idx] == f[j]) & (st_idx < j))
+        assert ((d < 1e-3) & above).any()
+    assert not rem[~stuck].any()
+
+
+# --------------------------------------------------------------------- Phase 4 (Sec. 3.2.4)
+
+@pytest.mark.parametrize("d", [2, 5, 16, 64])
+def test_householder_qr_matches_library(d):
+    G = np.random.default_rng(d).standard_normal((d, d))
+    Q, R = M.householder_qr(G)
+    q, r = np.linalg.qr(G)
+    sgn = np.sign(np.diag(r))
+    np.testing.assert_allclose(Q, q * sgn[None, :], atol=1e-12)
+    np.testing.assert_allclose(Q @ R, G, atol=1e-12)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(d), atol=1e-12)
+    assert (np.diag(R) > 0).all() and np.allclose(np.tril(R, -1), 0.0, atol=1e-12)
+
+
+def test_ray_exit_hand_cases():
+    lo, hi = np.array([-1.0, -1.0]), np.array([1.0, 1.0])
+    p = np.array([[0.0, 0.0], [0.5, 0.0], [1.0, 0.0]])
+    u = np.array([[1.0, 0.0], [np.sqrt(0.5), -np.sqrt(0.5)], [1.0, 0.0]])
+    np.testing.assert_allclose(M.ray_exit(p, u, lo, hi), [1.0, 0.5 / np.sqrt(0.5), 0.0])
+
+
+def _reseed_setup(n_unfrozen, d=3, N=40):
+    p = I.small_mixture(d, 3, N, seed=9)
+    st = M.new_state(p.x0, 4)
+    st.f = -np.arange(N, dtype=np.float64)
+    st.stuck[:] = True
+    st.stuck[N - n_unfrozen:] = False
+    st.removed[:] = False
+    st.removed[1:10] = True                             # 9 free slots, removed from the stuck set
+    st.stuck &= ~st.removed
+    st.hlen[:] = 3
+    return p, st
+
+
+def test_repulse_monkey_children_on_parent_rays():
+    p, st = _reseed_setup(n_unfrozen=12)
+    x_before = st.x.copy()
+    P = M.Params(seed=11)
+    M.reseed(p, st, P, cycle=2)
+    assert st.last_reseed == M.RESEED_RM
+    free = np.arange(1, 10)
+    unfrozen = np.flatnonzero(~st.stuck)
+    unfrozen = unfrozen[~np.isin(unfrozen, free)]
+    w = PX.words(11, np.arange(9), 0, PX.TAG_RM, 2, 0, 0, 0)
+    pick = ((w[:, 0].astype(np.uint64) * np.uint64(unfrozen.size)) >> np.uint64(32)).astype(int)
+    parents = x_before[unfrozen[pick]]
+    z = PX.normal_rows(11, np.arange(9), 3, PX.TAG_RM_DIR, 2, 0, 0, 0)
+    u = z / np.linalg.norm(z, axis=1, keepdims=True)
+    delta = st.x[free] - parents
+    t = np.einsum("nd,nd->n", delta, u)
+    np.testing.assert_allclose(delta, t[:, None] * u, atol=1e-12)            # on the ray
+    assert (t >= 0).all() and (t <= M.ray_exit(parents, u, p.lo, p.hi) + 1e-12).all()
+    assert (st.x >= p.lo).all() and (st.x <= p.hi).all()
+    assert not st.stuck[free].any() and (st.hlen[free] == 0).all()
+
+
+def test_golden_rooster_orthonormal_rays_round_robin():
+    p, st = _reseed_setup(n_unfrozen=2, d=4)
+    x_before = st.x.copy()
+    P = M.Params(seed=5)
+    M.reseed(p, st, P, cycle=1)
+    assert st.last_reseed == M.RESEED_GR
+    surv = np.flatnonzero(st.stuck)
+    ranked = surv[np.lexsort((surv, -st.f[surv]))]
+    Gm = PX.normal_rows(5, np.arange(4), 4, PX.TAG_GR_MAT, 1, 0, 0, 0)
+    Q, _ = M.householder_qr(Gm)
+    S = ranked.size
+    for r, slot in enumerate(range(1, 10)):
+        peak = x_before[ranked[r % S]]
+        u = Q[:, (r // S) % 4] * (1.0 if (r // (S * 4)) % 2 == 0 else -1.0)
+        delta = st.x[slot] - peak
+        t = delta @ u
+        np.testing.assert_allclose(delta, t * u, atol=1e-12)
+        assert t >= -1e-15
+
+
+def test_golden_rooster_disables_after_patience():
+    P = M.Params(seed=1, gr_patience=2)
+    modes = []
+    st = None
+    for gen in range(4):
+        p, st2 = _reseed_setup(n_unfrozen=2, d=2)
+        if st is not None:
+            st2.gr_enabled, st2.gr_noprog, st2.gr_prev_surv = st.gr_enabled, st.gr_noprog, st.gr_prev_surv
+        M.reseed(p, st2, P, cycle=gen + 1)
+        modes.append(st2.last_reseed)
+        st = st2
+    # same survivor count every generation: GR, GR (1 no-progress), then disabled -> uniform
+    assert modes == [M.RESEED_GR, M.RESEED_GR, M.RESEED_UNIFORM, M.RESEED_UNIFORM]
+    assert not st.gr_enabled
+
+
+def test_uniform_redraw_inside_box():
+    p, st = _reseed_setup(n_unfrozen=2, d=3)
+    st.gr_enabled = False
+    M.reseed(p, st, M.Params(seed=2), cycle=1)
+    assert st.last_reseed == M.RESEED_UNIFORM
+    u = PX.uniform_rows(2, np.arange(9), 3, PX.TAG_UNIFORM, 1, 0, 0, 0)
+    np.testing.assert_allclose(st.x[1:10], p.lo + u * (p.hi - p.lo), atol=1e-12)
+
+
+# --------------------------------------------------------------------- Phases 5-6
+
+def _quad_state(N=64, d=3, seed=3):
+    p = I.small_quadratic(d, N, seed=seed, cond=4.0)
+    p.lo, p.hi = np.full(d, -100.0), np.full(d, 100.0)
+    st = M.new_state(p.x0, 4)
+    return p, st
+
+
+def test_population_scales_hand_case():
+    obj = I.Objective(3, 2, {"center": np.zeros(2), "Q": np.eye(2), "lam": np.array([1.0, 1.0])})
+    p = I.Problem(2, 3, np.full(2, -9.0), np.full(2, 9.0), obj, np.zeros((3, 2), np.float32), 1e-6, 1.0)
+    st = M.new_state(np.array([[1.0, 0.0], [3.0, 2.0], [8.0, 8.0]]), 2)
+    unf = np.array([True, True, False])
+    P = M.Params(grad_mode=M.GRAD_ADJOINT)
+    idx, G, sigma, alpha, s, g_rms = M.population_scales(p, st, P, unf)
+    # var_x = 1, var_y = 1 -> s = 1; grad = -2x: (-2,0), (-6,-4) -> g_rms = sqrt(56/4)
+    assert s == pytest.approx(1.0) and sigma == pytest.approx(0.1)
+    assert g_rms == pytest.approx(np.sqrt(14.0))
+    assert alpha == pytest.approx(0.1 / np.sqrt(14.0))
+
+
+def test_hlc_step_algebra_and_unbiasedness():
+    """Appendix B: for a quadratic, grad f(theta + sigma z) = grad f(theta) + sigma H z,
+    so one HLC step is x + alpha (grad f(x) + sigma H zbar) with zbar the mean of
+    the M perturbations, and sqrt(M) zbar ~ N(0, I) (chi-square check)."""
+    p, st = _quad_state(N=400, d=3)
+    P = M.Params(n_cloud=1, M=8, grad_mode=M.GRAD_ADJOINT, seed=4)
+    x0 = st.x.copy()
+    sigma, alpha = M.hlc(p, st, P, cycle=1)
+    H = -2.0 * p.objective.arrays["Q"].T @ np.diag(p.objective.arrays["lam"]) @ p.objective.arrays["Q"]
+    g0 = -2.0 * (x0 - p.objective.arrays["center"]) @ (p.objective.arrays["Q"].T @ np.diag(p.objective.arrays["lam"]) @ p.objective.arrays["Q"])
+    zbar = np.mean([PX.normal_rows(4, np.arange(400), 3, PX.TAG_HLC, 1, 0, 0, k) for k in range(8)], axis=0)
+    np.testing.assert_allclose(st.x, x0 + alpha * (g0 + sigma * zbar @ H.T), rtol=1e-10, atol=1e-10)
+    chi2 = float((8.0 * zbar * zbar).sum())
+    dof = zbar.size
+    assert abs(chi2 - dof) < 5 * np.sqrt(2 * dof)
+
+
+def test_anti_convergence_momentum_algebra():
+    """Eq. 6 with a linear f (constant gradient g): v1 = -a g, v2 = -a g (1 + mu)."""
+    obj = I.Objective(3, 1, {"center": np.array([0.0]), "Q": np.eye(1), "lam": np.array([1e-12])})
+    p = I.Problem(1, 6, np.array([-1e6]), np.array([1e6]), obj, np.zeros((6, 1), np.float32), 1e-6, 1.0)
+    # f = -1e-12 x^2 is locally linear: use the analytic gradient and a fixed alpha
+    st = M.new_state(np.linspace(1000.0, 1005.0, 6)[:, None], 2)
+    P = M.Params(n_anti=2, mu=0.9, alpha=3.0, grad_mode=M.GRAD_ADJOINT)
+    x0 = st.x.copy()
+    g = -2e-12 * x0
+    M.anti_converge(p, st, P)
+    g1 = -2e-12 * (x0 - 3.0 * g)
+    np.testing.assert_allclose(st.x, x0 - 3.0 * g + (0.9 * (-3.0 * g) - 3.0 * g1), rtol=1e-14)
+
+
+def test_anti_convergence_zeroes_velocity_on_clamped_coordinates():
+    obj = I.Objective(3, 2, {"center": np.array([0.0, 0.0]), "Q": np.eye(2), "lam": np.array([1.0, 1.0])})
+    p = I.Problem(2, 1, np.array([-1.0, -1.0]), np.array([1.0, 1.0]), obj, np.zeros((1, 2), np.float32), 1e-6, 1.0)
+    st = M.new_state(np.array([[0.9, 0.1]]), 2)
+    P = M.Params(n_anti=2, mu=0.5, alpha=1.0, grad_mode=M.GRAD_ADJOINT)
+    M.anti_converge(p, st, P)
+    # step 1: g = (-1.8, -0.2), v = (1.8, 0.2), x = (2.7 -> 1.0 clamped, 0.3), v_x := 0
+    # step 2: g = (-2, -0.6), v = (0 + 2, 0.1 + 0.6), x = (1.0 clamped, 1.0)
+    np.testing.assert_allclose(st.x, [[1.0, 1.0]], atol=1e-12)
