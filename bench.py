@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the ChiSao population step (one oscillation cycle = one step).
+
+Default workload: the d=64 rotated ill-conditioned quadratic (Lambda from 1 to
+1e4, c uniform in [-5, 5]^64) over N=65536 samples, FP32 state, m=10,
+n_conv = max(10, 3 log2 d) = 18, exact (adjoint) gradients; every timed step
+is a non-final cycle (Phases 1-6).  The same workload with central FD
+gradients (FP64 stencil at h=1e-5) is timed beside it.
+
+Prints one JSON line.  Under torchrun every rank runs an independent replica
+population (its own seed): the work per GPU is fixed (weak scaling) and the
+reported value is the sum over ranks of samples x cycles divided by the
+slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS_PER_STEP = 18   # kernel launches in one non-final cycle of one problem
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="quadratic_d64")
+    ap.add_argument("--grad", default="adjoint", choices=["adjoint", "fd64", "fd32"])
+    ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
+    ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+GRAD = {"fd64": 0, "fd32": 1, "adjoint": 2}
+
+
+def make_problem(name, seed):
+    from paper_2606_26164_gb300 import inputs as I
+    return I.WORKLOADS[name](seed=seed)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in ("obj_kernels.cuh", "objectives.cuh", "dev_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_26164_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` recorded in profiles/*.md, if the
+    recorded source hash matches the current kernel source."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    cur = kernel_source_hash()
+    for f in sorted(os.listdir(pdir)):
+        if not f.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, f)).read()
+        m = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.eE+]+)\s+source_hash:\s*(\w+)" % kernel, txt)
+        if m and m.group(2) == cur:
+            return float(m.group(1))
+    return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def allmax(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+
+def cpu_leg(spec):
+    """Time the FP64 oracle on a bounded sample of the workload (run in a child
+    process with single-threaded BLAS so `cores` is exact)."""
+    a = json.loads(spec)
+    from oracle import method as M
+    prob = make_problem(a["workload"], a["seed"])
+    from paper_2606_26164_gb300 import inputs as I
+    rows = np.arange(a["sample_n"])
+    sub = I.Problem(prob.d, rows.size, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad,
+                    prob.sigma_mode)
+    P = M.Params(n_osc=10 ** 6, m=10, eps_grad=prob.eps_grad, grad_mode=GRAD[a["grad"]], seed=a["seed"])
+    st = M.new_state(sub.x0, P.m)
+    t0 = time.perf_counter()
+    cycles = 0
+    times = []
+    while True:
+        c0 = time.perf_counter()
+        M.cycle(sub, st, P, last=False)
+        times.append(time.perf_counter() - c0)
+        cycles += 1
+        if time.perf_counter() - t0 >= a["budget_s"] or cycles >= a.get("max_cycles", 10 ** 6):
+            break
+    el = time.perf_counter() - t0
+    return {"value": rows.size * cycles / el, "cycles": cycles, "seconds": el, "evals": st.evals,
+            "evals_per_s": st.evals / el, "step_times": times}
+
+
+def run_cpu_leg(workload, grad, seed, sample_n, budget_s, max_cycles=10 ** 6):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    spec = json.dumps({"workload": workload, "grad": grad, "seed": seed, "sample_n": sample_n,
+                       "budget_s": budget_s, "max_cycles": max_cycles})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", spec], env=env,
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------------------- GPU legs
+
+def gpu_timed(model, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        model.step()
+    model.synchronize()
+    c0 = model.counters(0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(model._stream)
+    for _ in range(steps):
+        model.step()
+    e1.record(model._stream)
+    e1.synchronize()
+    c1 = model.counters(0)
+    return e0.elapsed_time(e1) / 1e3, c0, c1
+
+
+def main():
+    args = parse()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args.cpu_leg)))
+        return
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2606_26164_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(world)
+    from paper_2606_26164_gb300 import chisao as CH
+
+    prob = make_problem(args.workload, seed=rank)
+    N, d = prob.n, prob.d
+    gm = GRAD[args.grad]
+    n_osc = 10 ** 6                      # every timed cycle is a non-final cycle
+    params = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=gm, seed=rank)
+    model = CH.Chisao([prob], params)
+    n_conv = max(10, int(np.ceil(3 * np.log2(d))))
+
+    barrier(world)
+    clk = Clocks(local)
+    clk.start()
+    t, c0, c1 = gpu_timed(model, args.steps, args.warmup)
+    clocks = clk.stop()
+    t_max = allmax(t, world)
+    value = N * args.steps * world / t_max
+    evals = (c1["evals"] - c0["evals"]) * world / t_max
+    grads = (c1["grads"] - c0["grads"]) * world / t_max
+
+    out = {"metric": f"sample-cycles/s ({args.grad} gradients) at N={N}, d={d}", "value": value,
+           "unit": "sample-cycles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "N": N, "d": d, "m": 10, "n_conv": n_conv,
+                      "objective": "rotated quadratic, Lambda 1..1e4" if args.workload == "quadratic_d64" else args.workload,
+                      "grad": args.grad, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2: per-step state (x, g, m=10 history) "
+                            f"{(2 * N * d * 4 + 2 * N * 10 * d * 4 + N * 80) / 1e6:.0f} MB > 129 MB"},
+           "evals_per_s": evals, "grads_per_s": grads, "gpu_launches": KERNELS_PER_STEP * args.steps,
+           "clocks": clocks}
+
+    if not args.no_extras and rank == 0:
+        # --- dominant kernel: Phase 1 (fused L-BFGS) alone, CUDA events on the context stream
+        reps = 5
+        k0 = model.counters(0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        model.load_population(0, prob.x0)
+        e0.record(model._stream)
+        for _ in range(reps):
+            model.run_phase(0, CH.PHASE_LBFGS, n_conv)
+        e1.record(model._stream)
+        e1.synchronize()
+        k1 = model.counters(0)
+        t_k = e0.elapsed_time(e1) / 1e3 / reps
+        ev_k = (k1["evals"] - k0["evals"]) / reps
+        # FLOPs per objective evaluation of the quadratic (value and gradient from one
+        # d x d matrix-vector product): 2 d^2 + 4 d; per L-BFGS iteration the two-loop
+        # and the update take 8 m d + 8 d.
+        flop = ev_k * (2 * d * d + 4 * d) + N * n_conv * (8 * 10 * d + 8 * d)
+        mhz = clocks.get("sm_mhz") or 1900.0
+        peak_tf = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        achieved_tf = flop / t_k / 1e12
+        out["roofline"] = {"kernel": "k_phase1", "bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                           "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                           "traffic": profiled_traffic("k_phase1"),
+                           "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz (sampled)",
+                           "launch_ms": 1e3 * t_k, "evals_per_launch": ev_k}
+        # --- FD leg: the plain form (central differences, FP64 stencil, h = 1e-5)
+        fd = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=CH.GRAD_FD64, seed=rank)
+        mfd = CH.Chisao([prob], fd)
+        tf, f0, f1 = gpu_timed(mfd, args.fd_steps, 1)
+        out["fd64"] = {"value": N * args.fd_steps / tf, "unit": "sample-cycles/s",
+                       "evals_per_s": (f1["evals"] - f0["evals"]) / tf, "ms_per_step": 1e3 * tf / args.fd_steps,
+                       "steps": args.fd_steps}
+        mfd.close()
+        # --- end to end through the C ABI: pinned host population in, modes out, every step
+        xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
+        xh.copy_(torch.from_numpy(prob.x0))
+        xh_np = xh.numpy()
+        for _ in range(2):
+            model.load_population(0, xh_np)
+            model.step()
+            model.modes(0)
+        ts = time.perf_counter()
+        mode_rows = 0
+        for _ in range(args.steps):
+            model.load_population(0, xh_np)
+            model.step()
+            xm, fm = model.modes(0)
+            mode_rows += xm.shape[0]
+        te = time.perf_counter() - ts
+        out["e2e"] = {"value": N * args.steps / te, "unit": "sample-cycles/s",
+                      "h2d_bytes_per_step": N * d * 4,
+                      "d2h_bytes_per_step": int(112 + 4 * (d + 1) * mode_rows / args.steps)}
+        # --- CPU oracle on a bounded sample of the same workload
+        try:
+            cpu = run_cpu_leg(args.workload, args.grad, 0, sample_n=512, budget_s=12.0)
+            out["cpu_baseline"] = {"value": cpu["value"], "unit": "sample-cycles/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{512} of {N} samples, {cpu['cycles']} non-final cycles, "
+                                             f"{args.grad} gradients, FP64 NumPy, single-threaded BLAS",
+                                   "evals_per_s": cpu["evals_per_s"]}
+        except Exception as e:  # report, do not hide
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    model.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reference_arm(args, world, rank):
+    """The oracle as it stands on the host cores, same workload/metric/unit;
+    each step a bounded sample (512 samples, one non-final cycle)."""
+    if rank != 0:
+        return
+    prob = make_problem(args.workload, 0)
+    sample_n = 512
+    cpu = run_cpu_leg(args.workload, args.grad, 0, sample_n=sample_n, budget_s=1e9,
+                      max_cycles=args.warmup + args.steps)
+    ts = cpu["step_times"][args.warmup:]
+    el = float(np.sum(ts))
+    value = sample_n * len(ts) / el
+    out = {"impl": "reference", "metric": f"sample-cycles/s ({args.grad} gradients) at N={prob.n}, d={prob.d}",
+           "value": value, "unit": "sample-cycles/s", "n_gpus": world, "steps": len(ts), "warmup": args.warmup,
+           "ms_per_step": 1e3 * el / max(1, len(ts)), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "N": prob.n, "d": prob.d, "grad": args.grad,
+                      "sample": f"{sample_n} samples per step"},
+           "cpu_baseline": {"value": value, "unit": "sample-cycles/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{sample_n} of {prob.n} samples per step, FP64 NumPy, single-threaded"},
+           "e2e": {"value": value, "unit": "sample-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

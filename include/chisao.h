@@ -1,0 +1,252 @@
+/*
+ * chisao.h -- C ABI of the GB300 (sm_103a) ChiSao population step.
+ *
+ * ChiSao ("Convergence-Halt-Invert-Stick-And-Oscillate") looks for every
+ * significant mode of f on a box Theta (Section 3.1, Eq. 1) by running a
+ * population of N samples through oscillation cycles of six phases
+ * (Algorithm 1): batched L-BFGS ascent (Phase 1, Eq. 2), stick detection
+ * (Phase 2, Eq. 3), L-infinity deduplication (Phase 3, Eq. 4), Repulse Monkey /
+ * Golden Rooster reseeding (Phase 4, Sec. 3.2.4), Hands Like Clouds smoothed
+ * ascent (Phase 5, Eq. 5) and momentum anti-convergence (Phase 6, Eq. 6).
+ * Phases 4-6 are skipped on the last cycle.
+ *
+ * One context owns the device state of one or more independent problems.
+ * Every phase runs in hand-written CUDA kernels on the context's stream;
+ * nothing here falls back to the CPU.
+ *
+ * Conventions
+ *   - Every call returns a chisao_status; none aborts.  On failure the
+ *     context (when there is one) keeps a message for chisao_last_error().
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the context's device.  The library never keeps a
+ *     caller pointer past the call that received it.
+ *   - Populations are row-major float32 [n][d].
+ *   - Calls on one context are not thread-safe; distinct contexts are
+ *     independent.
+ */
+#ifndef CHISAO_H
+#define CHISAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHISAO_MAX_DIM 64        /* largest supported dimension d            */
+#define CHISAO_MAX_MEMORY 10     /* largest L-BFGS memory m                  */
+
+typedef enum {
+  CHISAO_OK = 0,
+  CHISAO_ERR_ARG = 1,        /* invalid argument (sizes, pointers, ranges)   */
+  CHISAO_ERR_CUDA = 2,       /* a CUDA runtime call failed                    */
+  CHISAO_ERR_OOM = 3,        /* device allocation or arena too small         */
+  CHISAO_ERR_CAPACITY = 4,   /* output buffer smaller than the result        */
+  CHISAO_ERR_STATE = 5       /* call not valid in the context's state         */
+} chisao_status;
+
+/* Objective families (built-in device objectives). */
+typedef enum {
+  /* log sum_k w_k N(x; mu_k, diag(sigma_k^2))   (Appendix D mixture)       */
+  CHISAO_OBJ_MIXTURE_DIAG = 1,
+  /* log sum_k w_k N(x; mu_k, L_k L_k^T), L_k lower-triangular Cholesky     */
+  CHISAO_OBJ_MIXTURE_FULL = 2,
+  /* -(x - c)^T Q^T diag(lam) Q (x - c), a log-concave target (Prop. 1)     */
+  CHISAO_OBJ_QUADRATIC = 3
+} chisao_objective_kind;
+
+/* How gradients are obtained (Section 3.1: "by finite differences, or
+ * supplied analytically"). */
+typedef enum {
+  /* central differences at absolute step h; stencil coordinates and every
+   * stencil evaluation in FP64, quotient in FP64, result stored FP32       */
+  CHISAO_GRAD_FD64 = 0,
+  /* central differences at h_j = h_rel * max(1, |x_j|), evaluations FP32   */
+  CHISAO_GRAD_FD32 = 1,
+  /* exact gradient from the objective's hand-written adjoint, FP32         */
+  CHISAO_GRAD_ADJOINT = 2
+} chisao_grad_mode;
+
+/* Objective description.  All arrays are host FP64, row-major, read during
+ * chisao_create only.  Unused fields may be NULL.
+ *   MIXTURE_DIAG: weights[K], means[K][d], sigmas[K][d]  (sigma > 0)
+ *   MIXTURE_FULL: weights[K], means[K][d], chol[K][d][d] (lower, diag > 0)
+ *   QUADRATIC:    center[d], Q[d][d], lam[d]             (K ignored)        */
+typedef struct {
+  int32_t kind;            /* chisao_objective_kind                          */
+  int32_t n_comp;          /* K for mixtures                                 */
+  const double *weights;
+  const double *means;     /* mixtures: means; quadratic: unused             */
+  const double *sigmas;
+  const double *chol;
+  const double *center;
+  const double *Q;
+  const double *lam;
+} chisao_objective;
+
+/* One problem: dimension, population size, the box Theta and the initial
+ * population (host, float32 [n][d], copied at create). */
+typedef struct {
+  int32_t d;               /* 1 .. CHISAO_MAX_DIM                           */
+  int64_t n;               /* population size, >= 1                          */
+  const double *lo;        /* host [d] lower corner of Theta                 */
+  const double *hi;        /* host [d] upper corner, hi > lo                 */
+  const float *x0;         /* host [n][d] initial population                 */
+  chisao_objective objective;
+} chisao_problem;
+
+/* Hyperparameters: Table 1 of the paper plus the values that fix details
+ * the paper leaves open (line search, FD step, step-size rule). */
+typedef struct {
+  int32_t n_osc;           /* oscillation cycles (Table 1: 3)                */
+  int32_t n_conv;          /* L-BFGS steps per Phase 1; 0: max(10, ceil(3 log2 d)) */
+  int32_t n_anti;          /* anti-convergence steps (5)                      */
+  int32_t n_cloud;         /* Hands Like Clouds steps (3)                     */
+  int32_t M;               /* perturbations per smoothed gradient (Eq. 5)    */
+  int32_t m;               /* L-BFGS memory, 1 .. CHISAO_MAX_MEMORY (10)     */
+  int32_t T_ls;            /* backtracking trials per line search (20)       */
+  int32_t grad_mode;       /* chisao_grad_mode                                */
+  double eps_grad;         /* stick threshold on |grad f|_inf (Eq. 3)        */
+  double eps_dup;          /* dedup L-inf radius (Eq. 4)                      */
+  double delta;            /* quality threshold, stuck iff f >= f_max + log delta */
+  double mu;               /* momentum (Eq. 6)                                */
+  double alpha;            /* anti/HLC step; <= 0: alpha_scale * s / g_rms    */
+  double sigma;            /* HLC smoothing scale; <= 0: c_sigma * s          */
+  double c_sigma;          /* 0.1                                             */
+  double alpha_scale;      /* 0.1                                             */
+  double h;                /* FD64 absolute step (1e-5)                       */
+  double h_rel;            /* FD32 relative step (2^(-23/3))                  */
+  double c1;               /* Armijo constant (1e-4)                          */
+  double curv_eps;         /* keep (s, y) iff s^T y > curv_eps |s| |y|        */
+  uint64_t seed;           /* Philox key                                      */
+  int32_t rm_min_unfrozen; /* Repulse Monkey iff >= this many unfrozen (5)    */
+  int32_t gr_patience;     /* Golden Rooster off after this many idle generations (2) */
+  int32_t use_graph;       /* 1: capture each cycle in a CUDA graph           */
+  int32_t reserved;
+} chisao_params;
+
+/* Per-problem counters accumulated on the device since create. */
+typedef struct {
+  uint64_t evals;          /* objective evaluations (value computations)      */
+  uint64_t grads;          /* gradient computations (FD or adjoint)           */
+  uint64_t ls_trials;      /* line-search trial points                         */
+  uint64_t ls_fail;        /* line searches with no acceptable step            */
+  int64_t cycles;          /* completed cycles                                  */
+  int64_t n_stuck;         /* stuck samples after the last deduplication        */
+  int64_t k_lost;          /* samples removed by the last deduplication         */
+  int64_t n_unfrozen;      /* unfrozen samples counted for the last reseeding   */
+  int32_t last_reseed;     /* 0 none, 1 Repulse Monkey, 2 Golden Rooster, 3 uniform */
+  int32_t gr_enabled;      /* Golden Rooster still enabled                      */
+  float f_max;             /* max_i f(x_i) of the last Phase 2                   */
+  float sigma;             /* last HLC smoothing scale                           */
+  float alpha_hlc;         /* last HLC step                                      */
+  float alpha_anti;        /* last anti-convergence step                         */
+} chisao_counters;
+
+typedef struct chisao_ctx chisao_ctx;
+
+/* Fill *p with the defaults of Table 1 (n_osc 3, n_anti 5, n_cloud 3,
+ * eps_grad 1e-6, eps_dup 1e-3, delta 0.1, mu 0.9, sigma/alpha auto) and the
+ * stated readings (M 8, m 10, T_ls 20, h 1e-5, c1 1e-4). */
+void chisao_default_params(chisao_params *p);
+
+/* Bytes of device memory a context for these problems needs.  Returns
+ * CHISAO_ERR_ARG for invalid problems or parameters. */
+chisao_status chisao_arena_bytes(const chisao_problem *probs, int32_t n_probs,
+                                 const chisao_params *params, size_t *bytes);
+
+/* Create a context: validate, carve the device state out of `arena` (device,
+ * >= chisao_arena_bytes, 256-byte aligned; it stays owned by the caller and
+ * must outlive the context) or, when arena is NULL, allocate it with
+ * cudaMalloc; copy objectives and initial populations; bind `cuda_stream`
+ * (a cudaStream_t, NULL for the legacy default stream).  *out receives the
+ * context.  Synchronous. */
+chisao_status chisao_create(const chisao_problem *probs, int32_t n_probs,
+                            const chisao_params *params, void *arena,
+                            size_t arena_bytes, void *cuda_stream,
+                            chisao_ctx **out);
+
+/* One oscillation cycle (Algorithm 1, one iteration of its outer loop) for
+ * every problem: asynchronous on the context's stream.  The n_osc-th call runs
+ * the last cycle (Phases 1-3 only); calls after it return CHISAO_ERR_STATE. */
+chisao_status chisao_step(chisao_ctx *c);
+
+/* Replace problem `prob`'s population by host x[n][d] (float32) and reset its
+ * per-sample state (history, stuck flags, counters) and the context's cycle
+ * count.  The copy is ordered on the context's stream: x_host must stay
+ * unchanged until the stream has passed it (any later synchronizing call
+ * such as chisao_modes, or a stream synchronize). */
+chisao_status chisao_load_population(chisao_ctx *c, int32_t prob, const float *x_host);
+
+/* The estimated mode set {x_i : stuck_i} of problem `prob` after the last
+ * deduplication (Algorithm 1's return value), in sample-index order:
+ * x_out host [cap][d], f_out host [cap] (may be NULL).  *count receives the
+ * number of modes; CHISAO_ERR_CAPACITY (nothing written) when cap < count.
+ * Synchronizes the stream. */
+chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
+                           float *f_out, int64_t cap, int64_t *count);
+
+/* Counters of problem `prob` (synchronizes the stream). */
+chisao_status chisao_get_counters(chisao_ctx *c, int32_t prob, chisao_counters *out);
+
+/* Evaluate problem `prob`'s objective at n device points x_dev[n][d]:
+ * f_dev[n] (may be NULL) and, when g_dev[n][d] is not NULL, the gradient by
+ * `grad_mode`.  This is the device objective the step uses, exposed for
+ * autograd wrappers and tests.  Asynchronous on the context's stream. */
+chisao_status chisao_eval(chisao_ctx *c, int32_t prob, const float *x_dev, int64_t n,
+                          float *f_dev, float *g_dev, int32_t grad_mode);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *chisao_last_error(const chisao_ctx *c);
+
+/* Free the context and everything it allocated (not a caller arena). */
+void chisao_destroy(chisao_ctx *c);
+
+/* ---------------------------------------------------------------------------
+ * Test hooks: per-phase entry points and raw state access, used by the parity
+ * tests to run one phase from a state both sides share.  They act on one
+ * problem, asynchronously on the context's stream unless stated.
+ * ------------------------------------------------------------------------- */
+
+typedef enum {
+  CHISAO_FIELD_X = 0,        /* float [n][dp]   positions (dp = padded d)     */
+  CHISAO_FIELD_G = 1,        /* float [n][dp]   gradient of f                  */
+  CHISAO_FIELD_F = 2,        /* float [n]       f                              */
+  CHISAO_FIELD_HS = 3,       /* float [n][m_max][dp]  s pairs, slot 0 newest    */
+  CHISAO_FIELD_HY = 4,       /* float [n][m_max][dp]  y pairs of F = -f          */
+  CHISAO_FIELD_HRHO = 5,     /* double [n][m_max]     1 / s^T y                  */
+  CHISAO_FIELD_HLEN = 6,     /* int32 [n]       stored pairs                    */
+  CHISAO_FIELD_STUCK = 7,    /* uint32 [ceil(n/32)] stuck bit mask               */
+  CHISAO_FIELD_REMOVED = 8   /* uint32 [ceil(n/32)] removed-by-dedup bit mask     */
+} chisao_field;
+
+typedef enum {
+  CHISAO_PHASE_LBFGS = 1,     /* arg iterations of Phase 1 (arg<0: -arg, no fresh gradient) */
+  CHISAO_PHASE_FREEZE = 2,    /* Phase 2 on the current f, g                 */
+  CHISAO_PHASE_DEDUP = 3,     /* Phase 3 on the stuck mask (compacts it first) */
+  CHISAO_PHASE_RESEED = 4,    /* Phase 4 for cycle number arg                 */
+  CHISAO_PHASE_HLC = 5,       /* Phase 5 for cycle number arg                 */
+  CHISAO_PHASE_ANTI = 6,      /* Phase 6                                       */
+  CHISAO_PHASE_DIRECTION = 7, /* write the L-BFGS direction p into G         */
+  CHISAO_PHASE_LISTS = 8      /* stuck &= ~removed, then the free / unfrozen /
+                                 survivor lists from the two masks            */
+} chisao_phase;
+
+/* Padded row length dp and m_max used by the raw fields of problem prob. */
+chisao_status chisao_layout(chisao_ctx *c, int32_t prob, int32_t *dp, int32_t *m_max);
+/* Copy a raw field to / from host memory (synchronous; bytes must match). */
+chisao_status chisao_state_get(chisao_ctx *c, int32_t prob, int32_t field, void *host, size_t bytes);
+chisao_status chisao_state_set(chisao_ctx *c, int32_t prob, int32_t field, const void *host, size_t bytes);
+/* Run one phase of problem prob (see chisao_phase); asynchronous on the
+ * context's stream (state_get synchronizes). */
+chisao_status chisao_run_phase(chisao_ctx *c, int32_t prob, int32_t phase, int32_t arg);
+/* Set the Golden Rooster bookkeeping (enabled, idle generations, survivor
+ * count at the previous generation, -1 for none). */
+chisao_status chisao_set_gr_state(chisao_ctx *c, int32_t prob, int32_t enabled,
+                                  int32_t noprog, int32_t prev_surv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHISAO_H */

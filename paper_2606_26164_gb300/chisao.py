@@ -1,0 +1,295 @@
+"""ctypes binding of the C ABI in include/chisao.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libchisao.so``; when it is
+missing this module raises instead of falling back to anything else.  PyTorch
+supplies device memory (the context arena) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libchisao.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE = 0, 1, 2, 3, 4, 5
+GRAD_FD64, GRAD_FD32, GRAD_ADJOINT = 0, 1, 2
+FIELD_X, FIELD_G, FIELD_F, FIELD_HS, FIELD_HY, FIELD_HRHO, FIELD_HLEN, FIELD_STUCK, FIELD_REMOVED = range(9)
+PHASE_LBFGS, PHASE_FREEZE, PHASE_DEDUP, PHASE_RESEED, PHASE_HLC, PHASE_ANTI, PHASE_DIRECTION, PHASE_LISTS = range(1, 9)
+MMAX = 10
+
+EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chisao_step",
+           "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
+           "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
+           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state"]
+
+
+class CParams(C.Structure):
+    _fields_ = [("n_osc", C.c_int32), ("n_conv", C.c_int32), ("n_anti", C.c_int32), ("n_cloud", C.c_int32),
+                ("M", C.c_int32), ("m", C.c_int32), ("T_ls", C.c_int32), ("grad_mode", C.c_int32),
+                ("eps_grad", C.c_double), ("eps_dup", C.c_double), ("delta", C.c_double), ("mu", C.c_double),
+                ("alpha", C.c_double), ("sigma", C.c_double), ("c_sigma", C.c_double),
+                ("alpha_scale", C.c_double), ("h", C.c_double), ("h_rel", C.c_double), ("c1", C.c_double),
+                ("curv_eps", C.c_double), ("seed", C.c_uint64), ("rm_min_unfrozen", C.c_int32),
+                ("gr_patience", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class CObjective(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_comp", C.c_int32), ("weights", _DP), ("means", _DP),
+                ("sigmas", _DP), ("chol", _DP), ("center", _DP), ("Q", _DP), ("lam", _DP)]
+
+
+class CProblem(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n", C.c_int64), ("lo", _DP), ("hi", _DP),
+                ("x0", C.POINTER(C.c_float)), ("objective", CObjective)]
+
+
+class CCounters(C.Structure):
+    _fields_ = [("evals", C.c_uint64), ("grads", C.c_uint64), ("ls_trials", C.c_uint64), ("ls_fail", C.c_uint64),
+                ("cycles", C.c_int64), ("n_stuck", C.c_int64), ("k_lost", C.c_int64), ("n_unfrozen", C.c_int64),
+                ("last_reseed", C.c_int32), ("gr_enabled", C.c_int32), ("f_max", C.c_float),
+                ("sigma", C.c_float), ("alpha_hlc", C.c_float), ("alpha_anti", C.c_float)]
+
+
+_lib = None
+
+
+def library() -> C.CDLL:
+    """Load the CUDA library; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_2606_26164_gb300.build)")
+        lib = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        lib.chisao_default_params.argtypes = [C.POINTER(CParams)]
+        lib.chisao_default_params.restype = None
+        lib.chisao_arena_bytes.argtypes = [C.POINTER(CProblem), C.c_int32, C.POINTER(CParams), C.POINTER(C.c_size_t)]
+        lib.chisao_create.argtypes = [C.POINTER(CProblem), C.c_int32, C.POINTER(CParams), vp, C.c_size_t, vp,
+                                      C.POINTER(vp)]
+        lib.chisao_step.argtypes = [vp]
+        lib.chisao_load_population.argtypes = [vp, C.c_int32, C.POINTER(C.c_float)]
+        lib.chisao_modes.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
+                                     C.POINTER(C.c_int64)]
+        lib.chisao_get_counters.argtypes = [vp, C.c_int32, C.POINTER(CCounters)]
+        lib.chisao_eval.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, vp, C.c_int32]
+        lib.chisao_last_error.argtypes = [vp]
+        lib.chisao_last_error.restype = C.c_char_p
+        lib.chisao_destroy.argtypes = [vp]
+        lib.chisao_destroy.restype = None
+        lib.chisao_layout.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        lib.chisao_state_get.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
+        lib.chisao_state_set.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
+        lib.chisao_run_phase.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+        lib.chisao_set_gr_state.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+        for name in EXPORTS:
+            if name not in ("chisao_default_params", "chisao_last_error", "chisao_destroy"):
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def default_params(**over) -> CParams:
+    p = CParams()
+    library().chisao_default_params(C.byref(p))
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class ChisaoError(RuntimeError):
+    pass
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return a.ctypes.data_as(_DP) if a is not None else None
+
+
+class Chisao:
+    """One context over one or more problems (``inputs.Problem``)."""
+
+    def __init__(self, problems: Sequence[I.Problem], params: CParams, use_torch_arena: bool = True,
+                 stream=None):
+        lib = library()
+        self._keep = []
+        cprobs = (CProblem * len(problems))()
+        for q, pr in enumerate(problems):
+            ob = pr.objective
+            A = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in ob.arrays.items()}
+            lo = np.ascontiguousarray(pr.lo, np.float64)
+            hi = np.ascontiguousarray(pr.hi, np.float64)
+            x0 = np.ascontiguousarray(pr.x0, np.float32)
+            self._keep += [A, lo, hi, x0]
+            co = CObjective(kind=ob.kind, n_comp=ob.n_comp, weights=_dptr(A.get("weights")),
+                            means=_dptr(A.get("means")), sigmas=_dptr(A.get("sigmas")), chol=_dptr(A.get("chol")),
+                            center=_dptr(A.get("center")), Q=_dptr(A.get("Q")), lam=_dptr(A.get("lam")))
+            cprobs[q] = CProblem(d=pr.d, n=pr.n, lo=_dptr(lo), hi=_dptr(hi),
+                                 x0=x0.ctypes.data_as(C.POINTER(C.c_float)), objective=co)
+        self.problems = list(problems)
+        self.params = params
+        nbytes = C.c_size_t(0)
+        st = lib.chisao_arena_bytes(cprobs, len(problems), C.byref(params), C.byref(nbytes))
+        if st != OK:
+            raise ChisaoError(f"chisao_arena_bytes failed ({st})")
+        self.arena_bytes = nbytes.value
+        arena_ptr = None
+        self._arena = None
+        self._stream = None
+        import torch
+        if stream is None:
+            self._stream = torch.cuda.Stream()
+            stream_ptr = self._stream.cuda_stream
+        else:
+            self._stream = stream
+            stream_ptr = stream.cuda_stream
+        if use_torch_arena:
+            self._arena = torch.empty(self.arena_bytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._arena.data_ptr()
+            arena_ptr = (base + 255) // 256 * 256
+        ctx = C.c_void_p()
+        st = lib.chisao_create(cprobs, len(problems), C.byref(params), arena_ptr, self.arena_bytes,
+                               C.c_void_p(stream_ptr), C.byref(ctx))
+        if st != OK:
+            raise ChisaoError(f"chisao_create failed ({st})")
+        self.ctx = ctx
+        self._keep = []
+
+    # ------------------------------------------------------------------ core API
+    def _check(self, st, what):
+        if st != OK:
+            msg = library().chisao_last_error(self.ctx).decode()
+            raise ChisaoError(f"{what} failed ({st}): {msg}")
+
+    def step(self):
+        self._check(library().chisao_step(self.ctx), "chisao_step")
+
+    def load_population(self, prob: int, x: np.ndarray):
+        x = np.ascontiguousarray(x, np.float32)
+        self._check(library().chisao_load_population(self.ctx, prob, x.ctypes.data_as(C.POINTER(C.c_float))),
+                    "chisao_load_population")
+        self.synchronize()
+
+    def modes(self, prob: int = 0, cap: Optional[int] = None):
+        pr = self.problems[prob]
+        cap = pr.n if cap is None else cap
+        xo = np.empty((max(cap, 1), pr.d), np.float32)
+        fo = np.empty(max(cap, 1), np.float32)
+        cnt = C.c_int64(0)
+        self._check(library().chisao_modes(self.ctx, prob, xo.ctypes.data_as(C.POINTER(C.c_float)),
+                                           fo.ctypes.data_as(C.POINTER(C.c_float)), cap, C.byref(cnt)),
+                    "chisao_modes")
+        k = cnt.value
+        return xo[:k].copy(), fo[:k].copy()
+
+    def counters(self, prob: int = 0) -> dict:
+        c = CCounters()
+        self._check(library().chisao_get_counters(self.ctx, prob, C.byref(c)), "chisao_get_counters")
+        return {name: getattr(c, name) for name, _ in CCounters._fields_}
+
+    def eval(self, prob: int, x, grad_mode: int = GRAD_ADJOINT, want_grad: bool = True):
+        """f (and grad f) at device points x (a CUDA float32 tensor [n, d])."""
+        import torch
+        x = x.contiguous()
+        n = x.shape[0]
+        f = torch.empty(n, dtype=torch.float32, device=x.device)
+        g = torch.empty_like(x) if want_grad else None
+        self._stream.wait_stream(torch.cuda.current_stream())
+        self._check(library().chisao_eval(self.ctx, prob, x.data_ptr(), n, f.data_ptr(),
+                                          g.data_ptr() if g is not None else None, grad_mode), "chisao_eval")
+        torch.cuda.current_stream().wait_stream(self._stream)
+        return f, g
+
+    def synchronize(self):
+        self._stream.synchronize()
+
+    # ------------------------------------------------------------------ test hooks
+    def layout(self, prob: int = 0):
+        dp, mm = C.c_int32(0), C.c_int32(0)
+        self._check(library().chisao_layout(self.ctx, prob, C.byref(dp), C.byref(mm)), "chisao_layout")
+        return dp.value, mm.value
+
+    def _field_shape(self, prob, field):
+        pr = self.problems[prob]
+        dp, mm = self.layout(prob)
+        n = pr.n
+        return {FIELD_X: ((n, dp), np.float32), FIELD_G: ((n, dp), np.float32), FIELD_F: ((n,), np.float32),
+                FIELD_HS: ((n, mm, dp), np.float32), FIELD_HY: ((n, mm, dp), np.float32),
+                FIELD_HRHO: ((n, mm), np.float64), FIELD_HLEN: ((n,), np.int32),
+                FIELD_STUCK: (((n + 31) // 32,), np.uint32), FIELD_REMOVED: (((n + 31) // 32,), np.uint32)}[field]
+
+    def get(self, prob: int, field: int) -> np.ndarray:
+        shape, dt = self._field_shape(prob, field)
+        a = np.empty(shape, dt)
+        self._check(library().chisao_state_get(self.ctx, prob, field, a.ctypes.data, a.nbytes), "chisao_state_get")
+        return a
+
+    def set(self, prob: int, field: int, value: np.ndarray):
+        shape, dt = self._field_shape(prob, field)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(value, dtype=dt), shape))
+        self._check(library().chisao_state_set(self.ctx, prob, field, a.ctypes.data, a.nbytes), "chisao_state_set")
+
+    def run_phase(self, prob: int, phase: int, arg: int = 0):
+        self._check(library().chisao_run_phase(self.ctx, prob, phase, arg), "chisao_run_phase")
+
+    def set_gr_state(self, prob: int, enabled: int, noprog: int, prev_surv: int):
+        self._check(library().chisao_set_gr_state(self.ctx, prob, enabled, noprog, prev_surv),
+                    "chisao_set_gr_state")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            library().chisao_destroy(self.ctx)
+            self.ctx = None
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:
+    b = np.unpackbits(words.view(np.uint8), bitorder="little")
+    return b[:n].astype(bool)
+
+
+def pack_bits(mask: np.ndarray) -> np.ndarray:
+    n = mask.shape[0]
+    nw = (n + 31) // 32
+    b = np.zeros(nw * 32, np.uint8)
+    b[:n] = mask.astype(np.uint8)
+    return np.packbits(b, bitorder="little").view(np.uint32)
+
+
+class ChisaoObjective:
+    """torch.autograd.Function over the library's objective: forward = value,
+    backward = the hand-written adjoint (exact gradient) times grad_output."""
+
+    @staticmethod
+    def apply(model: Chisao, prob: int, x):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, xin):
+                f, g = model.eval(prob, xin.detach(), GRAD_ADJOINT, want_grad=True)
+                ctx.save_for_backward(g)
+                return f
+
+            @staticmethod
+            def backward(ctx, gout):
+                (g,) = ctx.saved_tensors
+                return gout[:, None] * g
+
+        return _Fn.apply(x)

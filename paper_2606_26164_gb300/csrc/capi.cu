@@ -1,0 +1,717 @@
+// C ABI of the ChiSao population step (declared in include/chisao.h).
+//
+// Host responsibilities only: argument validation, the device-memory layout,
+// FP64 preparation of the objective parameters (mixture constants, triangular
+// inverses, A = Q^T diag(lam) Q), enqueueing the per-cycle kernel sequence of
+// Algorithm 1 and capturing it in CUDA graphs.  Every phase itself runs in the
+// kernels of phase_kernels.cu and obj_kernels.cuh.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/chisao.h"
+#include "host.h"
+
+using namespace chisao;
+
+namespace {
+
+constexpr int MAX_PART_BLOCKS = 608;
+constexpr size_t ALIGN = 256;
+constexpr long long MAX_N = 1ll << 27;
+
+struct ProbHost {
+  int d = 0, dp = 0, kind = 0, K = 0;
+  long long n = 0;
+  ProbDev dev{};
+  StepParams sp{};
+  float* gather_x = nullptr;
+  float* gather_f = nullptr;
+};
+
+// Bump allocator over the arena; with a null base it only measures.
+struct Bump {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + ALIGN - 1) / ALIGN * ALIGN;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int pad_dim(int d) {
+  int dp = 4;
+  while (dp < d) dp <<= 1;
+  return dp;
+}
+
+}  // namespace
+
+struct chisao_ctx {
+  chisao_params params{};
+  std::vector<ProbHost> probs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  int cycles_done = 0;
+  cudaGraphExec_t g_mid = nullptr, g_last = nullptr;
+  std::string err;
+};
+
+namespace {
+
+chisao_status fail(chisao_ctx* c, chisao_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+chisao_status cuda_fail(chisao_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, CHISAO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);    \
+  } while (0)
+
+chisao_status validate_params(const chisao_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return CHISAO_ERR_ARG; }
+  if (p->n_osc < 1) { why = "n_osc must be >= 1"; return CHISAO_ERR_ARG; }
+  if (p->n_conv < 0 || p->n_anti < 0 || p->n_cloud < 0) { why = "step counts must be >= 0"; return CHISAO_ERR_ARG; }
+  if (p->M < 1 || p->M > 65535) { why = "M must be in [1, 65535]"; return CHISAO_ERR_ARG; }
+  if (p->m < 1 || p->m > CHISAO_MAX_MEMORY) { why = "m must be in [1, 10]"; return CHISAO_ERR_ARG; }
+  if (p->T_ls < 1 || p->T_ls > 126) { why = "T_ls must be in [1, 126]"; return CHISAO_ERR_ARG; }
+  if (p->n_cloud > 255) { why = "n_cloud must be <= 255"; return CHISAO_ERR_ARG; }
+  if (p->grad_mode < 0 || p->grad_mode > 2) { why = "unknown grad_mode"; return CHISAO_ERR_ARG; }
+  if (!(p->eps_grad > 0) || !(p->eps_dup > 0)) { why = "eps_grad and eps_dup must be > 0"; return CHISAO_ERR_ARG; }
+  if (!(p->delta > 0 && p->delta < 1)) { why = "delta must be in (0, 1)"; return CHISAO_ERR_ARG; }
+  if (!(p->h > 0) || !(p->h_rel > 0) || !(p->c1 > 0 && p->c1 < 1)) { why = "h, h_rel > 0 and c1 in (0,1) required"; return CHISAO_ERR_ARG; }
+  if (!std::isfinite(p->mu) || !std::isfinite(p->alpha) || !std::isfinite(p->sigma)) { why = "mu, alpha, sigma must be finite"; return CHISAO_ERR_ARG; }
+  if (p->rm_min_unfrozen < 1 || p->gr_patience < 1) { why = "rm_min_unfrozen and gr_patience must be >= 1"; return CHISAO_ERR_ARG; }
+  return CHISAO_OK;
+}
+
+chisao_status validate_problem(const chisao_problem* pr, std::string& why) {
+  if (pr->d < 1 || pr->d > CHISAO_MAX_DIM) { why = "d must be in [1, 64]"; return CHISAO_ERR_ARG; }
+  if (pr->n < 1 || pr->n > MAX_N) { why = "n must be in [1, 2^27]"; return CHISAO_ERR_ARG; }
+  if (!pr->lo || !pr->hi || !pr->x0) { why = "lo, hi and x0 are required"; return CHISAO_ERR_ARG; }
+  for (int j = 0; j < pr->d; ++j)
+    if (!(std::isfinite(pr->lo[j]) && std::isfinite(pr->hi[j]) && pr->lo[j] < pr->hi[j])) {
+      why = "box needs finite lo < hi";
+      return CHISAO_ERR_ARG;
+    }
+  const chisao_objective& o = pr->objective;
+  if (o.kind == CHISAO_OBJ_MIXTURE_DIAG || o.kind == CHISAO_OBJ_MIXTURE_FULL) {
+    if (o.n_comp < 1 || o.n_comp > 65536) { why = "mixture needs 1 <= K <= 65536"; return CHISAO_ERR_ARG; }
+    if (!o.weights || !o.means) { why = "mixture needs weights and means"; return CHISAO_ERR_ARG; }
+    for (int k = 0; k < o.n_comp; ++k)
+      if (!(o.weights[k] > 0)) { why = "mixture weights must be > 0"; return CHISAO_ERR_ARG; }
+    if (o.kind == CHISAO_OBJ_MIXTURE_DIAG) {
+      if (!o.sigmas) { why = "diagonal mixture needs sigmas"; return CHISAO_ERR_ARG; }
+      for (long long t = 0; t < (long long)o.n_comp * pr->d; ++t)
+        if (!(o.sigmas[t] > 0)) { why = "sigmas must be > 0"; return CHISAO_ERR_ARG; }
+    } else {
+      if (!o.chol) { why = "full mixture needs chol"; return CHISAO_ERR_ARG; }
+      for (int k = 0; k < o.n_comp; ++k)
+        for (int j = 0; j < pr->d; ++j)
+          if (!(o.chol[((size_t)k * pr->d + j) * pr->d + j] > 0)) { why = "Cholesky diagonals must be > 0"; return CHISAO_ERR_ARG; }
+    }
+  } else if (o.kind == CHISAO_OBJ_QUADRATIC) {
+    if (!o.center || !o.Q || !o.lam) { why = "quadratic needs center, Q and lam"; return CHISAO_ERR_ARG; }
+  } else {
+    why = "unknown objective kind";
+    return CHISAO_ERR_ARG;
+  }
+  return CHISAO_OK;
+}
+
+size_t obj_elems(const chisao_problem& pr, int dp, size_t* n0, size_t* n1, size_t* n2, size_t* n3) {
+  const size_t K = (size_t)pr.objective.n_comp;
+  switch (pr.objective.kind) {
+    case CHISAO_OBJ_MIXTURE_DIAG: *n0 = K * dp; *n1 = K * dp; *n2 = K; *n3 = 0; break;
+    case CHISAO_OBJ_MIXTURE_FULL: *n0 = K * dp; *n1 = K * dp * dp; *n2 = K; *n3 = K * dp * dp; break;
+    default: *n0 = dp; *n1 = (size_t)dp * dp; *n2 = 0; *n3 = 0; break;
+  }
+  return *n0 + *n1 + *n2 + *n3;
+}
+
+// Carve one problem's buffers (measure-only when b.base is null).
+void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
+  const int d = pr.d, dp = pad_dim(d);
+  const size_t n = (size_t)pr.n, nw = (n + 31) / 32;
+  ProbDev& P = ph.dev;
+  P.x = b.take<float>(n * dp);
+  P.g = b.take<float>(n * dp);
+  P.f = b.take<float>(n);
+  P.hs = b.take<float>(n * MMAX * dp);
+  P.hy = b.take<float>(n * MMAX * dp);
+  P.hrho = b.take<double>(n * MMAX);
+  P.hlen = b.take<int>(n);
+  P.hgam = nullptr;
+  P.stuck = b.take<uint32_t>(nw);
+  P.removed = b.take<uint32_t>(nw);
+  P.l_stuck = b.take<int>(n);
+  P.l_free = b.take<int>(n);
+  P.l_unf = b.take<int>(n);
+  P.l_surv = b.take<int>(n);
+  P.l_rank = b.take<int>(n);
+  P.lo = b.take<float>(dp);
+  P.hi = b.take<float>(dp);
+  P.cnt = b.take<Counters>(1);
+  P.partials = b.take<double>((size_t)MAX_PART_BLOCKS * (2 * dp + 2));
+  P.max_part_blocks = MAX_PART_BLOCKS;
+  P.grq = b.take<double>((size_t)d * d);
+  size_t n0, n1, n2, n3;
+  obj_elems(pr, dp, &n0, &n1, &n2, &n3);
+  P.obj.f32.p0 = b.take<float>(n0);
+  P.obj.f32.p1 = b.take<float>(n1);
+  P.obj.f32.p2 = n2 ? b.take<float>(n2) : nullptr;
+  P.obj.f32.p3 = n3 ? b.take<float>(n3) : nullptr;
+  P.obj.f64.p0 = b.take<double>(n0);
+  P.obj.f64.p1 = b.take<double>(n1);
+  P.obj.f64.p2 = n2 ? b.take<double>(n2) : nullptr;
+  P.obj.f64.p3 = n3 ? b.take<double>(n3) : nullptr;
+  ph.gather_x = b.take<float>(n * d);
+  ph.gather_f = b.take<float>(n);
+}
+
+// FP64 objective constants on the host, padded to dp (zeros in the padding).
+void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0, std::vector<double>& a1,
+                       std::vector<double>& a2, std::vector<double>& a3) {
+  const int d = pr.d;
+  const chisao_objective& o = pr.objective;
+  size_t n0, n1, n2, n3;
+  obj_elems(pr, dp, &n0, &n1, &n2, &n3);
+  a0.assign(n0, 0.0);
+  a1.assign(n1, 0.0);
+  a2.assign(n2, 0.0);
+  a3.assign(n3, 0.0);
+  const double half_log2pi = 0.5 * std::log(2.0 * M_PI);
+  if (o.kind == CHISAO_OBJ_MIXTURE_DIAG) {
+    for (int k = 0; k < o.n_comp; ++k) {
+      double ls = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const double s = o.sigmas[(size_t)k * d + j];
+        a0[(size_t)k * dp + j] = o.means[(size_t)k * d + j];
+        a1[(size_t)k * dp + j] = 1.0 / (s * s);
+        ls += std::log(s);
+      }
+      a2[k] = std::log(o.weights[k]) - ls - d * half_log2pi;
+    }
+  } else if (o.kind == CHISAO_OBJ_MIXTURE_FULL) {
+    std::vector<double> inv((size_t)d * d);
+    for (int k = 0; k < o.n_comp; ++k) {
+      const double* L = o.chol + (size_t)k * d * d;
+      // inverse of the lower-triangular L by forward substitution, column by column
+      std::fill(inv.begin(), inv.end(), 0.0);
+      for (int c = 0; c < d; ++c) {
+        for (int i = c; i < d; ++i) {
+          double s = (i == c) ? 1.0 : 0.0;
+          for (int j = c; j < i; ++j) s -= L[(size_t)i * d + j] * inv[(size_t)j * d + c];
+          inv[(size_t)i * d + c] = s / L[(size_t)i * d + i];
+        }
+      }
+      double ld = 0.0;
+      for (int j = 0; j < d; ++j) {
+        ld += std::log(L[(size_t)j * d + j]);
+        a0[(size_t)k * dp + j] = o.means[(size_t)k * d + j];
+      }
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          a1[((size_t)k * dp + i) * dp + j] = inv[(size_t)i * d + j];
+          a3[((size_t)k * dp + j) * dp + i] = inv[(size_t)i * d + j];
+        }
+      a2[k] = std::log(o.weights[k]) - ld - d * half_log2pi;
+    }
+  } else {
+    for (int j = 0; j < d; ++j) a0[j] = o.center[j];
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) s += o.Q[(size_t)i * d + a] * o.lam[i] * o.Q[(size_t)i * d + b];
+        a1[(size_t)a * dp + b] = s;
+      }
+  }
+}
+
+StepParams make_step_params(const chisao_params& p, int d) {
+  StepParams s{};
+  s.n_conv = p.n_conv > 0 ? p.n_conv : (d > 1 ? std::max(10, (int)std::ceil(3.0 * std::log2((double)d))) : 10);
+  s.n_anti = p.n_anti;
+  s.n_cloud = p.n_cloud;
+  s.M = p.M;
+  s.m = p.m;
+  s.T_ls = p.T_ls;
+  s.grad_mode = p.grad_mode;
+  s.rm_min = p.rm_min_unfrozen;
+  s.gr_patience = p.gr_patience;
+  s.eps_grad = (float)p.eps_grad;
+  s.eps_dup = (float)p.eps_dup;
+  s.log_delta = (float)std::log(p.delta);
+  s.mu = (float)p.mu;
+  s.alpha_fixed = (float)p.alpha;
+  s.sigma_fixed = (float)p.sigma;
+  s.c_sigma = (float)p.c_sigma;
+  s.alpha_scale = (float)p.alpha_scale;
+  s.h = p.h;
+  s.h_rel = p.h_rel;
+  s.c1 = p.c1;
+  s.curv_eps = p.curv_eps;
+  s.seed_lo = (unsigned)(p.seed & 0xffffffffu);
+  s.seed_hi = (unsigned)(p.seed >> 32);
+  return s;
+}
+
+cudaError_t launch_objective(int which, const ProbHost& ph, int gm, int arg, const EvalArgs* ea, cudaStream_t st) {
+  switch (ph.kind) {
+    case CHISAO_OBJ_MIXTURE_DIAG: return launch_obj_mixdiag(which, gm, ph.dev, ph.sp, arg, ea, st);
+    case CHISAO_OBJ_MIXTURE_FULL: return launch_obj_mixfull(which, gm, ph.dev, ph.sp, arg, ea, st);
+    default: return launch_obj_quad(which, gm, ph.dev, ph.sp, arg, ea, st);
+  }
+}
+
+__global__ void k_reset_problem(ProbDev P) {
+  if (threadIdx.x != 0) return;
+  Counters* c = P.cnt;
+  memset(c, 0, sizeof(Counters));
+  c->gr_enabled = 1;
+  c->gr_prev_surv = -1;
+}
+
+// Phases 4-6 of one problem (reseed, HLC with its scale pass, anti with its scale pass).
+cudaError_t enqueue_explore(const ProbHost& ph, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_reseed(ph.dev, ph.sp, st)) != cudaSuccess) return e;
+  if ((e = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_scales(ph.dev, ph.sp, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_objective(OKID_HLC, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_scales(ph.dev, ph.sp, 1, st)) != cudaSuccess) return e;
+  return launch_objective(OKID_ANTI, ph, ph.sp.grad_mode, 0, nullptr, st);
+}
+
+// One oscillation cycle (Algorithm 1) of every problem.
+cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
+  cudaError_t e;
+  for (const ProbHost& ph : c->probs) {
+    if ((e = launch_cycle_begin(ph.dev, c->stream)) != cudaSuccess) return e;                  // release all
+    if ((e = launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, ph.sp.n_conv, nullptr, c->stream)) != cudaSuccess)
+      return e;                                                                                 // Phase 1
+    if ((e = launch_freeze(ph.dev, ph.sp, c->stream)) != cudaSuccess) return e;                // Phase 2
+    if ((e = launch_dedup(ph.dev, ph.sp, c->stream)) != cudaSuccess) return e;                 // Phase 3
+    if (!last && (e = enqueue_explore(ph, c->stream)) != cudaSuccess) return e;                // Phases 4-6
+    if ((e = launch_cycle_end(ph.dev, c->stream)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+chisao_status check_prob(chisao_ctx* c, int32_t prob) {
+  if (!c) return CHISAO_ERR_ARG;
+  if (prob < 0 || prob >= (int32_t)c->probs.size()) return fail(c, CHISAO_ERR_ARG, "problem index out of range");
+  return CHISAO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void chisao_default_params(chisao_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->n_osc = 3;
+  p->n_conv = 0;
+  p->n_anti = 5;
+  p->n_cloud = 3;
+  p->M = 8;
+  p->m = 10;
+  p->T_ls = 20;
+  p->grad_mode = CHISAO_GRAD_FD64;
+  p->eps_grad = 1e-6;
+  p->eps_dup = 1e-3;
+  p->delta = 0.1;
+  p->mu = 0.9;
+  p->alpha = 0.0;
+  p->sigma = 0.0;
+  p->c_sigma = 0.1;
+  p->alpha_scale = 0.1;
+  p->h = 1e-5;
+  p->h_rel = std::pow(2.0, -23.0 / 3.0);
+  p->c1 = 1e-4;
+  p->curv_eps = 1e-10;
+  p->seed = 0;
+  p->rm_min_unfrozen = 5;
+  p->gr_patience = 2;
+  p->use_graph = 1;
+}
+
+chisao_status chisao_arena_bytes(const chisao_problem* probs, int32_t n_probs, const chisao_params* params,
+                                 size_t* bytes) {
+  std::string why;
+  if (!probs || n_probs < 1 || n_probs > 65536 || !bytes) return CHISAO_ERR_ARG;
+  if (validate_params(params, why) != CHISAO_OK) return CHISAO_ERR_ARG;
+  Bump b;
+  for (int q = 0; q < n_probs; ++q) {
+    if (validate_problem(&probs[q], why) != CHISAO_OK) return CHISAO_ERR_ARG;
+    ProbHost ph;
+    layout_problem(b, probs[q], ph);
+  }
+  *bytes = (b.off + ALIGN - 1) / ALIGN * ALIGN;
+  return CHISAO_OK;
+}
+
+chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const chisao_params* params, void* arena,
+                            size_t arena_bytes, void* cuda_stream, chisao_ctx** out) {
+  if (!out) return CHISAO_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (!probs || n_probs < 1 || n_probs > 65536) return CHISAO_ERR_ARG;
+  if (validate_params(params, why) != CHISAO_OK) {
+    fprintf(stderr, "chisao_create: %s\n", why.c_str());
+    return CHISAO_ERR_ARG;
+  }
+  for (int q = 0; q < n_probs; ++q)
+    if (validate_problem(&probs[q], why) != CHISAO_OK) {
+      fprintf(stderr, "chisao_create: problem %d: %s\n", q, why.c_str());
+      return CHISAO_ERR_ARG;
+    }
+  size_t need = 0;
+  chisao_arena_bytes(probs, n_probs, params, &need);
+  if (arena && (arena_bytes < need || (reinterpret_cast<uintptr_t>(arena) % ALIGN) != 0)) return CHISAO_ERR_OOM;
+
+  chisao_ctx* c = new chisao_ctx();
+  c->params = *params;
+  if (prepare_kernel_attributes() != cudaSuccess) {
+    delete c;
+    return CHISAO_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return CHISAO_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (arena) {
+    c->arena = reinterpret_cast<char*>(arena);
+    c->arena_bytes = arena_bytes;
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      chisao_destroy(c);
+      return CHISAO_ERR_OOM;
+    }
+    c->arena = reinterpret_cast<char*>(p);
+    c->arena_bytes = need;
+    c->own_arena = true;
+  }
+  Bump b;
+  b.base = c->arena;
+  c->probs.resize(n_probs);
+  std::vector<double> a0, a1, a2, a3;
+  std::vector<float> f0, f1, f2, f3, box;
+  auto to32 = [](const std::vector<double>& v, std::vector<float>& o) {
+    o.resize(v.size());
+    for (size_t t = 0; t < v.size(); ++t) o[t] = (float)v[t];
+  };
+  chisao_status st = CHISAO_OK;
+  for (int q = 0; q < n_probs && st == CHISAO_OK; ++q) {
+    const chisao_problem& pr = probs[q];
+    ProbHost& ph = c->probs[q];
+    ph.d = pr.d;
+    ph.dp = pad_dim(pr.d);
+    ph.n = pr.n;
+    ph.kind = pr.objective.kind;
+    ph.K = pr.objective.n_comp;
+    layout_problem(b, pr, ph);
+    ProbDev& P = ph.dev;
+    P.d = ph.d;
+    P.dp = ph.dp;
+    P.n = (int)ph.n;
+    P.nwords = (int)((ph.n + 31) / 32);
+    P.prob_index = q;
+    P.m = params->m;
+    P.obj.kind = ph.kind;
+    P.obj.f32.K = P.obj.f64.K = (ph.kind == CHISAO_OBJ_QUADRATIC) ? 0 : ph.K;
+    P.obj.f32.d = P.obj.f64.d = ph.d;
+    P.obj.f32.dp = P.obj.f64.dp = ph.dp;
+    ph.sp = make_step_params(*params, ph.d);
+    prepare_objective(pr, ph.dp, a0, a1, a2, a3);
+    to32(a0, f0); to32(a1, f1); to32(a2, f2); to32(a3, f3);
+    auto up = [&](const void* dst, const void* src, size_t bytes) {
+      if (bytes && cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = cuda_fail(c, cudaGetLastError(), "objective upload");
+    };
+    up(P.obj.f64.p0, a0.data(), a0.size() * 8);
+    up(P.obj.f64.p1, a1.data(), a1.size() * 8);
+    if (P.obj.f64.p2) up(P.obj.f64.p2, a2.data(), a2.size() * 8);
+    if (P.obj.f64.p3) up(P.obj.f64.p3, a3.data(), a3.size() * 8);
+    up(P.obj.f32.p0, f0.data(), f0.size() * 4);
+    up(P.obj.f32.p1, f1.data(), f1.size() * 4);
+    if (P.obj.f32.p2) up(P.obj.f32.p2, f2.data(), f2.size() * 4);
+    if (P.obj.f32.p3) up(P.obj.f32.p3, f3.data(), f3.size() * 4);
+    box.assign(ph.dp, 0.f);
+    for (int j = 0; j < ph.d; ++j) box[j] = (float)pr.lo[j];
+    up(P.lo, box.data(), box.size() * 4);
+    for (int j = 0; j < ph.d; ++j) box[j] = (float)pr.hi[j];
+    up(P.hi, box.data(), box.size() * 4);
+  }
+  if (st != CHISAO_OK) {
+    chisao_destroy(c);
+    return st;
+  }
+  for (int q = 0; q < n_probs; ++q) {
+    if ((st = chisao_load_population(c, q, probs[q].x0)) != CHISAO_OK) {
+      fprintf(stderr, "chisao_create: %s\n", c->err.c_str());
+      chisao_destroy(c);
+      return st;
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    chisao_destroy(c);
+    return CHISAO_ERR_CUDA;
+  }
+  *out = c;
+  return CHISAO_OK;
+}
+
+chisao_status chisao_load_population(chisao_ctx* c, int32_t prob, const float* x_host) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (!x_host) return fail(c, CHISAO_ERR_ARG, "x_host is NULL");
+  ProbHost& ph = c->probs[prob];
+  ProbDev& P = ph.dev;
+  const size_t n = (size_t)ph.n;
+  CK(cudaMemsetAsync(P.x, 0, n * ph.dp * sizeof(float), c->stream));
+  CK(cudaMemcpy2DAsync(P.x, ph.dp * sizeof(float), x_host, ph.d * sizeof(float), ph.d * sizeof(float), n,
+                       cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(P.g, 0, n * ph.dp * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(P.f, 0, n * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(P.hlen, 0, n * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(P.stuck, 0, P.nwords * sizeof(uint32_t), c->stream));
+  CK(cudaMemsetAsync(P.removed, 0, P.nwords * sizeof(uint32_t), c->stream));
+  k_reset_problem<<<1, 32, 0, c->stream>>>(P);
+  CK(cudaGetLastError());
+  c->cycles_done = 0;
+  return CHISAO_OK;
+}
+
+chisao_status chisao_step(chisao_ctx* c) {
+  if (!c) return CHISAO_ERR_ARG;
+  if (c->cycles_done >= c->params.n_osc) return fail(c, CHISAO_ERR_STATE, "all n_osc cycles have run");
+  const bool last = c->cycles_done + 1 >= c->params.n_osc;
+  if (c->params.use_graph) {
+    cudaGraphExec_t& ge = last ? c->g_last : c->g_mid;
+    if (!ge) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t e = enqueue_cycle(c, last);
+      const cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(c, e, "cycle capture");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+      const cudaError_t e3 = cudaGraphInstantiate(&ge, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) {
+        ge = nullptr;
+        return cuda_fail(c, e3, "cudaGraphInstantiate");
+      }
+    }
+    CK(cudaGraphLaunch(ge, c->stream));
+  } else {
+    const cudaError_t e = enqueue_cycle(c, last);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cycle launch");
+  }
+  c->cycles_done += 1;
+  return CHISAO_OK;
+}
+
+chisao_status chisao_modes(chisao_ctx* c, int32_t prob, float* x_out, float* f_out, int64_t cap, int64_t* count) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (!count || cap < 0 || (cap > 0 && !x_out)) return fail(c, CHISAO_ERR_ARG, "bad output arguments");
+  ProbHost& ph = c->probs[prob];
+  Counters cnt;
+  CK(cudaMemcpyAsync(&cnt, ph.dev.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *count = cnt.n_surv;
+  if (cnt.n_surv > cap) return fail(c, CHISAO_ERR_CAPACITY, "output capacity below the number of modes");
+  if (cnt.n_surv == 0) return CHISAO_OK;
+  CK(launch_gather_modes(ph.dev, ph.gather_x, ph.gather_f, c->stream));
+  CK(cudaMemcpyAsync(x_out, ph.gather_x, sizeof(float) * cnt.n_surv * ph.d, cudaMemcpyDeviceToHost, c->stream));
+  if (f_out) CK(cudaMemcpyAsync(f_out, ph.gather_f, sizeof(float) * cnt.n_surv, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return CHISAO_OK;
+}
+
+chisao_status chisao_get_counters(chisao_ctx* c, int32_t prob, chisao_counters* out) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (!out) return fail(c, CHISAO_ERR_ARG, "out is NULL");
+  Counters cnt;
+  CK(cudaMemcpyAsync(&cnt, c->probs[prob].dev.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof(*out));
+  out->evals = cnt.evals;
+  out->grads = cnt.grads;
+  out->ls_trials = cnt.ls_trials;
+  out->ls_fail = cnt.ls_fail;
+  out->cycles = cnt.cycle;
+  out->n_stuck = cnt.n_stuck;
+  out->k_lost = cnt.n_removed;
+  out->n_unfrozen = cnt.n_unfrozen;
+  out->last_reseed = cnt.reseed_mode;
+  out->gr_enabled = cnt.gr_enabled;
+  out->f_max = cnt.fmax;
+  out->sigma = cnt.sigma;
+  out->alpha_hlc = cnt.alpha_hlc;
+  out->alpha_anti = cnt.alpha_anti;
+  return CHISAO_OK;
+}
+
+chisao_status chisao_eval(chisao_ctx* c, int32_t prob, const float* x_dev, int64_t n, float* f_dev, float* g_dev,
+                          int32_t grad_mode) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (n < 0 || n > MAX_N || (n > 0 && !x_dev)) return fail(c, CHISAO_ERR_ARG, "bad points");
+  if (grad_mode < 0 || grad_mode > 2) return fail(c, CHISAO_ERR_ARG, "unknown grad_mode");
+  if (n == 0 || (!f_dev && !g_dev)) return CHISAO_OK;
+  EvalArgs ea{x_dev, (int)n, f_dev, g_dev};
+  CK(launch_objective(OKID_EVAL, c->probs[prob], grad_mode, 0, &ea, c->stream));
+  return CHISAO_OK;
+}
+
+const char* chisao_last_error(const chisao_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void chisao_destroy(chisao_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->g_mid) cudaGraphExecDestroy(c->g_mid);
+  if (c->g_last) cudaGraphExecDestroy(c->g_last);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+chisao_status chisao_layout(chisao_ctx* c, int32_t prob, int32_t* dp, int32_t* m_max) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (dp) *dp = c->probs[prob].dp;
+  if (m_max) *m_max = MMAX;
+  return CHISAO_OK;
+}
+
+static chisao_status field_ptr(chisao_ctx* c, int32_t prob, int32_t field, void** ptr, size_t* bytes) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  ProbHost& ph = c->probs[prob];
+  ProbDev& P = ph.dev;
+  const size_t n = (size_t)ph.n;
+  switch (field) {
+    case CHISAO_FIELD_X: *ptr = P.x; *bytes = n * ph.dp * 4; break;
+    case CHISAO_FIELD_G: *ptr = P.g; *bytes = n * ph.dp * 4; break;
+    case CHISAO_FIELD_F: *ptr = P.f; *bytes = n * 4; break;
+    case CHISAO_FIELD_HS: *ptr = P.hs; *bytes = n * MMAX * ph.dp * 4; break;
+    case CHISAO_FIELD_HY: *ptr = P.hy; *bytes = n * MMAX * ph.dp * 4; break;
+    case CHISAO_FIELD_HRHO: *ptr = P.hrho; *bytes = n * MMAX * 8; break;
+    case CHISAO_FIELD_HLEN: *ptr = P.hlen; *bytes = n * 4; break;
+    case CHISAO_FIELD_STUCK: *ptr = P.stuck; *bytes = (size_t)P.nwords * 4; break;
+    case CHISAO_FIELD_REMOVED: *ptr = P.removed; *bytes = (size_t)P.nwords * 4; break;
+    default: return fail(c, CHISAO_ERR_ARG, "unknown field");
+  }
+  return CHISAO_OK;
+}
+
+chisao_status chisao_state_get(chisao_ctx* c, int32_t prob, int32_t field, void* host, size_t bytes) {
+  void* p;
+  size_t want;
+  chisao_status s = field_ptr(c, prob, field, &p, &want);
+  if (s != CHISAO_OK) return s;
+  if (!host || bytes != want) return fail(c, CHISAO_ERR_ARG, "state_get: size mismatch");
+  CK(cudaMemcpyAsync(host, p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return CHISAO_OK;
+}
+
+chisao_status chisao_state_set(chisao_ctx* c, int32_t prob, int32_t field, const void* host, size_t bytes) {
+  void* p;
+  size_t want;
+  chisao_status s = field_ptr(c, prob, field, &p, &want);
+  if (s != CHISAO_OK) return s;
+  if (!host || bytes != want) return fail(c, CHISAO_ERR_ARG, "state_set: size mismatch");
+  CK(cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return CHISAO_OK;
+}
+
+chisao_status chisao_run_phase(chisao_ctx* c, int32_t prob, int32_t phase, int32_t arg) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  const ProbHost& ph = c->probs[prob];
+  cudaStream_t st = c->stream;
+  switch (phase) {
+    case CHISAO_PHASE_LBFGS:
+      CK(launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, arg, nullptr, st));
+      break;
+    case CHISAO_PHASE_FREEZE:
+      CK(launch_cycle_begin(ph.dev, st));
+      CK(launch_freeze(ph.dev, ph.sp, st));
+      break;
+    case CHISAO_PHASE_DEDUP:
+      CK(launch_compact_stuck(ph.dev, st));
+      CK(launch_dedup(ph.dev, ph.sp, st));
+      break;
+    case CHISAO_PHASE_LISTS:
+      CK(launch_lists(ph.dev, st));
+      break;
+    case CHISAO_PHASE_RESEED:
+      CK(launch_set_cycle(ph.dev, arg - 1, st));
+      CK(launch_reseed(ph.dev, ph.sp, st));
+      break;
+    case CHISAO_PHASE_HLC:
+      CK(launch_set_cycle(ph.dev, arg - 1, st));
+      CK(launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st));
+      CK(launch_finalize_scales(ph.dev, ph.sp, 0, st));
+      CK(launch_objective(OKID_HLC, ph, ph.sp.grad_mode, 0, nullptr, st));
+      break;
+    case CHISAO_PHASE_ANTI:
+      CK(launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st));
+      CK(launch_finalize_scales(ph.dev, ph.sp, 1, st));
+      CK(launch_objective(OKID_ANTI, ph, ph.sp.grad_mode, 0, nullptr, st));
+      break;
+    case CHISAO_PHASE_DIRECTION:
+      CK(launch_objective(OKID_DIRECTION, ph, ph.sp.grad_mode, 0, nullptr, st));
+      break;
+    default:
+      return fail(c, CHISAO_ERR_ARG, "unknown phase");
+  }
+  return CHISAO_OK;
+}
+
+chisao_status chisao_set_gr_state(chisao_ctx* c, int32_t prob, int32_t enabled, int32_t noprog, int32_t prev_surv) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  Counters cnt;
+  Counters* dptr = c->probs[prob].dev.cnt;
+  CK(cudaMemcpy(&cnt, dptr, sizeof(cnt), cudaMemcpyDeviceToHost));
+  cnt.gr_enabled = enabled;
+  cnt.gr_noprog = noprog;
+  cnt.gr_prev_surv = prev_surv;
+  CK(cudaMemcpy(dptr, &cnt, sizeof(cnt), cudaMemcpyHostToDevice));
+  return CHISAO_OK;
+}
+
+}  // extern "C"

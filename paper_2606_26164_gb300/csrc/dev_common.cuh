@@ -1,0 +1,263 @@
+// Device-side building blocks shared by every kernel of the ChiSao step.
+//
+// Layout (sample-major SoA, one problem):
+//   x, g      float [n][dp]          dp = padded dimension (power of two >= 4)
+//   f         float [n]
+//   hs, hy    float [n][MMAX][dp]    L-BFGS pairs, slot 0 = newest
+//   hrho      double [n][MMAX]       1 / s^T y (FP64 curvature product)
+//   hlen      int [n], hgam float [n]
+//   stuck, removed   uint32 bit masks [ceil(n/32)]
+// Padded coordinates are zero in x, g, the history and every objective
+// parameter, so they never contribute to a dot product or a norm.
+//
+// A sample is processed by a "group" of LPS = dp/2 consecutive lanes of one
+// warp; lane l of the group owns coordinates 2l and 2l+1 (a float2).  Group
+// reductions are xor-butterflies restricted to the group's lane mask, so every
+// lane of the group ends with the bitwise-identical result and all control
+// decisions stay group-uniform.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace chisao {
+
+constexpr int MMAX = 10;                 // register-resident L-BFGS memory
+constexpr int GRAD_FD64 = 0, GRAD_FD32 = 1, GRAD_ADJOINT = 2;
+constexpr int OBJ_MIXTURE_DIAG = 1, OBJ_MIXTURE_FULL = 2, OBJ_QUADRATIC = 3;
+constexpr int RESEED_NONE = 0, RESEED_RM = 1, RESEED_GR = 2, RESEED_UNIFORM = 3;
+// Philox stream tags (same layout as the paper-side definition of the method's
+// random draws; see the stream description in the library documentation).
+constexpr unsigned TAG_RM = 1, TAG_RM_DIR = 2, TAG_GR_MAT = 3, TAG_GR_T = 4,
+                   TAG_UNIFORM = 5, TAG_HLC = 6, TAG_NOISE = 7;
+
+// Objective parameters in one precision.  Interpretation by kind:
+//   MIXTURE_DIAG: p0 = mu [K][dp], p1 = 1/sigma^2 [K][dp], p2 = c [K]
+//   MIXTURE_FULL: p0 = mu [K][dp], p1 = L^-1 [K][dp][dp] row-major,
+//                 p3 = (L^-1)^T [K][dp][dp], p2 = c [K]
+//   QUADRATIC:    p0 = center [dp], p1 = A = Q^T diag(lam) Q [dp][dp]
+// with c_k = log w_k - log|L_k| - (d/2) log(2 pi).
+template <typename T>
+struct ObjParams {
+  int K, d, dp;
+  const T* p0;
+  const T* p1;
+  const T* p2;
+  const T* p3;
+};
+
+struct ObjDev {
+  int kind;
+  ObjParams<float> f32;
+  ObjParams<double> f64;
+};
+
+// Device counters of one problem (one 256-byte block).
+struct Counters {
+  unsigned int fmax_key;        // order-preserving key of max f (0: no finite f)
+  int n_stuck0;                 // stuck after Phase 2
+  int n_removed;                // K_lost of the last Phase 3
+  int n_stuck;                  // stuck after Phase 3
+  int n_unfrozen;               // unfrozen when Phase 4 chose its strategy
+  int n_surv;                   // survivors (stuck after Phase 3)
+  int reseed_mode;
+  int gr_enabled;
+  int gr_noprog;
+  int gr_prev_surv;
+  int cycle;                    // completed cycles
+  int n_free;                   // free slots (== n_removed)
+  unsigned long long evals, grads, ls_trials, ls_fail;
+  float fmax;
+  float sigma;                  // scales of the last Phase 5 / 6 start
+  float alpha_hlc;
+  float alpha_anti;
+  float sc_sigma;               // scales computed by the last finalize
+  float sc_alpha;
+  int sc_count;
+  int err;                      // device-side error flag (0 ok)
+};
+
+struct ProbDev {
+  int d, dp, n, nwords, prob_index, m;
+  float* x;
+  float* g;
+  float* f;
+  float* hs;
+  float* hy;
+  double* hrho;
+  int* hlen;
+  float* hgam;
+  uint32_t* stuck;
+  uint32_t* removed;
+  int* l_stuck;                 // stuck samples, index order
+  int* l_free;                  // removed samples (free slots), index order
+  int* l_unf;                   // unfrozen samples, index order
+  int* l_surv;                  // survivors, index order
+  int* l_rank;                  // survivors ranked by (f desc, index asc)
+  const float* lo;              // [dp] box, padded with 0
+  const float* hi;
+  Counters* cnt;
+  double* partials;             // [max_part_blocks][2 dp + 2]
+  int max_part_blocks;
+  double* grq;                  // Golden Rooster Q [d][d], column-major
+  ObjDev obj;
+};
+
+struct StepParams {
+  int n_conv, n_anti, n_cloud, M, m, T_ls, grad_mode, rm_min, gr_patience;
+  float eps_grad, eps_dup, log_delta, mu, alpha_fixed, sigma_fixed, c_sigma, alpha_scale;
+  double h, h_rel, c1, curv_eps;
+  unsigned seed_lo, seed_hi;
+};
+
+enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5 };
+
+// Caller points for plain objective evaluation.
+struct EvalArgs {
+  const float* x;   // [n][d] device
+  int n;
+  float* f;         // [n] device or null
+  float* g;         // [n][d] device or null
+};
+
+// ------------------------------------------------------------------ groups
+template <int LPS>
+struct Grp {
+  unsigned mask;
+  int l;
+  __device__ __forceinline__ Grp() {
+    const int lane = threadIdx.x & 31;
+    l = lane & (LPS - 1);
+    mask = (LPS == 32) ? 0xffffffffu : (((1u << LPS) - 1u) << (lane & ~(LPS - 1)));
+  }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v) const {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, LPS);
+    return v;
+  }
+  __device__ __forceinline__ float maxf(float v) const {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, LPS));
+    return v;
+  }
+  template <typename T>
+  __device__ __forceinline__ T bcast(T v, int src) const {
+    return __shfl_sync(mask, v, src, LPS);
+  }
+  __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type ldg2(const T* p) {
+  return __ldg(reinterpret_cast<const typename Vec2<T>::type*>(p));
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of the two multiply-hi/lo
+// S-boxes with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 rng_words(const StepParams& S, unsigned c0, unsigned c1, unsigned tag,
+                                           unsigned cycle, unsigned step, unsigned prob, unsigned k) {
+  const uint4 c = make_uint4(c0, c1, (tag << 24) | ((cycle & 0xffffu) << 8) | (step & 0xffu),
+                             ((prob & 0xffffu) << 16) | (k & 0xffffu));
+  return philox4x32_10(c, make_uint2(S.seed_lo, S.seed_hi));
+}
+
+// u = (2 (w >> 9) + 1) 2^-24: exact in binary32, strictly inside (0, 1).
+__device__ __forceinline__ float u01f(unsigned w) {
+  return (float)(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+
+// Box-Muller pairs (w0, w1) and (w2, w3) -> four standard normals.
+__device__ __forceinline__ float4 normals4f(uint4 w) {
+  float s0, c0, s1, c1;
+  const float r0 = sqrtf(-2.0f * logf(u01f(w.x)));
+  const float r1 = sqrtf(-2.0f * logf(u01f(w.z)));
+  sincospif(2.0f * u01f(w.y), &s0, &c0);
+  sincospif(2.0f * u01f(w.w), &s1, &c1);
+  return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+__device__ __forceinline__ void normals4d(uint4 w, double out[4]) {
+  double s0, c0, s1, c1;
+  const double r0 = sqrt(-2.0 * log((double)u01f(w.x)));
+  const double r1 = sqrt(-2.0 * log((double)u01f(w.z)));
+  sincospi(2.0 * (double)u01f(w.y), &s0, &c0);
+  sincospi(2.0 * (double)u01f(w.w), &s1, &c1);
+  out[0] = r0 * c0;
+  out[1] = r0 * s0;
+  out[2] = r1 * c1;
+  out[3] = r1 * s1;
+}
+
+// The two normals of coordinates 2l, 2l+1 (block (2l)/4, positions (2l)%4, +1).
+__device__ __forceinline__ float2 normals_pair(const StepParams& S, unsigned row, int l, unsigned tag,
+                                               unsigned cycle, unsigned step, unsigned prob, unsigned k) {
+  const float4 z = normals4f(rng_words(S, row, (unsigned)(l >> 1), tag, cycle, step, prob, k));
+  return (l & 1) ? make_float2(z.z, z.w) : make_float2(z.x, z.y);
+}
+
+// ------------------------------------------------------------------ misc
+// order-preserving map float -> uint32 (for atomicMax over floats)
+__device__ __forceinline__ unsigned fkey(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t* bits, int i) {
+  return (bits[i >> 5] >> (i & 31)) & 1u;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// Block-wide sum of 64-bit counters into device memory: one atomic per block.
+template <int NT>
+__device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long* dst) {
+  __shared__ unsigned long long red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    if (t) atomicAdd(dst, t);
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ void block_max_key(unsigned v, unsigned* dst) {
+  __shared__ unsigned red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < NT / 32; ++w) t = max(t, red[w]);
+    if (t) atomicMax(dst, t);
+  }
+  __syncthreads();
+}
+
+}  // namespace chisao

@@ -1,0 +1,13 @@
+// Instantiation of the objective-dependent kernels for one objective kind
+// (one translation unit per kind keeps the parallel build short).
+#include "host.h"
+#include "obj_kernels.cuh"
+
+namespace chisao {
+
+cudaError_t launch_obj_mixdiag(int which, int gm, const ProbDev& P, const StepParams& S, int arg, const EvalArgs* ea,
+                         cudaStream_t st) {
+  return launch_obj<OBJ_MIXTURE_DIAG>(which, gm, P, S, arg, ea, st);
+}
+
+}  // namespace chisao

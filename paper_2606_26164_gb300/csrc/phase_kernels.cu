@@ -1,0 +1,526 @@
+// Objective-independent kernels of one oscillation cycle: f_max and the stick
+// test (Phase 2, Eq. 3), ordered compaction of the sample sets, L-infinity
+// deduplication (Phase 3, Eq. 4), the reseeding strategies (Phase 4,
+// Sec. 3.2.4) with the Golden Rooster's FP64 Householder QR, and the scale
+// estimates' final reduction (Phases 5/6).
+#include "host.h"
+#include "dev_common.cuh"
+
+namespace chisao {
+
+constexpr int NT_LIN = 256;       // threads of the elementwise kernels
+constexpr int NT_ONE = 1024;      // threads of the single-block kernels
+
+// ------------------------------------------------------------ cycle bookkeeping
+__global__ void k_cycle_begin(ProbDev P) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < P.nwords; w += gridDim.x * blockDim.x) {
+    P.stuck[w] = 0u;                 // Phase 1: release all
+    P.removed[w] = 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.cnt->fmax_key = 0u;
+    P.cnt->n_stuck0 = 0;
+    P.cnt->reseed_mode = RESEED_NONE;
+  }
+}
+
+__global__ void k_cycle_end(ProbDev P) {
+  if (threadIdx.x == 0) P.cnt->cycle += 1;
+}
+
+__global__ void k_set_cycle(ProbDev P, int completed) {
+  if (threadIdx.x == 0) P.cnt->cycle = completed;
+}
+
+// ------------------------------------------------------------ Phase 2
+// f_max over the finite f (max is order-independent, so atomics are exact).
+__global__ void __launch_bounds__(NT_LIN) k_fmax(ProbDev P) {
+  unsigned key = 0u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const float v = P.f[i];
+    if (isfinite(v)) key = max(key, fkey(v));
+  }
+  block_max_key<NT_LIN>(key, &P.cnt->fmax_key);
+}
+
+// stuck_i = (|g_i|_inf < eps_grad) and (f_i >= fl(f_max + log delta)), binary32
+// compares; one warp ballot per 32 samples writes one mask word.
+__global__ void __launch_bounds__(NT_LIN) k_freeze(ProbDev P, StepParams S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned key = P.cnt->fmax_key;
+  const float fmax = key ? fkey_inv(key) : -CUDART_INF_F;
+  const float thr = fmax + S.log_delta;
+  bool st = false;
+  if (i < P.n) {
+    float gm = 0.f;
+    bool bad = false;
+    const float4* row = reinterpret_cast<const float4*>(P.g + (size_t)i * P.dp);
+    for (int q = 0; q < P.dp / 4; ++q) {
+      const float4 v = row[q];
+      const float a = fabsf(v.x), b = fabsf(v.y), c = fabsf(v.z), e = fabsf(v.w);
+      bad |= (a != a) | (b != b) | (c != c) | (e != e);
+      gm = fmaxf(gm, fmaxf(fmaxf(a, b), fmaxf(c, e)));
+    }
+    st = !bad && (gm < S.eps_grad) && (P.f[i] >= thr);
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, st);
+  if ((threadIdx.x & 31) == 0 && (i >> 5) < P.nwords) {
+    P.stuck[i >> 5] = b;
+    if (b) atomicAdd(&P.cnt->n_stuck0, __popc(b));
+  }
+  if (i == 0) P.cnt->fmax = fmax;
+}
+
+// ------------------------------------------------------------ ordered compaction
+// One block; thread t owns a contiguous run of mask words; a block scan of the
+// per-thread counts gives each run its output offset, so the list comes out
+// in increasing sample index.
+template <class WordFn>
+__device__ int block_compact(int nwords, WordFn word_of, int* out) {
+  __shared__ int scan[NT_ONE];
+  const int t = threadIdx.x;
+  const int per = (nwords + NT_ONE - 1) / NT_ONE;
+  const int w0 = min(nwords, t * per), w1 = min(nwords, w0 + per);
+  int c = 0;
+  for (int w = w0; w < w1; ++w) c += __popc(word_of(w));
+  scan[t] = c;
+  __syncthreads();
+  for (int off = 1; off < NT_ONE; off <<= 1) {
+    const int v = t >= off ? scan[t - off] : 0;
+    __syncthreads();
+    scan[t] += v;
+    __syncthreads();
+  }
+  int base = scan[t] - c;
+  const int total = scan[NT_ONE - 1];
+  for (int w = w0; w < w1; ++w) {
+    unsigned m = word_of(w);
+    while (m) {
+      const int b = __ffs(m) - 1;
+      out[base++] = w * 32 + b;
+      m &= m - 1u;
+    }
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ unsigned valid_mask(const ProbDev& P, int w) {
+  const int rem = P.n - w * 32;
+  return rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+}
+
+__global__ void __launch_bounds__(NT_ONE) k_compact_stuck(ProbDev P) {
+  const int S = block_compact(P.nwords, [&](int w) { return P.stuck[w]; }, P.l_stuck);
+  if (threadIdx.x == 0) P.cnt->n_stuck0 = S;
+}
+
+// After deduplication: stuck &= ~removed, then the free-slot list (removed),
+// the unfrozen list (neither stuck nor removed) and the survivor list.
+__global__ void __launch_bounds__(NT_ONE) k_compact_dedup(ProbDev P) {
+  for (int w = threadIdx.x; w < P.nwords; w += NT_ONE) P.stuck[w] &= ~P.removed[w];
+  __syncthreads();
+  const int K = block_compact(P.nwords, [&](int w) { return P.removed[w]; }, P.l_free);
+  const int U = block_compact(P.nwords, [&](int w) { return ~(P.stuck[w] | P.removed[w]) & valid_mask(P, w); },
+                              P.l_unf);
+  const int S = block_compact(P.nwords, [&](int w) { return P.stuck[w]; }, P.l_surv);
+  if (threadIdx.x == 0) {
+    Counters* c = P.cnt;
+    c->n_removed = K;
+    c->n_free = K;
+    c->n_unfrozen = U;
+    c->n_surv = S;
+    c->n_stuck = S;
+  }
+}
+
+// ------------------------------------------------------------ Phase 3
+// For every stuck x_j: removed iff some other stuck x_i ranks above it
+// (f desc, index asc) and max_k |x_ik - x_jk| < eps_dup (binary32).  The scan
+// over i stops at the first such neighbour.
+template <int DP>
+__global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
+  constexpr int LPS = DP / 2;
+  const Grp<LPS> g;
+  const int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int Sn = P.cnt->n_stuck0;
+  if (jj >= Sn) return;
+  const int j = P.l_stuck[jj];
+  const int c0 = 2 * g.l;
+  const float2 xj = *reinterpret_cast<const float2*>(P.x + (size_t)j * DP + c0);
+  const float fj = P.f[j];
+  const float eps = S.eps_dup;
+  bool rem = false;
+  for (int ii = 0; ii < Sn; ++ii) {
+    const int i = P.l_stuck[ii];
+    if (i == j) continue;
+    const float fi = P.f[i];
+    if (!(fi > fj || (fi == fj && i < j))) continue;
+    const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
+    if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) {
+      rem = true;
+      break;
+    }
+  }
+  if (rem && g.l == 0) atomicOr(&P.removed[j >> 5], 1u << (j & 31));
+}
+
+// ------------------------------------------------------------ Phase 4
+// Strategy choice and Golden Rooster bookkeeping (single thread):
+//   K_lost = 0 -> none; >= rm_min unfrozen -> Repulse Monkey; else Golden
+//   Rooster while enabled and some survivor exists; it disables itself after
+//   gr_patience successive generations whose survivor count did not grow;
+//   otherwise a uniform redraw.
+__global__ void k_reseed_decide(ProbDev P, StepParams S) {
+  if (threadIdx.x != 0) return;
+  Counters* c = P.cnt;
+  const int K = c->n_free, U = c->n_unfrozen, Sv = c->n_surv;
+  int mode = RESEED_NONE;
+  if (K > 0) {
+    mode = RESEED_UNIFORM;
+    if (U >= S.rm_min) {
+      mode = RESEED_RM;
+    } else if (c->gr_enabled && Sv > 0) {
+      if (c->gr_prev_surv >= 0) c->gr_noprog = (Sv > c->gr_prev_surv) ? 0 : c->gr_noprog + 1;
+      if (c->gr_noprog >= S.gr_patience) {
+        c->gr_enabled = 0;
+      } else {
+        mode = RESEED_GR;
+        c->gr_prev_surv = Sv;
+      }
+    }
+  }
+  c->reseed_mode = mode;
+}
+
+// Survivors ranked by (f desc, index asc): rank_j = #{i : i above j}.
+__global__ void __launch_bounds__(NT_LIN) k_gr_rank(ProbDev P) {
+  if (P.cnt->reseed_mode != RESEED_GR) return;
+  const int Sv = P.cnt->n_surv;
+  const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jj >= Sv) return;
+  const int j = P.l_surv[jj];
+  const float fj = P.f[j];
+  int r = 0;
+  for (int ii = 0; ii < Sv; ++ii) {
+    const int i = P.l_surv[ii];
+    const float fi = P.f[i];
+    r += (fi > fj || (fi == fj && i < j)) ? 1 : 0;
+  }
+  P.l_rank[r] = j;
+}
+
+// One Gaussian d x d matrix per Golden Rooster generation (FP64 Box-Muller on
+// the GR stream, row i / column block b), its Householder QR (Golub & Van
+// Loan, Algorithm 5.2.1) with Q accumulated explicitly, columns of Q flipped
+// so that diag(R) > 0.  Q is written column-major to grq.
+__global__ void __launch_bounds__(NT_LIN) k_gr_qr(ProbDev P, StepParams S) {
+  if (P.cnt->reseed_mode != RESEED_GR) return;
+  extern __shared__ double sm[];
+  const int d = P.d;
+  double* A = sm;              // [d][d] row-major
+  double* Q = sm + d * d;      // [d][d] row-major
+  double* v = Q + d * d;       // [d]
+  double* w = v + d;           // [d]
+  __shared__ double red[NT_LIN / 32];
+  __shared__ double bc;
+  const unsigned cyc = (unsigned)P.cnt->cycle + 1u;
+  const int nb = (d + 3) / 4;
+  for (int t = threadIdx.x; t < d * nb; t += blockDim.x) {
+    const int i = t / nb, b = t % nb;
+    double z[4];
+    normals4d(rng_words(S, (unsigned)i, (unsigned)b, TAG_GR_MAT, cyc, 0u, (unsigned)P.prob_index, 0u), z);
+    for (int q = 0; q < 4; ++q)
+      if (4 * b + q < d) A[i * d + 4 * b + q] = z[q];
+  }
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) Q[t] = (t / d == t % d) ? 1.0 : 0.0;
+  __syncthreads();
+  auto block_sum = [&](double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int q = 0; q < NT_LIN / 32; ++q) s += red[q];
+      bc = s;
+    }
+    __syncthreads();
+    const double r = bc;
+    __syncthreads();
+    return r;
+  };
+  for (int j = 0; j + 1 < d; ++j) {
+    const int len = d - j;
+    const double xt = threadIdx.x < len ? A[(j + threadIdx.x) * d + j] : 0.0;
+    const double alpha = sqrt(block_sum(xt * xt));
+    if (alpha == 0.0) continue;
+    const double x0 = A[j * d + j];
+    double vt = xt;
+    if (threadIdx.x == 0) vt += copysign(alpha, x0);
+    const double vn = sqrt(block_sum(threadIdx.x < len ? vt * vt : 0.0));
+    if (threadIdx.x < len) v[threadIdx.x] = vt / vn;
+    __syncthreads();
+    // A[j:, :] -= 2 v (v^T A[j:, :])
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+      double s = 0.0;
+      for (int r = 0; r < len; ++r) s += v[r] * A[(j + r) * d + c];
+      w[c] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < len * d; t += blockDim.x) {
+      const int r = t / d, c = t % d;
+      A[(j + r) * d + c] -= 2.0 * v[r] * w[c];
+    }
+    __syncthreads();
+    // Q[:, j:] -= 2 (Q[:, j:] v) v^T
+    for (int r = threadIdx.x; r < d; r += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < len; ++k) s += Q[r * d + j + k] * v[k];
+      w[r] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < d * len; t += blockDim.x) {
+      const int r = t / len, k = t % len;
+      Q[r * d + j + k] -= 2.0 * w[r] * v[k];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    const int r = t / d, c = t % d;                       // Q[r][c] -> column-major
+    const double sg = A[c * d + c] < 0.0 ? -1.0 : 1.0;
+    P.grq[c * d + r] = sg * Q[r * d + c];
+  }
+}
+
+// Largest t >= 0 keeping p + t u inside the box, reduced over the group.
+template <int LPS>
+__device__ __forceinline__ float ray_exit(float p0, float p1, float u0, float u1, float lo0, float lo1, float hi0,
+                                          float hi1, bool v0, bool v1, const Grp<LPS>& g) {
+  float t = CUDART_INF_F;
+  if (v0 && u0 > 0.f) t = fminf(t, (hi0 - p0) / u0);
+  if (v0 && u0 < 0.f) t = fminf(t, (lo0 - p0) / u0);
+  if (v1 && u1 > 0.f) t = fminf(t, (hi1 - p1) / u1);
+  if (v1 && u1 < 0.f) t = fminf(t, (lo1 - p1) / u1);
+#pragma unroll
+  for (int o = LPS / 2; o > 0; o >>= 1) t = fminf(t, __shfl_xor_sync(g.mask, t, o, LPS));
+  if (!(t < CUDART_INF_F)) t = 0.f;
+  return fmaxf(t, 0.f);
+}
+
+// Fill free slot r (r-th removed sample in index order) by the chosen strategy.
+template <int DP>
+__global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
+  constexpr int LPS = DP / 2;
+  const Grp<LPS> g;
+  const int mode = P.cnt->reseed_mode;
+  const int K = P.cnt->n_free;
+  const int r = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  if (mode == RESEED_NONE || r >= K) return;
+  const int slot = P.l_free[r];
+  const int d = P.d, j0 = 2 * g.l;
+  const bool v0 = j0 < d, v1 = j0 + 1 < d;
+  const unsigned cyc = (unsigned)P.cnt->cycle + 1u, pid = (unsigned)P.prob_index;
+  const float lo0 = P.lo[j0], lo1 = P.lo[j0 + 1], hi0 = P.hi[j0], hi1 = P.hi[j0 + 1];
+  float c0 = 0.f, c1 = 0.f;
+  if (mode == RESEED_RM || mode == RESEED_GR) {
+    float u0, u1, p0, p1, uu;
+    if (mode == RESEED_RM) {
+      const uint4 w = rng_words(S, (unsigned)r, 0u, TAG_RM, cyc, 0u, pid, 0u);
+      const unsigned U = (unsigned)P.cnt->n_unfrozen;
+      const int parent = P.l_unf[(unsigned)(((unsigned long long)w.x * U) >> 32)];
+      const float2 z = normals_pair(S, (unsigned)r, g.l, TAG_RM_DIR, cyc, 0u, pid, 0u);
+      const float z0 = v0 ? z.x : 0.f, z1 = v1 ? z.y : 0.f;
+      const float nz = sqrtf(g.sum(z0 * z0 + z1 * z1));
+      u0 = z0 / nz;
+      u1 = z1 / nz;
+      const float2 pv = *reinterpret_cast<const float2*>(P.x + (size_t)parent * DP + j0);
+      p0 = pv.x;
+      p1 = pv.y;
+      uu = u01f(w.y);
+    } else {
+      const int Sv = P.cnt->n_surv;
+      const int peak = P.l_rank[r % Sv];
+      const int col = (r / Sv) % d;
+      const float sg = ((r / (Sv * d)) % 2 == 0) ? 1.f : -1.f;
+      u0 = v0 ? sg * (float)P.grq[col * d + j0] : 0.f;
+      u1 = v1 ? sg * (float)P.grq[col * d + j0 + 1] : 0.f;
+      const float2 pv = *reinterpret_cast<const float2*>(P.x + (size_t)peak * DP + j0);
+      p0 = pv.x;
+      p1 = pv.y;
+      const uint4 w = rng_words(S, (unsigned)r, 0u, TAG_GR_T, cyc, 0u, pid, 0u);
+      uu = u01f(w.x);
+    }
+    const float t = uu * ray_exit<LPS>(p0, p1, u0, u1, lo0, lo1, hi0, hi1, v0, v1, g);
+    c0 = v0 ? clampf(fmaf(t, u0, p0), lo0, hi0) : 0.f;
+    c1 = v1 ? clampf(fmaf(t, u1, p1), lo1, hi1) : 0.f;
+  } else {
+    const uint4 w = rng_words(S, (unsigned)r, (unsigned)(g.l >> 1), TAG_UNIFORM, cyc, 0u, pid, 0u);
+    const float a = u01f((g.l & 1) ? w.z : w.x), b = u01f((g.l & 1) ? w.w : w.y);
+    c0 = v0 ? fmaf(a, hi0 - lo0, lo0) : 0.f;
+    c1 = v1 ? fmaf(b, hi1 - lo1, lo1) : 0.f;
+  }
+  *reinterpret_cast<float2*>(P.x + (size_t)slot * DP + j0) = make_float2(c0, c1);
+  if (g.l == 0) P.hlen[slot] = 0;
+}
+
+// ------------------------------------------------------------ Phase 5/6 scales
+// Fixed-order sum of the per-block partials, then
+//   s = sqrt(mean_j var_j), sigma = c_sigma s, g_rms = sqrt(sum g^2 / (U d)),
+//   alpha = alpha_scale s / max(g_rms, 1e-30)   (fixed values when supplied).
+__global__ void __launch_bounds__(NT_LIN) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
+  const int W = 2 * P.dp + 2;
+  extern __shared__ double tot[];
+  for (int t = threadIdx.x; t < W; t += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < nblocks; ++b) a += P.partials[(size_t)b * W + t];
+    tot[t] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double U = tot[2 * P.dp + 1];
+    Counters* c = P.cnt;
+    if (U <= 0.0) {
+      c->sc_count = 0;
+      c->sc_sigma = 0.f;
+      c->sc_alpha = 0.f;
+      return;
+    }
+    double vs = 0.0;
+    for (int j = 0; j < P.d; ++j) {
+      const double m = tot[j] / U;
+      vs += fmax(tot[P.dp + j] / U - m * m, 0.0);
+    }
+    const double s = sqrt(vs / P.d);
+    const double grms = sqrt(tot[2 * P.dp] / (U * P.d));
+    const double sigma = S.sigma_fixed > 0.f ? (double)S.sigma_fixed : (double)S.c_sigma * s;
+    const double alpha = S.alpha_fixed > 0.f ? (double)S.alpha_fixed : (double)S.alpha_scale * s / fmax(grms, 1e-30);
+    c->sc_count = (int)U;
+    c->sc_sigma = (float)sigma;
+    c->sc_alpha = (float)alpha;
+    if (which == 0) {
+      c->sigma = (float)sigma;
+      c->alpha_hlc = (float)alpha;
+    } else {
+      c->alpha_anti = (float)alpha;
+    }
+  }
+}
+
+// ------------------------------------------------------------ modes gather
+__global__ void __launch_bounds__(NT_LIN) k_gather_modes(ProbDev P, float* xo, float* fo) {
+  const int Sv = P.cnt->n_surv;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Sv * P.d; t += gridDim.x * blockDim.x) {
+    const int r = t / P.d, j = t % P.d;
+    const int i = P.l_surv[r];
+    xo[t] = P.x[(size_t)i * P.dp + j];
+    if (j == 0) fo[r] = P.f[i];
+  }
+}
+
+// ------------------------------------------------------------ host launchers
+static unsigned lin_blocks(long long n, int nt) {
+  long long b = (n + nt - 1) / nt;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+cudaError_t launch_cycle_begin(const ProbDev& P, cudaStream_t st) {
+  k_cycle_begin<<<lin_blocks(P.nwords, NT_LIN), NT_LIN, 0, st>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t launch_cycle_end(const ProbDev& P, cudaStream_t st) {
+  k_cycle_end<<<1, 32, 0, st>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_cycle(const ProbDev& P, int completed, cudaStream_t st) {
+  k_set_cycle<<<1, 32, 0, st>>>(P, completed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_stuck(const ProbDev& P, cudaStream_t st) {
+  k_compact_stuck<<<1, NT_ONE, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lists(const ProbDev& P, cudaStream_t st) {
+  k_compact_dedup<<<1, NT_ONE, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_freeze(const ProbDev& P, const StepParams& S, cudaStream_t st) {
+  unsigned nb = lin_blocks(P.n, NT_LIN);
+  k_fmax<<<nb < 1216 ? nb : 1216, NT_LIN, 0, st>>>(P);
+  k_freeze<<<nb, NT_LIN, 0, st>>>(P, S);
+  k_compact_stuck<<<1, NT_ONE, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int DP>
+static void dedup_dp(const ProbDev& P, const StepParams& S, cudaStream_t st) {
+  const long long th = (long long)P.n * (DP / 2);
+  k_dedup_impl<DP><<<lin_blocks(th, 128), 128, 0, st>>>(P, S);
+}
+
+cudaError_t launch_dedup(const ProbDev& P, const StepParams& S, cudaStream_t st) {
+  cudaMemsetAsync(P.removed, 0, sizeof(uint32_t) * P.nwords, st);
+  switch (P.dp) {
+    case 4: dedup_dp<4>(P, S, st); break;
+    case 8: dedup_dp<8>(P, S, st); break;
+    case 16: dedup_dp<16>(P, S, st); break;
+    case 32: dedup_dp<32>(P, S, st); break;
+    case 64: dedup_dp<64>(P, S, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  k_compact_dedup<<<1, NT_ONE, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+size_t gr_qr_smem(int d) { return sizeof(double) * (2 * (size_t)d * d + 2 * (size_t)d); }
+
+cudaError_t prepare_kernel_attributes() {
+  return cudaFuncSetAttribute(k_gr_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gr_qr_smem(64));
+}
+
+template <int DP>
+static void reseed_dp(const ProbDev& P, const StepParams& S, cudaStream_t st) {
+  const long long th = (long long)P.n * (DP / 2);
+  k_reseed<DP><<<lin_blocks(th, 128), 128, 0, st>>>(P, S);
+}
+
+cudaError_t launch_reseed(const ProbDev& P, const StepParams& S, cudaStream_t st) {
+  k_reseed_decide<<<1, 32, 0, st>>>(P, S);
+  k_gr_rank<<<lin_blocks(P.n, NT_LIN), NT_LIN, 0, st>>>(P);
+  k_gr_qr<<<1, NT_LIN, gr_qr_smem(P.d), st>>>(P, S);
+  switch (P.dp) {
+    case 4: reseed_dp<4>(P, S, st); break;
+    case 8: reseed_dp<8>(P, S, st); break;
+    case 16: reseed_dp<16>(P, S, st); break;
+    case 32: reseed_dp<32>(P, S, st); break;
+    case 64: reseed_dp<64>(P, S, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int scale_blocks(const ProbDev& P) {
+  const int gpb = 256 / (P.dp / 2);
+  long long nb = (P.n + gpb - 1) / gpb;
+  if (nb > 608) nb = 608;
+  if (nb > P.max_part_blocks) nb = P.max_part_blocks;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int which, cudaStream_t st) {
+  k_finalize_scales<<<1, NT_LIN, sizeof(double) * (2 * P.dp + 2), st>>>(P, S, scale_blocks(P), which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_modes(const ProbDev& P, float* xo, float* fo, cudaStream_t st) {
+  k_gather_modes<<<lin_blocks((long long)P.n * P.d, NT_LIN) < 2048 ? lin_blocks((long long)P.n * P.d, NT_LIN) : 2048,
+                   NT_LIN, 0, st>>>(P, xo, fo);
+  return cudaGetLastError();
+}
+
+}  // namespace chisao

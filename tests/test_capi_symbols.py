@@ -1,0 +1,73 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+include/chisao.h declares (no GPU needed: only host-side calls are made)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2606_26164_gb300 import build
+from paper_2606_26164_gb300 import chisao as CH
+from paper_2606_26164_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "chisao.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chisao_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return CH.library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(CH.EXPORTS) == names
+
+
+def test_default_params_follow_table1(lib):
+    p = CH.default_params()
+    assert (p.n_osc, p.n_anti, p.n_cloud, p.m) == (3, 5, 3, 10)
+    assert (p.eps_grad, p.eps_dup, p.delta, p.mu) == (1e-6, 1e-3, 0.1, 0.9)
+    assert p.alpha == 0.0 and p.sigma == 0.0 and p.c_sigma == 0.1
+
+
+def _cproblem(pr, keep):
+    A = {k: np.ascontiguousarray(v, np.float64) for k, v in pr.objective.arrays.items()}
+    lo, hi = np.ascontiguousarray(pr.lo), np.ascontiguousarray(pr.hi)
+    x0 = np.ascontiguousarray(pr.x0)
+    keep += [A, lo, hi, x0]
+    dp = CH._dptr
+    co = CH.CObjective(kind=pr.objective.kind, n_comp=pr.objective.n_comp, weights=dp(A.get("weights")),
+                       means=dp(A.get("means")), sigmas=dp(A.get("sigmas")), chol=dp(A.get("chol")),
+                       center=dp(A.get("center")), Q=dp(A.get("Q")), lam=dp(A.get("lam")))
+    return CH.CProblem(d=pr.d, n=pr.n, lo=dp(lo), hi=dp(hi), x0=x0.ctypes.data_as(C.POINTER(C.c_float)), objective=co)
+
+
+def test_arena_bytes_and_argument_checks(lib):
+    keep = []
+    pr = I.small_mixture(5, 3, 100, seed=0)
+    probs = (CH.CProblem * 1)(_cproblem(pr, keep))
+    p = CH.default_params()
+    nb = C.c_size_t(0)
+    assert lib.chisao_arena_bytes(probs, 1, C.byref(p), C.byref(nb)) == CH.OK
+    # x, g (100 x 8 floats), histories (2 x 100 x 10 x 8 floats) dominate
+    assert nb.value >= 4 * (2 * 100 * 8 + 2 * 100 * 10 * 8)
+    bad = CH.default_params(m=11)
+    assert lib.chisao_arena_bytes(probs, 1, C.byref(bad), C.byref(nb)) == CH.ERR_ARG
+    bad = CH.default_params(delta=1.5)
+    assert lib.chisao_arena_bytes(probs, 1, C.byref(bad), C.byref(nb)) == CH.ERR_ARG
+    probs[0].d = 65
+    assert lib.chisao_arena_bytes(probs, 1, C.byref(p), C.byref(nb)) == CH.ERR_ARG
+    ctx = C.c_void_p()
+    assert lib.chisao_create(probs, 1, C.byref(p), None, 0, None, C.byref(ctx)) == CH.ERR_ARG
+    assert lib.chisao_step(None) == CH.ERR_ARG

@@ -1,0 +1,129 @@
+"""End-to-end parity of whole oscillation cycles (Algorithm 1) through the C ABI:
+recovered mode sets against the ground-truth modes of Eq. 1 (Newton from every
+mean) and against the oracle's own run, plus properties that hold at the full
+workload sizes in the launch configuration the benchmark times."""
+import numpy as np
+import pytest
+
+import gpu_util as U
+from oracle import method as M
+from oracle import modes as MD
+from oracle import objectives as OB
+from paper_2606_26164_gb300 import chisao as CH
+from paper_2606_26164_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(model, n):
+    for _ in range(n):
+        model.step()
+    return model.modes(0)
+
+
+def test_mixture4_d2_plain_method_recovers_all_modes():
+    """d=2, 4 isotropic components, N=1024, central FD at h=1e-5 (FP64
+    stencil), m=5, 50 cycles, Philox seed 0: all four modes, no spurious."""
+    prob = I.mixture4_d2()
+    P = M.Params(n_osc=50, m=5, M=8, eps_grad=1e-5, grad_mode=M.GRAD_FD64, seed=0)
+    model = U.open_ctx(prob, P)
+    fx, ff = _run(model, P.n_osc)
+    mx, mf, negH = MD.significant_modes(prob)
+    frac, worst, _ = MD.recovery(fx, mx, negH)
+    assert frac == 1.0 and worst <= 1e-3
+    assert fx.shape[0] == 4
+    with pytest.raises(CH.ChisaoError):
+        model.step()                                   # all n_osc cycles ran
+    # the oracle's run of the same configuration (first 5 cycles) returns the same modes
+    Po = M.Params(n_osc=5, m=5, M=8, eps_grad=1e-5, grad_mode=M.GRAD_FD64, seed=0)
+    (ox, of), _ = M.run(prob, Po)
+    frac_o, worst_o, _ = MD.recovery(ox, mx, negH)
+    assert frac_o == 1.0 and ox.shape[0] == 4
+    model.close()
+
+
+def test_mixture_d16_modes_are_true_modes():
+    prob = I.mixture32_d16(n=4096)
+    P = M.Params(n_osc=6, m=10, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=1)
+    model = U.open_ctx(prob, P)
+    fx, ff = _run(model, P.n_osc)
+    mx, mf, negH = MD.significant_modes(prob)
+    frac, worst, best = MD.recovery(fx, mx, negH)
+    # every returned point is one of the significant modes (no spurious modes)
+    for x in fx:
+        e = min(MD.mahalanobis(x[None], m, H)[0] for m, H in zip(mx, negH))
+        assert e <= 1e-3
+    assert frac > 0
+    # the oracle on the same configuration recovers a comparable fraction
+    (ox, of), _ = M.run(I.mixture32_d16(n=4096), P)
+    frac_o, _, _ = MD.recovery(ox, mx, negH)
+    assert abs(frac - frac_o) <= 0.5
+    model.close()
+
+
+def test_quadratic_proposition1_with_sufficient_iterations():
+    """Proposition 1 / Remark 1 on the d=64 rotated quadratic (Lambda 1..1e4):
+    with enough L-BFGS steps one cycle sticks samples at c and dedup leaves one."""
+    prob = I.quadratic_d64(n=2048)
+    P = M.Params(n_osc=1, n_conv=2500, m=10, eps_grad=0.05, grad_mode=M.GRAD_ADJOINT, seed=3)
+    model = U.open_ctx(prob, P)
+    fx, ff = _run(model, 1)
+    c = prob.objective.arrays["center"]
+    mx, mf, negH = MD.significant_modes(prob)
+    assert fx.shape[0] == 1
+    assert MD.mahalanobis(fx, c, negH[0])[0] <= 1e-3
+    model.close()
+
+
+def test_determinism_and_graph_equivalence():
+    prob = I.small_mixture(5, 6, 3000, seed=20)
+    P = M.Params(n_osc=4, m=6, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=9)
+    outs = []
+    for use_graph in (1, 1, 0):
+        model = U.open_ctx(prob, P, use_graph=use_graph)
+        for _ in range(3):
+            model.step()
+        outs.append(model.get(0, CH.FIELD_X).copy())
+        model.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+def test_full_size_quadratic_step_properties():
+    """quadratic_d64 at N=65536 in the benchmark's launch configuration: Phase 1
+    never decreases f; sampled rows match the oracle's Phase 1 on the same rows
+    (Phase 1 is independent per sample) to 1e-3 of their distance moved."""
+    prob = I.quadratic_d64()
+    P = M.Params(n_osc=1000, m=10, eps_grad=0.05, grad_mode=M.GRAD_ADJOINT, seed=3)
+    model = U.open_ctx(prob, P)
+    x0 = model.get(0, CH.FIELD_X)[:, :64].astype(np.float64)
+    f0 = OB.value(prob.objective, x0)
+    model.run_phase(0, CH.PHASE_LBFGS, 3)
+    st = U.read_state(model, prob, P.m)
+    assert np.all(st.f >= f0.astype(np.float32) - 1e-6 * np.abs(f0))
+    rows = np.random.default_rng(0).choice(prob.n, 48, replace=False)
+    sub = I.Problem(64, 48, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad, prob.sigma_mode)
+    ref = M.new_state(x0[rows], P.m)
+    M.lbfgs_iterations(sub, ref, P, 3)
+    move = np.abs(ref.x - x0[rows]).max(axis=1)
+    err = np.abs(st.x[rows] - ref.x).max(axis=1)
+    assert np.median(err / move) <= 1e-3
+    model.step()                                      # a full non-final cycle runs
+    c = model.counters(0)
+    assert c["cycles"] == 1 and c["evals"] > 0 and c["ls_fail"] <= c["ls_trials"]
+    model.close()
+
+
+def test_modes_capacity_and_errors():
+    prob = I.mixture4_d2(n=256)
+    P = M.Params(n_osc=2, m=5, eps_grad=1e-5, grad_mode=M.GRAD_ADJOINT)
+    model = U.open_ctx(prob, P)
+    model.step()
+    model.step()
+    x, f = model.modes(0)
+    with pytest.raises(CH.ChisaoError):
+        model.modes(0, cap=max(0, x.shape[0] - 1))
+    model.load_population(0, prob.x0)                   # resets the cycle count
+    model.step()
+    assert model.counters(0)["cycles"] == 1
+    model.close()

@@ -1,0 +1,123 @@
+"""Parity of Phases 4-6 (reseeding, Hands Like Clouds, anti-convergence) with
+the oracle from identical binary32 state and the same Philox streams.
+
+Reseeding: the strategy, the parent / peak / column / sign indices (integer
+Philox arithmetic on both sides) and therefore every child's ray are
+identical; positions agree to binary32 rounding (1e-5 of the box width).
+HLC and anti-convergence: positions agree to 1e-5 of the distance moved plus
+binary32 rounding of the position; the scale estimates to 1e-6.
+"""
+import numpy as np
+import pytest
+
+import gpu_util as U
+from oracle import method as M
+from paper_2606_26164_gb300 import chisao as CH
+from paper_2606_26164_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _reseed_case(case, d, N, rng):
+    stuck = rng.random(N) < 0.6
+    removed = stuck & (rng.random(N) < 0.4)
+    gr = (0, 0, -1)
+    if case in ("gr", "gr_off", "no_surv"):
+        stuck = np.ones(N, bool)
+        stuck[rng.choice(N, 3, replace=False)] = False          # 3 unfrozen: Golden Rooster
+        removed = stuck & (rng.random(N) < 0.5)
+        if case == "no_surv":
+            removed = stuck.copy()
+    if case == "none":
+        removed[:] = False
+    if case == "gr_off":
+        gr = (1, 1, int((stuck & ~removed).sum()))               # no growth again -> disabled
+    else:
+        gr = (1, 0, -1)
+    return stuck, removed, gr
+
+
+@pytest.mark.parametrize("case,d", [("rm", 5), ("rm", 64), ("gr", 5), ("gr", 64), ("gr_off", 8),
+                                    ("none", 5), ("no_surv", 3)])
+def test_reseed(case, d):
+    rng = np.random.default_rng(hash((case, d)) % 2 ** 32)
+    N = 777
+    prob = I.small_mixture(d, 3, N, seed=12)
+    P = M.Params(seed=21)
+    stuck, removed, gr = _reseed_case(case, d, N, rng)
+    st = M.new_state(prob.x0, P.m)
+    st.f = rng.normal(0, 1, N).astype(np.float32).astype(np.float64)
+    st.hlen[:] = 2
+    st = U.rounded(st)
+    model = U.open_ctx(prob, P)
+    st.stuck, st.removed = stuck, removed
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_LISTS)
+    model.set_gr_state(0, *gr)
+    model.run_phase(0, CH.PHASE_RESEED, 3)
+    got = U.read_state(model, prob, P.m)
+    ref = M.State(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.__dict__.items()})
+    ref.stuck = stuck & ~removed
+    ref.gr_enabled, ref.gr_noprog, ref.gr_prev_surv = bool(gr[0]), gr[1], gr[2]
+    M.reseed(prob, ref, P, cycle=3)
+    c = model.counters(0)
+    assert c["last_reseed"] == ref.last_reseed
+    assert c["gr_enabled"] == int(ref.gr_enabled)
+    width = (prob.hi - prob.lo).max()
+    np.testing.assert_allclose(got.x, ref.x, rtol=0, atol=1e-5 * width)
+    untouched = ~removed
+    np.testing.assert_array_equal(got.x[untouched], st.x[untouched])
+    assert np.all(got.hlen[removed] == 0) and np.all(got.hlen[untouched] == 2)
+    model.close()
+
+
+@pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64])
+@pytest.mark.parametrize("d", [3, 16])
+def test_hands_like_clouds(mode, d):
+    rng = np.random.default_rng(d)
+    N = 901
+    prob = I.small_mixture(d, 4, N, seed=13)
+    P = M.Params(n_cloud=3, M=8, grad_mode=mode, seed=3)
+    st = M.new_state(prob.x0, P.m)
+    st.stuck = rng.random(N) < 0.3
+    st.hlen[:] = 1
+    st = U.rounded(st)
+    model = U.open_ctx(prob, P)
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_HLC, 2)
+    got = U.read_state(model, prob, P.m)
+    ref = M.State(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.__dict__.items()})
+    sigma, alpha = M.hlc(prob, ref, P, cycle=2)
+    c = model.counters(0)
+    assert c["sigma"] == pytest.approx(sigma, rel=1e-6)
+    assert c["alpha_hlc"] == pytest.approx(alpha, rel=1e-5)
+    move = np.abs(ref.x - st.x).max(axis=1)
+    err = np.abs(got.x - ref.x).max(axis=1)
+    assert np.all(err <= 1e-5 * move + 2e-6 * np.abs(st.x).max(axis=1)), (err / np.maximum(move, 1e-30)).max()
+    np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
+    assert np.all(got.hlen[~st.stuck] == 0) and np.all(got.hlen[st.stuck] == 1)
+    model.close()
+
+
+@pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64])
+@pytest.mark.parametrize("d", [2, 16])
+def test_anti_convergence(mode, d):
+    rng = np.random.default_rng(d + 100)
+    N = 1203
+    prob = I.small_mixture(d, 4, N, seed=14)
+    P = M.Params(n_anti=5, mu=0.9, grad_mode=mode)
+    st = M.new_state(prob.x0 * np.float32(0.8), P.m)
+    st.stuck = rng.random(N) < 0.25
+    st = U.rounded(st)
+    model = U.open_ctx(prob, P)
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_ANTI)
+    got = U.read_state(model, prob, P.m)
+    ref = M.State(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.__dict__.items()})
+    alpha = M.anti_converge(prob, ref, P)
+    assert model.counters(0)["alpha_anti"] == pytest.approx(alpha, rel=1e-5)
+    move = np.abs(ref.x - st.x).max(axis=1)
+    err = np.abs(got.x - ref.x).max(axis=1)
+    assert np.all(err <= 1e-5 * move + 2e-6 * np.abs(st.x).max(axis=1)), (err / np.maximum(move, 1e-30)).max()
+    np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
+    model.close()
