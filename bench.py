@@ -74,7 +74,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -275,10 +275,10 @@ def main():
     if not args.no_extras and rank == 0:
         # --- dominant kernel: Phase 1 (fused L-BFGS) alone, CUDA events on the context stream
         reps = 5
-        k0 = model.counters(0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         model.load_population(0, prob.x0)
+        k0 = model.counters(0)
         e0.record(model._stream)
         for _ in range(reps):
             model.run_phase(0, CH.PHASE_LBFGS, n_conv)

@@ -215,7 +215,7 @@ typedef enum {
   CHISAO_FIELD_F = 2,        /* float [n]       f                              */
   CHISAO_FIELD_HS = 3,       /* float [n][m_max][dp]  s pairs, slot 0 newest    */
   CHISAO_FIELD_HY = 4,       /* float [n][m_max][dp]  y pairs of F = -f          */
-  CHISAO_FIELD_HRHO = 5,     /* double [n][m_max]     1 / s^T y                  */
+  CHISAO_FIELD_HRHO = 5,     /* float [n][m_max]      1 / s^T y                  */
   CHISAO_FIELD_HLEN = 6,     /* int32 [n]       stored pairs                    */
   CHISAO_FIELD_STUCK = 7,    /* uint32 [ceil(n/32)] stuck bit mask               */
   CHISAO_FIELD_REMOVED = 8   /* uint32 [ceil(n/32)] removed-by-dedup bit mask     */

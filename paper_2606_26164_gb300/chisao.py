@@ -225,7 +225,7 @@ class Chisao:
         n = pr.n
         return {FIELD_X: ((n, dp), np.float32), FIELD_G: ((n, dp), np.float32), FIELD_F: ((n,), np.float32),
                 FIELD_HS: ((n, mm, dp), np.float32), FIELD_HY: ((n, mm, dp), np.float32),
-                FIELD_HRHO: ((n, mm), np.float64), FIELD_HLEN: ((n,), np.int32),
+                FIELD_HRHO: ((n, mm), np.float32), FIELD_HLEN: ((n,), np.int32),
                 FIELD_STUCK: (((n + 31) // 32,), np.uint32), FIELD_REMOVED: (((n + 31) // 32,), np.uint32)}[field]
 
     def get(self, prob: int, field: int) -> np.ndarray:

@@ -153,9 +153,8 @@ void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
   P.f = b.take<float>(n);
   P.hs = b.take<float>(n * MMAX * dp);
   P.hy = b.take<float>(n * MMAX * dp);
-  P.hrho = b.take<double>(n * MMAX);
+  P.hrho = b.take<float>(n * MMAX);
   P.hlen = b.take<int>(n);
-  P.hgam = nullptr;
   P.stuck = b.take<uint32_t>(nw);
   P.removed = b.take<uint32_t>(nw);
   P.l_stuck = b.take<int>(n);
@@ -625,7 +624,7 @@ static chisao_status field_ptr(chisao_ctx* c, int32_t prob, int32_t field, void*
     case CHISAO_FIELD_F: *ptr = P.f; *bytes = n * 4; break;
     case CHISAO_FIELD_HS: *ptr = P.hs; *bytes = n * MMAX * ph.dp * 4; break;
     case CHISAO_FIELD_HY: *ptr = P.hy; *bytes = n * MMAX * ph.dp * 4; break;
-    case CHISAO_FIELD_HRHO: *ptr = P.hrho; *bytes = n * MMAX * 8; break;
+    case CHISAO_FIELD_HRHO: *ptr = P.hrho; *bytes = n * MMAX * 4; break;
     case CHISAO_FIELD_HLEN: *ptr = P.hlen; *bytes = n * 4; break;
     case CHISAO_FIELD_STUCK: *ptr = P.stuck; *bytes = (size_t)P.nwords * 4; break;
     case CHISAO_FIELD_REMOVED: *ptr = P.removed; *bytes = (size_t)P.nwords * 4; break;

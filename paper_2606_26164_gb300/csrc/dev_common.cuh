@@ -4,8 +4,8 @@
 //   x, g      float [n][dp]          dp = padded dimension (power of two >= 4)
 //   f         float [n]
 //   hs, hy    float [n][MMAX][dp]    L-BFGS pairs, slot 0 = newest
-//   hrho      double [n][MMAX]       1 / s^T y (FP64 curvature product)
-//   hlen      int [n], hgam float [n]
+//   hrho      float [n][MMAX]        1 / s^T y (s^T y accumulated in double-single)
+//   hlen      int [n]
 //   stuck, removed   uint32 bit masks [ceil(n/32)]
 // Padded coordinates are zero in x, g, the history and every objective
 // parameter, so they never contribute to a dot product or a norm.
@@ -84,9 +84,8 @@ struct ProbDev {
   float* f;
   float* hs;
   float* hy;
-  double* hrho;
+  float* hrho;                  // 1 / s^T y per slot
   int* hlen;
-  float* hgam;
   uint32_t* stuck;
   uint32_t* removed;
   int* l_stuck;                 // stuck samples, index order
@@ -120,6 +119,33 @@ struct EvalArgs {
   float* g;         // [n][d] device or null
 };
 
+// ------------------------------------------------------------------ double-single sums
+// s^T y of the L-BFGS update is accumulated beyond binary32: every product
+// s_j y_j is split exactly into hi + lo with one FMA, and the terms are summed
+// with Knuth's TwoSum, so the result carries ~48 significant bits (as accurate
+// as an FP64 accumulation of the same binary32 products) while running on the
+// FP32 pipe -- GB300's FP64 rate is a small fraction of its FP32 rate.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, t;
+  two_sum(h, bh, s, t);
+  t += l + bl;
+  h = s + t;
+  l = t - (h - s);
+}
+// exact s0*y0 + s1*y1 as a double-single pair
+__device__ __forceinline__ void ff_dot2(float s0, float y0, float s1, float y1, float& h, float& l) {
+  const float p0 = s0 * y0, e0 = fmaf(s0, y0, -p0);
+  const float p1 = s1 * y1, e1 = fmaf(s1, y1, -p1);
+  h = p0;
+  l = e0;
+  ff_add(h, l, p1, e1);
+}
+
 // ------------------------------------------------------------------ groups
 template <int LPS>
 struct Grp {
@@ -146,6 +172,15 @@ struct Grp {
     return __shfl_sync(mask, v, src, LPS);
   }
   __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
+  // double-single sum over the group (bitwise identical in every lane: TwoSum
+  // is exact, so swapping the operands of each butterfly step changes nothing)
+  __device__ __forceinline__ void ff_sum(float& h, float& l) const {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(mask, h, o, LPS), ol = __shfl_xor_sync(mask, l, o, LPS);
+      ff_add(h, l, oh, ol);
+    }
+  }
 };
 
 template <typename T> struct Vec2;

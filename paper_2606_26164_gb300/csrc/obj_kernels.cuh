@@ -13,12 +13,12 @@ constexpr int NT_SCALES = 256;  // threads per block of the scale reduction
 constexpr int SCALE_BLOCKS = 608;  // fixed grid of the scale reduction (4 x 152 SMs)
 
 // L-BFGS two-loop recursion (Nocedal & Wright, Algorithm 7.4) on F = -f with
-// the register-resident history (slot 0 newest), H0 = gam * I.  Dot products
-// are FP32 group sums; the FP64 rho multiplies them in FP64.
+// the register-resident history (slot 0 newest), H0 = gam * I, in binary32
+// with group-sum dot products.
 template <int LPS>
 __device__ __forceinline__ void two_loop(const float (&s0)[MMAX], const float (&s1)[MMAX],
                                          const float (&y0)[MMAX], const float (&y1)[MMAX],
-                                         const double (&rho)[MMAX], int len, float gam, float G0,
+                                         const float (&rho)[MMAX], int len, float gam, float G0,
                                          float G1, float& p0, float& p1, const Grp<LPS>& g) {
   float q0 = G0, q1 = G1;
   float al[MMAX];
@@ -26,8 +26,7 @@ __device__ __forceinline__ void two_loop(const float (&s0)[MMAX], const float (&
   for (int k = 0; k < MMAX; ++k) {
     al[k] = 0.f;
     if (k < len) {
-      const float dt = g.sum(s0[k] * q0 + s1[k] * q1);
-      al[k] = (float)(rho[k] * (double)dt);
+      al[k] = rho[k] * g.sum(s0[k] * q0 + s1[k] * q1);
       q0 = fmaf(-al[k], y0[k], q0);
       q1 = fmaf(-al[k], y1[k], q1);
     }
@@ -37,8 +36,7 @@ __device__ __forceinline__ void two_loop(const float (&s0)[MMAX], const float (&
 #pragma unroll
   for (int k = MMAX - 1; k >= 0; --k) {
     if (k < len) {
-      const float dt = g.sum(y0[k] * r0 + y1[k] * r1);
-      const float be = (float)(rho[k] * (double)dt);
+      const float be = rho[k] * g.sum(y0[k] * r0 + y1[k] * r1);
       r0 = fmaf(s0[k], al[k] - be, r0);
       r1 = fmaf(s1[k], al[k] - be, r1);
     }
@@ -47,10 +45,12 @@ __device__ __forceinline__ void two_loop(const float (&s0)[MMAX], const float (&
   p1 = -r1;
 }
 
+// History of sample i into registers; gam = s^T y / y^T y of the newest pair
+// (s^T y = 1 / rho).
 template <int DP, int LPS>
 __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, int len, float (&s0)[MMAX],
                                              float (&s1)[MMAX], float (&y0)[MMAX], float (&y1)[MMAX],
-                                             double (&rho)[MMAX], float& gam, const Grp<LPS>& g) {
+                                             float (&rho)[MMAX], float& gam, const Grp<LPS>& g) {
 #pragma unroll
   for (int k = 0; k < MMAX; ++k) {
     if (k < len) {
@@ -61,15 +61,11 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
       rho[k] = P.hrho[(size_t)i * MMAX + k];
     } else {
       s0[k] = s1[k] = y0[k] = y1[k] = 0.f;
-      rho[k] = 0.0;
+      rho[k] = 0.f;
     }
   }
   gam = 1.f;
-  if (len > 0) {
-    const double sy = g.sum((double)s0[0] * y0[0] + (double)s1[0] * y1[0]);
-    const double yy = g.sum((double)y0[0] * y0[0] + (double)y1[0] * y1[0]);
-    gam = (float)(sy / yy);
-  }
+  if (len > 0) gam = (1.0f / rho[0]) / g.sum(y0[0] * y0[0] + y1[0] * y1[0]);
 }
 
 // ------------------------------------------------------------------ Phase 1
@@ -78,8 +74,8 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 //   direction; backtracking Armijo over alpha0 2^-t on the box projection
 //   x_t = clip(x + alpha p), F(x_t) <= F(x) + c1 grad F^T (x_t - x), first pass
 //   wins (alpha0 = 1, or min(1, 1/|grad F|_inf) on an empty history); new
-//   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y| with s^T y, |s|, |y|
-//   accumulated in FP64.  A failed search clears the history.
+//   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y|, s^T y summed from
+//   exact products in double-single.  A failed search clears the history.
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh) {
   constexpr int LPS = DP / 2;
@@ -95,7 +91,8 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
     const float lo0 = P.lo[j0], lo1 = P.lo[j0 + 1], hi0 = P.hi[j0], hi1 = P.hi[j0 + 1];
     int len = P.hlen[i];
     float s0[MMAX], s1[MMAX], y0[MMAX], y1[MMAX], gam;
-    double rho[MMAX];
+    float rho[MMAX];
+    const float curv_eps = (float)S.curv_eps;
     load_history<DP, LPS>(P, i, j0, len, s0, s1, y0, y1, rho, gam, g);
     TE F;
     float G0, G1;
@@ -161,18 +158,21 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
         Gt1 = -a1g;
       }
       const float sv0 = xt0 - x0, sv1 = xt1 - x1, yv0 = Gt0 - G0, yv1 = Gt1 - G1;
-      const double sy = g.sum((double)sv0 * yv0 + (double)sv1 * yv1);
-      const double ss = g.sum((double)sv0 * sv0 + (double)sv1 * sv1);
-      const double yy = g.sum((double)yv0 * yv0 + (double)yv1 * yv1);
-      if (sy > S.curv_eps * sqrt(ss * yy)) {
+      float syh, syl;                                // s^T y, exact products + compensated sum
+      ff_dot2(sv0, yv0, sv1, yv1, syh, syl);
+      g.ff_sum(syh, syl);
+      const float sy = syh + syl;
+      const float ss = g.sum(sv0 * sv0 + sv1 * sv1);  // sums of squares: no cancellation
+      const float yy = g.sum(yv0 * yv0 + yv1 * yv1);
+      if (sy > curv_eps * sqrtf(ss) * sqrtf(yy)) {
 #pragma unroll
         for (int k = MMAX - 1; k > 0; --k) {
           s0[k] = s0[k - 1]; s1[k] = s1[k - 1]; y0[k] = y0[k - 1]; y1[k] = y1[k - 1]; rho[k] = rho[k - 1];
         }
         s0[0] = sv0; s1[0] = sv1; y0[0] = yv0; y1[0] = yv1;
-        rho[0] = 1.0 / sy;
+        rho[0] = 1.0f / sy;
         len = min(len + 1, S.m);
-        gam = (float)(sy / yy);
+        gam = sy / yy;
       }
       x0 = xt0; x1 = xt1; F = Ft; G0 = Gt0; G1 = Gt1;
     }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_direction(ProbDev P) {
   const int j0 = 2 * g.l;
   const int len = P.hlen[i];
   float s0[MMAX], s1[MMAX], y0[MMAX], y1[MMAX], gam;
-  double rho[MMAX];
+  float rho[MMAX];
   load_history<DP, LPS>(P, i, j0, len, s0, s1, y0, y1, rho, gam, g);
   const float2 gv = *reinterpret_cast<const float2*>(P.g + (size_t)i * DP + j0);
   float p0, p1;

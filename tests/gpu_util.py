@@ -73,7 +73,7 @@ def write_state(model: CH.Chisao, prob, st: M.State, q: int = 0):
     HY = np.zeros((n, mm, dp), np.float32)
     HS[:, :m, :d] = st.S
     HY[:, :m, :d] = st.Y
-    R = np.zeros((n, mm), np.float64)
+    R = np.zeros((n, mm), np.float32)
     s64, y64 = HS[:, :m, :d].astype(np.float64), HY[:, :m, :d].astype(np.float64)
     sy = np.einsum("nkd,nkd->nk", s64, y64)
     with np.errstate(divide="ignore"):
