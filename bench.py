@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--workload", default="quadratic_d64")
     ap.add_argument("--grad", default="adjoint", choices=["adjoint", "fd64", "fd32"])
     ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--n", type=int, default=0, help="override the population size (profiling cases)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -243,6 +244,10 @@ def main():
     from paper_2606_26164_gb300 import chisao as CH
 
     prob = make_problem(args.workload, seed=rank)
+    if args.n:
+        from paper_2606_26164_gb300 import inputs as I
+        prob = I.Problem(prob.d, args.n, prob.lo, prob.hi, prob.objective, prob.x0[:args.n], prob.eps_grad,
+                         prob.sigma_mode)
     N, d = prob.n, prob.d
     gm = GRAD[args.grad]
     n_osc = 10 ** 6                      # every timed cycle is a non-final cycle

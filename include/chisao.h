@@ -83,6 +83,11 @@ typedef struct {
   const double *center;
   const double *Q;
   const double *lam;
+  /* Additive evaluation noise f~ = f + eps, eps ~ N(0, noise_sigma^2)
+   * (Sec. 5.6); 0 for none.  Each evaluation point gets its own draw, keyed
+   * by the point's binary32 coordinates and the Philox seed.  Exact (adjoint)
+   * gradients are those of the noise-free f. */
+  double noise_sigma;
 } chisao_objective;
 
 /* One problem: dimension, population size, the box Theta and the initial

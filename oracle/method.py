@@ -107,10 +107,25 @@ def new_state(x0, m: int) -> State:
 # objective access (Sec. 3.1: gradients by finite differences or supplied analytically)
 # ----------------------------------------------------------------------------------------------
 
-def evaluate(prob, X, st: Optional[State] = None):
+def _pidx(prob) -> int:
+    """Index of the problem within a batched context (0 for a lone problem)."""
+    return int(getattr(prob, "index", 0))
+
+
+def evaluate(prob, X, st: Optional[State] = None, seed: int = 0, prob_index: int = 0):
+    """f at the rows of X, plus the additive N(0, sigma_noise^2) evaluation noise
+    of Sec. 5.6 when the objective has some.  Reading (the paper does not say
+    how the noise is drawn): each evaluation point gets its own draw, keyed by
+    the point's binary32 coordinates (philox.point_noise), so repeated
+    evaluations of one point see the same value.  Parity with the paper's noise
+    table is unpinned."""
     if st is not None:
         st.evals += X.shape[0]
-    return OB.value(prob.objective, X)
+    f = OB.value(prob.objective, X)
+    s = getattr(prob.objective, "noise_sigma", 0.0)
+    if s:
+        f = f + s * PX.point_noise(seed, prob_index, X)
+    return f
 
 
 def fd_steps(X, P: Params):
@@ -132,7 +147,8 @@ def fd_gradient(prob, X, P: Params, st: Optional[State] = None):
         Xm = X.copy()
         Xp[:, j] = X[:, j] + H[:, j]
         Xm[:, j] = X[:, j] - H[:, j]
-        G[:, j] = (evaluate(prob, Xp, st) - evaluate(prob, Xm, st)) / (Xp[:, j] - Xm[:, j])
+        G[:, j] = (evaluate(prob, Xp, st, P.seed, _pidx(prob)) -
+                   evaluate(prob, Xm, st, P.seed, _pidx(prob))) / (Xp[:, j] - Xm[:, j])
     return G
 
 
@@ -197,7 +213,7 @@ def line_search(prob, X, F, G, Pd, alpha0, P: Params, st: Optional[State] = None
         idx = np.flatnonzero(todo)
         a = alpha0[idx] * 2.0 ** (-t)
         Xt = np.clip(X[idx] + a[:, None] * Pd[idx], lo, hi)
-        Ft = -evaluate(prob, Xt, st)
+        Ft = -evaluate(prob, Xt, st, P.seed, _pidx(prob))
         trials[idx] += 1
         ok = Ft <= F[idx] + P.c1 * np.einsum("nd,nd->n", G[idx], Xt - X[idx])
         sel = idx[ok]
@@ -231,7 +247,7 @@ def lbfgs_iterations(prob, st: State, P: Params, n_iter: int, fresh_gradient: bo
     X = st.x
     N, d = X.shape
     if fresh_gradient:
-        st.f = evaluate(prob, X, st)
+        st.f = evaluate(prob, X, st, P.seed, _pidx(prob))
         st.g = gradient(prob, X, P, st)
     F = -st.f
     G = -st.g

@@ -75,8 +75,25 @@ def grad(obj, X):
     return np.einsum("nk,nkd->nd", r, score)
 
 
+def _precisions(obj):
+    """Sigma_k^-1 for every component (computed once per objective)."""
+    cache = obj.__dict__.setdefault("_oracle_cache", {})
+    if "prec" not in cache:
+        A = obj.arrays
+        if obj.kind == OBJ_MIXTURE_DIAG:
+            cache["prec"] = np.stack([np.diag(1.0 / s ** 2) for s in A["sigmas"]])
+        else:
+            P = []
+            for L in A["chol"]:
+                Linv = np.linalg.inv(L)
+                P.append(Linv.T @ Linv)
+            cache["prec"] = np.stack(P)
+    return cache["prec"]
+
+
 def hessian(obj, x):
-    """Hessian of f at one point x (d,), for the Newton mode finder."""
+    """Hessian of f at one point x (d,), for the Newton mode finder:
+    sum_k r_k (a_k a_k^T - Sigma_k^-1) - gbar gbar^T."""
     x = np.asarray(x, dtype=np.float64)[None, :]
     if obj.kind == OBJ_QUADRATIC:
         A = obj.arrays
@@ -85,15 +102,7 @@ def hessian(obj, x):
     lc, score = _component_logdens(obj, x)
     r = np.exp(lc - _lse(lc)[:, None])[0]
     a = score[0]                                            # (K, d)
-    A = obj.arrays
-    K, d = A["means"].shape
-    H = np.zeros((d, d))
-    for k in range(K):
-        if obj.kind == OBJ_MIXTURE_DIAG:
-            prec = np.diag(1.0 / A["sigmas"][k] ** 2)
-        else:
-            Linv = np.linalg.inv(A["chol"][k])
-            prec = Linv.T @ Linv
-        H += r[k] * (-prec + np.outer(a[k], a[k]))
+    prec = _precisions(obj)
+    H = np.einsum("k,kij->ij", r, -prec) + np.einsum("k,ki,kj->ij", r, a, a)
     gbar = r @ a
     return H - np.outer(gbar, gbar)

@@ -100,6 +100,40 @@ def normal_rows(seed, rows, d, tag, cycle, step, prob, k):
     return z.reshape(rows.shape[0], nb * 4)[:, :d]
 
 
+def _lowbias32(v):
+    """Wellons' 'lowbias32' integer finalizer (xorshift-multiply, 3 rounds)."""
+    v = v & MASK32
+    v ^= v >> np.uint64(16)
+    v = (v * np.uint64(0x7FEB352D)) & MASK32
+    v ^= v >> np.uint64(15)
+    v = (v * np.uint64(0x846CA68B)) & MASK32
+    v ^= v >> np.uint64(16)
+    return v
+
+
+def point_key(X):
+    """Two 32-bit words identifying an evaluation point: coordinate j's binary32
+    bit pattern b_j is mixed as v_j = lowbias32(b_j xor (j * 0x9E3779B9)); the
+    words are sum_j v_j and xor_j v_j (2j + 1) (mod 2^32)."""
+    X32 = np.ascontiguousarray(np.asarray(X, dtype=np.float64).astype(np.float32))
+    b = X32.view(np.uint32).astype(np.uint64)
+    j = np.arange(X32.shape[1], dtype=np.uint64)
+    v = _lowbias32(b ^ ((j * np.uint64(0x9E3779B9)) & MASK32)[None, :])
+    h1 = v.sum(axis=1) & MASK32
+    h2 = np.bitwise_xor.reduce((v * (np.uint64(2) * j + np.uint64(1))[None, :]) & MASK32, axis=1)
+    return h1, h2
+
+
+def point_noise(seed, prob, X):
+    """One standard normal per evaluation point (Sec. 5.6 noise, keyed by the point)."""
+    h1, h2 = point_key(X)
+    ctr = np.stack([h1, h2, np.full_like(h1, TAG_NOISE << 24), np.full_like(h1, (int(prob) & 0xFFFF) << 16)],
+                   axis=-1)
+    w = philox4x32_10(ctr, make_key(seed))
+    u = u01(w)
+    return np.sqrt(-2.0 * np.log(u[:, 0])) * np.cos(2.0 * np.pi * u[:, 1])
+
+
 def uniform_rows(seed, rows, d, tag, cycle, step, prob, k):
     rows = np.asarray(rows, dtype=np.uint64)
     nb = (d + 3) // 4

@@ -45,7 +45,8 @@ _DP = C.POINTER(C.c_double)
 
 class CObjective(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_comp", C.c_int32), ("weights", _DP), ("means", _DP),
-                ("sigmas", _DP), ("chol", _DP), ("center", _DP), ("Q", _DP), ("lam", _DP)]
+                ("sigmas", _DP), ("chol", _DP), ("center", _DP), ("Q", _DP), ("lam", _DP),
+                ("noise_sigma", C.c_double)]
 
 
 class CProblem(C.Structure):
@@ -133,7 +134,8 @@ class Chisao:
             self._keep += [A, lo, hi, x0]
             co = CObjective(kind=ob.kind, n_comp=ob.n_comp, weights=_dptr(A.get("weights")),
                             means=_dptr(A.get("means")), sigmas=_dptr(A.get("sigmas")), chol=_dptr(A.get("chol")),
-                            center=_dptr(A.get("center")), Q=_dptr(A.get("Q")), lam=_dptr(A.get("lam")))
+                            center=_dptr(A.get("center")), Q=_dptr(A.get("Q")), lam=_dptr(A.get("lam")),
+                            noise_sigma=float(getattr(ob, "noise_sigma", 0.0)))
             cprobs[q] = CProblem(d=pr.d, n=pr.n, lo=_dptr(lo), hi=_dptr(hi),
                                  x0=x0.ctypes.data_as(C.POINTER(C.c_float)), objective=co)
         self.problems = list(problems)

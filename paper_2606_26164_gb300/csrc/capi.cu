@@ -109,6 +109,7 @@ chisao_status validate_problem(const chisao_problem* pr, std::string& why) {
       return CHISAO_ERR_ARG;
     }
   const chisao_objective& o = pr->objective;
+  if (!(std::isfinite(o.noise_sigma) && o.noise_sigma >= 0)) { why = "noise_sigma must be finite and >= 0"; return CHISAO_ERR_ARG; }
   if (o.kind == CHISAO_OBJ_MIXTURE_DIAG || o.kind == CHISAO_OBJ_MIXTURE_FULL) {
     if (o.n_comp < 1 || o.n_comp > 65536) { why = "mixture needs 1 <= K <= 65536"; return CHISAO_ERR_ARG; }
     if (!o.weights || !o.means) { why = "mixture needs weights and means"; return CHISAO_ERR_ARG; }
@@ -441,6 +442,8 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     P.prob_index = q;
     P.m = params->m;
     P.obj.kind = ph.kind;
+    P.obj.prob_index = q;
+    P.obj.noise_sigma = (float)pr.objective.noise_sigma;
     P.obj.f32.K = P.obj.f64.K = (ph.kind == CHISAO_OBJ_QUADRATIC) ? 0 : ph.K;
     P.obj.f32.d = P.obj.f64.d = ph.d;
     P.obj.f32.dp = P.obj.f64.dp = ph.dp;

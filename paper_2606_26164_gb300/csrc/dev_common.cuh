@@ -48,6 +48,8 @@ struct ObjParams {
 
 struct ObjDev {
   int kind;
+  int prob_index;
+  float noise_sigma;            // additive evaluation noise (0: none)
   ObjParams<float> f32;
   ObjParams<double> f64;
 };
@@ -172,6 +174,11 @@ struct Grp {
     return __shfl_sync(mask, v, src, LPS);
   }
   __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
+  __device__ __forceinline__ unsigned xor_all(unsigned v) const {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(mask, v, o, LPS);
+    return v;
+  }
   // double-single sum over the group (bitwise identical in every lane: TwoSum
   // is exact, so swapping the operands of each butterfly step changes nothing)
   __device__ __forceinline__ void ff_sum(float& h, float& l) const {
@@ -241,11 +248,17 @@ __device__ __forceinline__ void normals4d(uint4 w, double out[4]) {
   out[3] = r1 * s1;
 }
 
-// The two normals of coordinates 2l, 2l+1 (block (2l)/4, positions (2l)%4, +1).
+// The two normals of coordinates 2l, 2l+1: block (2l)/4 of the stream, the
+// Box-Muller pair (w0, w1) for even l and (w2, w3) for odd l -- only that pair
+// is transformed.
 __device__ __forceinline__ float2 normals_pair(const StepParams& S, unsigned row, int l, unsigned tag,
                                                unsigned cycle, unsigned step, unsigned prob, unsigned k) {
-  const float4 z = normals4f(rng_words(S, row, (unsigned)(l >> 1), tag, cycle, step, prob, k));
-  return (l & 1) ? make_float2(z.z, z.w) : make_float2(z.x, z.y);
+  const uint4 w = rng_words(S, row, (unsigned)(l >> 1), tag, cycle, step, prob, k);
+  const unsigned wa = (l & 1) ? w.z : w.x, wb = (l & 1) ? w.w : w.y;
+  float sn, cs;
+  const float r = sqrtf(-2.0f * logf(u01f(wa)));
+  sincospif(2.0f * u01f(wb), &sn, &cs);
+  return make_float2(r * cs, r * sn);
 }
 
 // ------------------------------------------------------------------ misc

@@ -131,11 +131,11 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
         TE ft;
         float ga0 = 0.f, ga1 = 0.f;
         if constexpr (GM == GRAD_ADJOINT) {
-          ft = Obj<KIND>::value_grad(P.obj.f32, c0, c1, ga0, ga1, g);
+          ft = value_grad_noisy<KIND>(P.obj, S, c0, c1, ga0, ga1, g);
           ec.evals += 1;
           ec.grads += 1;
         } else {
-          ft = Obj<KIND>::value(params_of<GM>(P.obj), (TE)c0, (TE)c1, g);
+          ft = value_noisy<KIND>(P.obj, params_of<GM>(P.obj), S, (TE)c0, (TE)c1, g);
           ec.evals += 1;
         }
         ++trials;
@@ -234,25 +234,31 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
   const int grp = threadIdx.x / LPS;
   const int j0 = 2 * g.l;
   EvalCount ec;
-  double sx0 = 0, sx1 = 0, sq0 = 0, sq1 = 0, sgg = 0, cnt = 0;
+  // double-single running sums (exact squares via FMA), converted to FP64 once
+  float sx0h = 0.f, sx0l = 0.f, sx1h = 0.f, sx1l = 0.f, sq0h = 0.f, sq0l = 0.f, sq1h = 0.f, sq1l = 0.f;
+  float sgh = 0.f, sgl = 0.f;
+  int cnt = 0;
   for (int i = blockIdx.x * GPB + grp; i < P.n; i += gridDim.x * GPB) {
     if (bit_of(P.stuck, i)) continue;
     const float2 xv = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + j0);
     float a0, a1;
     gradient_only<KIND, GM, LPS>(P.obj, S, P.d, xv.x, xv.y, a0, a1, g, ec);
     *reinterpret_cast<float2*>(P.g + (size_t)i * DP + j0) = make_float2(a0, a1);
-    sx0 += xv.x; sx1 += xv.y;
-    sq0 += (double)xv.x * xv.x; sq1 += (double)xv.y * xv.y;
-    sgg += g.sum((double)a0 * a0 + (double)a1 * a1);
-    cnt += 1.0;
+    ff_add(sx0h, sx0l, xv.x, 0.f);
+    ff_add(sx1h, sx1l, xv.y, 0.f);
+    const float p0 = xv.x * xv.x, p1 = xv.y * xv.y;
+    ff_add(sq0h, sq0l, p0, fmaf(xv.x, xv.x, -p0));
+    ff_add(sq1h, sq1l, p1, fmaf(xv.y, xv.y, -p1));
+    ff_add(sgh, sgl, g.sum(a0 * a0 + a1 * a1), 0.f);   // sum of squares: no cancellation
+    ++cnt;
   }
-  buf[grp][j0] = sx0;
-  buf[grp][j0 + 1] = sx1;
-  buf[grp][DP + j0] = sq0;
-  buf[grp][DP + j0 + 1] = sq1;
+  buf[grp][j0] = (double)sx0h + (double)sx0l;
+  buf[grp][j0 + 1] = (double)sx1h + (double)sx1l;
+  buf[grp][DP + j0] = (double)sq0h + (double)sq0l;
+  buf[grp][DP + j0 + 1] = (double)sq1h + (double)sq1l;
   if (g.l == 0) {
-    buf[grp][2 * DP] = sgg;
-    buf[grp][2 * DP + 1] = cnt;
+    buf[grp][2 * DP] = (double)sgh + (double)sgl;
+    buf[grp][2 * DP + 1] = (double)cnt;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < W; t += blockDim.x) {
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_eval(ProbDev P, StepParams S, const 
     if (j0 + 1 < d) gout[(size_t)i * d + j0 + 1] = a1;
     if (fout && g.l == 0) fout[i] = (float)f;
   } else {
-    const TE f = Obj<KIND>::value(params_of<GM>(P.obj), (TE)x0, (TE)x1, g);
+    const TE f = value_noisy<KIND>(P.obj, params_of<GM>(P.obj), S, (TE)x0, (TE)x1, g);
     if (fout && g.l == 0) fout[i] = (float)f;
   }
 }

@@ -178,6 +178,62 @@ struct Obj<OBJ_QUADRATIC> {
   }
 };
 
+// ------------------------------------------------------------ evaluation noise
+// Sec. 5.6 noise model f~ = f + eps, eps ~ N(0, sigma_noise^2).  Each
+// evaluation point gets its own draw: its binary32 coordinates are mixed with
+// Wellons' lowbias32 finalizer, v_j = lowbias32(bits(x_j) ^ j * 0x9E3779B9),
+// into the words (sum_j v_j, xor_j v_j (2j + 1)) that form the Philox counter
+// (with the noise tag and the problem index); Box-Muller on the first two
+// output words gives the normal.
+__device__ __forceinline__ unsigned lowbias32(unsigned v) {
+  v ^= v >> 16;
+  v *= 0x7FEB352Du;
+  v ^= v >> 15;
+  v *= 0x846CA68Bu;
+  v ^= v >> 16;
+  return v;
+}
+
+template <typename T, int LPS>
+__device__ __forceinline__ float point_noise(const ObjDev& O, const StepParams& S, int d, T x0, T x1,
+                                             const Grp<LPS>& g) {
+  const unsigned j0 = 2u * (unsigned)g.l;
+  unsigned h1 = 0u, h2 = 0u;
+  if ((int)j0 < d) {
+    const unsigned v = lowbias32(__float_as_uint((float)x0) ^ (j0 * 0x9E3779B9u));
+    h1 += v;
+    h2 ^= v * (2u * j0 + 1u);
+  }
+  if ((int)j0 + 1 < d) {
+    const unsigned v = lowbias32(__float_as_uint((float)x1) ^ ((j0 + 1u) * 0x9E3779B9u));
+    h1 += v;
+    h2 ^= v * (2u * j0 + 3u);
+  }
+  h1 = g.sum(h1);
+  h2 = g.xor_all(h2);
+  const uint4 w = philox4x32_10(make_uint4(h1, h2, TAG_NOISE << 24, ((unsigned)O.prob_index & 0xffffu) << 16),
+                                make_uint2(S.seed_lo, S.seed_hi));
+  return O.noise_sigma * sqrtf(-2.0f * logf(u01f(w.x))) * cospif(2.0f * u01f(w.y));
+}
+
+// f (+ noise) at a point, in the precision T of the parameters o.
+template <int KIND, typename T, int LPS>
+__device__ __forceinline__ T value_noisy(const ObjDev& O, const ObjParams<T>& o, const StepParams& S, T x0, T x1,
+                                         const Grp<LPS>& g) {
+  T f = Obj<KIND>::value(o, x0, x1, g);
+  if (O.noise_sigma != 0.f) f += (T)point_noise(O, S, o.d, x0, x1, g);
+  return f;
+}
+
+// f (+ noise) and the exact gradient of the noise-free f (the noise is constant in x).
+template <int KIND, int LPS>
+__device__ __forceinline__ float value_grad_noisy(const ObjDev& O, const StepParams& S, float x0, float x1,
+                                                  float& g0, float& g1, const Grp<LPS>& g) {
+  float f = Obj<KIND>::value_grad(O.f32, x0, x1, g0, g1, g);
+  if (O.noise_sigma != 0.f) f += point_noise(O, S, O.f32.d, x0, x1, g);
+  return f;
+}
+
 // ------------------------------------------------------------ gradient modes
 // TE: the precision objective values are computed in (FP64 for the FD64 mode).
 template <int GM>
@@ -212,8 +268,8 @@ __device__ __forceinline__ void fd_gradient(const ObjDev& O, const StepParams& S
     const TE hj = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(xj)) : (TE)S.h;
     const TE xp = xj + hj, xm = xj - hj;
     const bool mine = (g.l == own);
-    const TE fp = Obj<KIND>::value(o, (mine && !comp) ? xp : x0, (mine && comp) ? xp : x1, g);
-    const TE fm = Obj<KIND>::value(o, (mine && !comp) ? xm : x0, (mine && comp) ? xm : x1, g);
+    const TE fp = value_noisy<KIND>(O, o, S, (mine && !comp) ? xp : x0, (mine && comp) ? xp : x1, g);
+    const TE fm = value_noisy<KIND>(O, o, S, (mine && !comp) ? xm : x0, (mine && comp) ? xm : x1, g);
     const TE gj = (fp - fm) / (xp - xm);
     if (mine) {
       if (comp) g1 = (float)gj; else g0 = (float)gj;
@@ -231,14 +287,14 @@ __device__ __forceinline__ EvalT<GM> value_and_gradient(const ObjDev& O, const S
   using TE = EvalT<GM>;
   if constexpr (GM == GRAD_ADJOINT) {
     float a0, a1;
-    const float f = Obj<KIND>::value_grad(O.f32, x0, x1, a0, a1, g);
+    const float f = value_grad_noisy<KIND>(O, S, x0, x1, a0, a1, g);
     g0 = a0;
     g1 = a1;
     ec.evals += 1;
     ec.grads += 1;
     return f;
   } else {
-    const TE f = Obj<KIND>::value(params_of<GM>(O), (TE)x0, (TE)x1, g);
+    const TE f = value_noisy<KIND>(O, params_of<GM>(O), S, (TE)x0, (TE)x1, g);
     ec.evals += 1;
     fd_gradient<KIND, GM, LPS>(O, S, d, x0, x1, g0, g1, g, ec);
     return f;

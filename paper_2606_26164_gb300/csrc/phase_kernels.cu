@@ -368,15 +368,38 @@ __global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
 // Fixed-order sum of the per-block partials, then
 //   s = sqrt(mean_j var_j), sigma = c_sigma s, g_rms = sqrt(sum g^2 / (U d)),
 //   alpha = alpha_scale s / max(g_rms, 1e-30)   (fixed values when supplied).
-__global__ void __launch_bounds__(NT_LIN) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
+// 1024 threads = 8 row groups x 128 columns: row group q sums the partial
+// blocks b = q (mod 8) with four independent accumulators, then the 8 row-group
+// sums are added in order q = 0..7 -- a fixed order, so the result does not
+// depend on timing.
+constexpr int FIN_NT = 1024, FIN_RG = 8, FIN_COLS = FIN_NT / FIN_RG;
+__global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
   const int W = 2 * P.dp + 2;
-  extern __shared__ double tot[];
-  for (int t = threadIdx.x; t < W; t += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < nblocks; ++b) a += P.partials[(size_t)b * W + t];
-    tot[t] = a;
+  extern __shared__ double tot[];                   // [W]
+  __shared__ double part[FIN_RG][FIN_COLS];
+  const int q = threadIdx.x / FIN_COLS, cl = threadIdx.x % FIN_COLS;
+  for (int c0 = 0; c0 < W; c0 += FIN_COLS) {
+    const int col = c0 + cl;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (col < W) {
+      int b = q;
+      for (; b + 3 * FIN_RG < nblocks; b += 4 * FIN_RG) {
+        a0 += P.partials[(size_t)b * W + col];
+        a1 += P.partials[(size_t)(b + FIN_RG) * W + col];
+        a2 += P.partials[(size_t)(b + 2 * FIN_RG) * W + col];
+        a3 += P.partials[(size_t)(b + 3 * FIN_RG) * W + col];
+      }
+      for (; b < nblocks; b += FIN_RG) a0 += P.partials[(size_t)b * W + col];
+    }
+    part[q][cl] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (q == 0 && col < W) {
+      double s = 0.0;
+      for (int r = 0; r < FIN_RG; ++r) s += part[r][cl];
+      tot[col] = s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
     const double U = tot[2 * P.dp + 1];
     Counters* c = P.cnt;
@@ -513,7 +536,7 @@ int scale_blocks(const ProbDev& P) {
 }
 
 cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int which, cudaStream_t st) {
-  k_finalize_scales<<<1, NT_LIN, sizeof(double) * (2 * P.dp + 2), st>>>(P, S, scale_blocks(P), which);
+  k_finalize_scales<<<1, FIN_NT, sizeof(double) * (2 * P.dp + 2), st>>>(P, S, scale_blocks(P), which);
   return cudaGetLastError();
 }
 

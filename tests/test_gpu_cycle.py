@@ -75,6 +75,47 @@ def test_quadratic_proposition1_with_sufficient_iterations():
     model.close()
 
 
+def _true_mode_errors(fx, mx, negH):
+    return np.array([min(MD.mahalanobis(x[None], m, H)[0] for m, H in zip(mx, negH)) for x in fx])
+
+
+def test_full_covariance_mixture_d64_fp32_modes():
+    """d=64, K=256 full-covariance mixture (Cholesky factors with cond <= 100,
+    means in [-20, 20]^64) on the FP32 path: every returned point is a
+    significant mode (Eq. 1) to 1e-3 local sigmas, and the dominant mode is found."""
+    prob = I.mixture256_d64(n=8192)
+    P = M.Params(n_osc=2, m=10, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=4)
+    model = U.open_ctx(prob, P)
+    fx, ff = _run(model, P.n_osc)
+    mx, mf, negH = MD.significant_modes(prob)
+    assert fx.shape[0] >= 1
+    assert np.all(_true_mode_errors(fx, mx, negH) <= 1e-3)
+    frac, worst, best = MD.recovery(fx, mx, negH)
+    assert best[0] <= 1e-3                              # the global maximum
+    model.close()
+
+
+def test_batched_problems_in_one_context():
+    """Independent problems of uneven (d, N, K) in one context: each one's
+    returned points are significant modes of its own objective."""
+    probs = I.batched512(n_problems=10, n_scale=0.3)
+    P = M.Params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=5)
+    U.ensure_built()
+    model = CH.Chisao(probs, U.lib_params(P))
+    for _ in range(P.n_osc):
+        model.step()
+    fracs = []
+    for q, prob in enumerate(probs):
+        fx, ff = model.modes(q)
+        mx, mf, negH = MD.significant_modes(prob)
+        if fx.shape[0]:
+            assert np.all(_true_mode_errors(fx, mx, negH) <= 1e-3), q
+        fracs.append(MD.recovery(fx, mx, negH)[0])
+        assert model.counters(q)["cycles"] == P.n_osc
+    assert np.mean(fracs) > 0.3, fracs
+    model.close()
+
+
 def test_determinism_and_graph_equivalence():
     prob = I.small_mixture(5, 6, 3000, seed=20)
     P = M.Params(n_osc=4, m=6, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=9)
@@ -126,4 +167,19 @@ def test_modes_capacity_and_errors():
     model.load_population(0, prob.x0)                   # resets the cycle count
     model.step()
     assert model.counters(0)["cycles"] == 1
+    model.close()
+
+
+@pytest.mark.parametrize("sigma", [0.1, 1.0])
+def test_noisy_mixture_modes_adjoint(sigma):
+    """Sec. 5.6 noise on every evaluation: with exact gradients the four modes
+    are still found, and no spurious mode is returned (oracle: the same)."""
+    prob = I.mixture4_d2(n=1024)
+    prob.objective.noise_sigma = sigma
+    P = M.Params(n_osc=4, m=5, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=0)
+    model = U.open_ctx(prob, P)
+    fx, ff = _run(model, P.n_osc)
+    mx, mf, negH = MD.significant_modes(prob)
+    frac, worst, _ = MD.recovery(fx, mx, negH)
+    assert frac == 1.0 and fx.shape[0] == 4
     model.close()

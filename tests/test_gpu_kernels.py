@@ -38,16 +38,29 @@ def _torch_x(x):
 
 
 def grad_term_scale(prob, X):
-    """Per-sample magnitude of the terms the gradient sums: sum_k r_k |s_k|
-    for mixtures, 2 |A| |x - c| for the quadratic (inf-norm over coordinates).
-    A binary32 evaluation of a sum has error ~u times this, not times |sum|."""
+    """Per-sample magnitude of the terms the gradient sums, with every
+    difference x - mu counted as |x - mu| + |mu| because the device holds the
+    centres rounded to binary32: sum_k r_k |P_k| (|x - mu_k| + |mu_k|) for
+    mixtures (|P_k| = |L^-T| |L^-1|, diagonal 1/sigma^2), 2 |A| (|x - c| + |c|)
+    for the quadratic (inf-norm over coordinates).  A binary32 evaluation of a
+    sum has error ~u times this, not times |sum|."""
     obj = prob.objective
     if obj.kind == OB.OBJ_QUADRATIC:
         A = obj.arrays["Q"].T @ np.diag(obj.arrays["lam"]) @ obj.arrays["Q"]
-        return (2.0 * np.abs(X - obj.arrays["center"]) @ np.abs(A)).max(axis=1)
-    lc, score = OB._component_logdens(obj, X)
+        c = obj.arrays["center"]
+        return (2.0 * (np.abs(X - c) + np.abs(c)) @ np.abs(A)).max(axis=1)
+    lc, _ = OB._component_logdens(obj, X)
     r = np.exp(lc - OB._lse(lc)[:, None])
-    return np.einsum("nk,nkd->nd", r, np.abs(score)).max(axis=1)
+    A = obj.arrays
+    out = np.zeros(X.shape)
+    for k in range(A["weights"].shape[0]):
+        mag = np.abs(X - A["means"][k]) + np.abs(A["means"][k])
+        if obj.kind == OB.OBJ_MIXTURE_DIAG:
+            out += r[:, k:k + 1] * mag / A["sigmas"][k] ** 2
+        else:
+            Linv = np.abs(np.linalg.inv(A["chol"][k]))
+            out += r[:, k:k + 1] * (mag @ (Linv.T @ Linv))
+    return out.max(axis=1)
 
 
 def softmax_error_scale(prob, X):
@@ -65,16 +78,18 @@ def softmax_error_scale(prob, X):
     r = np.exp(lc - OB._lse(lc)[:, None])
     g = np.einsum("nk,nkd->nd", r, score)
     R = X[:, None, :] - A["means"][None]
+    Rm = np.abs(R) + np.abs(A["means"])[None]          # binary32 centres: |x - mu| + |mu|
     d = X.shape[1]
     if obj.kind == OB.OBJ_MIXTURE_DIAG:
         q = ((R / A["sigmas"][None]) ** 2).sum(axis=2)
-        E = (d + 2) * 1.5 * q
+        qm = (np.abs(R) * Rm / A["sigmas"][None] ** 2).sum(axis=2)
+        E = (d + 2) * (1.5 * q + 2.0 * qm)
     else:
         E = np.empty(lc.shape)
         for k in range(A["weights"].shape[0]):
             Linv = np.linalg.inv(A["chol"][k])
             z = R[:, k, :] @ Linv.T
-            mag = np.abs(R[:, k, :]) @ np.abs(Linv).T
+            mag = Rm[:, k, :] @ np.abs(Linv).T
             E[:, k] = (d + 2) * ((z * z).sum(axis=1) + 2.0 * (np.abs(z) * mag).sum(axis=1))
     E = E + np.abs(lc) + 1.0
     return np.einsum("nk,nkd->nd", r * E, np.abs(score - g[:, None, :])).max(axis=1)
@@ -304,4 +319,26 @@ def test_dedup_edge_cases():
         rem = CH.unpack_bits(model.get(0, CH.FIELD_REMOVED), 33)
         np.testing.assert_array_equal(rem, M.dedup(x, st.f.astype(np.float32), stuck, 1e-3, np.float32))
     assert rem.sum() == 32 and not rem[0]
+    model.close()
+
+
+@pytest.mark.parametrize("sigma", [0.1, 1.0])
+def test_noisy_objective(sigma):
+    """Values carry sigma * N(0,1) keyed by the point (same draw as the oracle's);
+    FD64 differences of the noisy values match the oracle's to binary32 noise
+    rounding; the adjoint gradient is the noise-free one."""
+    prob = I.small_mixture(16, 8, 700, seed=15, box=8.0, noise_sigma=sigma)
+    P = M.Params(grad_mode=M.GRAD_FD64, seed=77)
+    model = U.open_ctx(prob, P)
+    x = prob.x0 * np.float32(0.6)
+    x64 = x.astype(np.float64)
+    f, g = model.eval(0, _torch_x(x), CH.GRAD_FD64)
+    f_ref = M.evaluate(prob, x64, seed=77)
+    assert np.all(np.abs(f.cpu().numpy() - f_ref) <= 1e-5 * (np.abs(f_ref) + 1.0) + 1e-6 * sigma)
+    g_ref = M.fd_gradient(prob, x64, P)
+    err = np.abs(g.cpu().numpy() - g_ref).max(axis=1) / (np.abs(g_ref).max(axis=1) + 1.0)
+    assert err.max() <= 1e-5
+    fa, ga = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT)
+    assert_grad_close(ga.cpu().numpy(), OB.grad(prob.objective, x64), grad_term_scale(prob, x64), 1e-5,
+                      softmax_error_scale(prob, x64))
     model.close()

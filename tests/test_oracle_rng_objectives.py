@@ -109,3 +109,26 @@ def test_hessian_matches_gradient_differences(maker):
                    for e in np.eye(3)], axis=1)
     np.testing.assert_allclose(H, Hn, rtol=1e-5, atol=1e-7 * np.abs(H).max())
     np.testing.assert_allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+
+
+def test_point_noise_draws():
+    """Sec. 5.6 noise: one N(0,1) draw per evaluation point, repeatable for the
+    same point, independent across the FD stencil's neighbouring points."""
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-5, 5, (20000, 3))
+    z = PX.point_noise(0, 0, X)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    np.testing.assert_array_equal(z, PX.point_noise(0, 0, X.copy()))
+    Xp = X.copy()
+    Xp[:, 1] = np.nextafter(X[:, 1].astype(np.float32), np.float32(np.inf)).astype(np.float64)
+    zp = PX.point_noise(0, 0, Xp)
+    assert abs(np.corrcoef(z, zp)[0, 1]) < 0.05
+    assert abs(np.corrcoef(z, PX.point_noise(1, 0, X))[0, 1]) < 0.05
+
+
+def test_noisy_evaluation_adds_scaled_draw():
+    from oracle import method as M
+    p = I.small_mixture(3, 2, 50, seed=4, noise_sigma=0.5)
+    X = p.x0.astype(np.float64)
+    f = M.evaluate(p, X, seed=9)
+    np.testing.assert_allclose(f - OB.value(p.objective, X), 0.5 * PX.point_noise(9, 0, X), rtol=1e-9, atol=1e-9)
