@@ -251,6 +251,42 @@ chisao_status chisao_run_phase(chisao_ctx *c, int32_t prob, int32_t phase, int32
 chisao_status chisao_set_gr_state(chisao_ctx *c, int32_t prob, int32_t enabled,
                                   int32_t noprog, int32_t prev_surv);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free deduplication.
+ *
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory and so cannot create a context -- code
+ * running while a CUDA graph is captured, hosts whose allocator owns the whole
+ * device, loops where a cudaMalloc/cudaFree would synchronize the GPU.  It runs
+ * the Phase 3 decision (a stuck x_j is removed when another stuck x_i ranks
+ * above it, f descending then index ascending, and every |x_ik - x_jk| <
+ * eps_dup, compared in binary32) on caller buffers only, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   x_dev       device float [n][d], row-major, d in 1..CHISAO_MAX_DIM
+ *   f_dev       device float [n]
+ *   stuck_dev   device uint32 [ceil(n/32)] bit mask (bit i%32 of word i/32)
+ *   removed_dev device uint32 [ceil(n/32)] output mask (cleared by the call)
+ *   k_lost_dev  device int32 [1] output count, or NULL
+ *   cuda_stream the cudaStream_t the kernels are queued on (NULL: default)
+ *
+ * Its scratch (the stuck list, CHISAO_DEDUP_NOALLOC_MAX_N ints plus 64
+ * counters, about 1 MiB) is one file-scope device array per GPU, held by every
+ * GPU that loads the library until the process exits.  n above
+ * CHISAO_DEDUP_NOALLOC_MAX_N returns CHISAO_ERR_CAPACITY without launching
+ * anything; bad pointers or sizes return CHISAO_ERR_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current: make that first call before any stream capture.  All
+ * calls on a device share the one array and each call starts by clearing the
+ * counters it needs, so calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race and must be serialized by the
+ * caller.  Asynchronous on cuda_stream. */
+#define CHISAO_DEDUP_NOALLOC_MAX_N (1 << 18)
+chisao_status chisao_dedup_noalloc(const float *x_dev, int32_t d, int64_t n,
+                                   const float *f_dev, const uint32_t *stuck_dev,
+                                   double eps_dup, uint32_t *removed_dev,
+                                   int32_t *k_lost_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

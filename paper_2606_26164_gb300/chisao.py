@@ -27,7 +27,7 @@ MMAX = 10
 EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chisao_step",
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
-           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state"]
+           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc"]
 
 
 class CParams(C.Structure):
@@ -92,6 +92,7 @@ def library() -> C.CDLL:
         lib.chisao_state_set.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
         lib.chisao_run_phase.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         lib.chisao_set_gr_state.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+        lib.chisao_dedup_noalloc.argtypes = [vp, C.c_int32, C.c_int64, vp, vp, C.c_double, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("chisao_default_params", "chisao_last_error", "chisao_destroy"):
                 getattr(lib, name).restype = C.c_int
