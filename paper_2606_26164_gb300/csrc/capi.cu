@@ -166,7 +166,7 @@ void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
   P.lo = b.take<float>(dp);
   P.hi = b.take<float>(dp);
   P.cnt = b.take<Counters>(1);
-  P.partials = b.take<double>((size_t)MAX_PART_BLOCKS * (2 * dp + 2));
+  P.partials = b.take<float2>((size_t)MAX_PART_BLOCKS * (2 * dp + 2));
   P.max_part_blocks = MAX_PART_BLOCKS;
   P.grq = b.take<double>((size_t)d * d);
   size_t n0, n1, n2, n3;

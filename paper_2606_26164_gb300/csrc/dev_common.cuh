@@ -10,13 +10,15 @@
 // Padded coordinates are zero in x, g, the history and every objective
 // parameter, so they never contribute to a dot product or a norm.
 //
-// A sample is processed by a "group" of LPS = dp/2 consecutive lanes of one
-// warp; lane l of the group owns coordinates 2l and 2l+1 (a float2).  Group
-// reductions are xor-butterflies restricted to the group's lane mask, so every
-// lane of the group ends with the bitwise-identical result and all control
-// decisions stay group-uniform.
+// A sample is processed by a "group" of LPS = dp/4 consecutive lanes of one
+// warp; lane l of the group owns the four coordinates 4l .. 4l+3 (a float4),
+// so a warp carries 32/LPS samples (two at d = 64, one per lane at d <= 4).
+// Group reductions are xor-butterflies restricted to the group's lane mask, so
+// every lane of the group ends with the bitwise-identical result and all
+// control decisions stay group-uniform.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -98,7 +100,7 @@ struct ProbDev {
   const float* lo;              // [dp] box, padded with 0
   const float* hi;
   Counters* cnt;
-  double* partials;             // [max_part_blocks][2 dp + 2]
+  float2* partials;             // [max_part_blocks][2 dp + 2] double-single sums
   int max_part_blocks;
   double* grq;                  // Golden Rooster Q [d][d], column-major
   ObjDev obj;
@@ -199,6 +201,47 @@ __device__ __forceinline__ typename Vec2<T>::type ldg2(const T* p) {
   return __ldg(reinterpret_cast<const typename Vec2<T>::type*>(p));
 }
 
+// V consecutive values (V = 1, 2 or 4) through the read-only path / plain loads / stores.
+template <typename T, int V>
+__device__ __forceinline__ void ldg_vec(const T* p, T (&a)[V]) {
+  if constexpr (V == 1) {
+    a[0] = __ldg(p);
+  } else if constexpr (V == 2) {
+    const auto t = ldg2(p);
+    a[0] = t.x; a[1] = t.y;
+  } else if constexpr (std::is_same<T, float>::value) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+  } else {
+    const auto t0 = ldg2(p), t1 = ldg2(p + 2);
+    a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void ld_vec(const float* p, float (&a)[V]) {
+  if constexpr (V == 1) {
+    a[0] = *p;
+  } else if constexpr (V == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    a[0] = t.x; a[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void st_vec(float* p, const float (&a)[V]) {
+  if constexpr (V == 1) {
+    *p = a[0];
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(a[0], a[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+  }
+}
+
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of the two multiply-hi/lo
 // S-boxes with the Weyl key schedule.
@@ -248,17 +291,26 @@ __device__ __forceinline__ void normals4d(uint4 w, double out[4]) {
   out[3] = r1 * s1;
 }
 
-// The two normals of coordinates 2l, 2l+1: block (2l)/4 of the stream, the
-// Box-Muller pair (w0, w1) for even l and (w2, w3) for odd l -- only that pair
-// is transformed.
-__device__ __forceinline__ float2 normals_pair(const StepParams& S, unsigned row, int l, unsigned tag,
-                                               unsigned cycle, unsigned step, unsigned prob, unsigned k) {
-  const uint4 w = rng_words(S, row, (unsigned)(l >> 1), tag, cycle, step, prob, k);
-  const unsigned wa = (l & 1) ? w.z : w.x, wb = (l & 1) ? w.w : w.y;
-  float sn, cs;
-  const float r = sqrtf(-2.0f * logf(u01f(wa)));
-  sincospif(2.0f * u01f(wb), &sn, &cs);
-  return make_float2(r * cs, r * sn);
+// The normals of the lane's coordinates V l .. V l + V - 1 (coordinate j is
+// normal j mod 4 of stream block j / 4): with V = 4 a lane's block is exactly
+// Philox block l; with V = 2 it is half of block l / 2 (one Box-Muller pair).
+template <int V>
+__device__ __forceinline__ void normals_lane(const StepParams& S, unsigned row, int l, unsigned tag,
+                                             unsigned cycle, unsigned step, unsigned prob, unsigned k,
+                                             float (&z)[V]) {
+  static_assert(V == 2 || V == 4, "lanes hold 2 or 4 coordinates");
+  if constexpr (V == 4) {
+    const float4 t = normals4f(rng_words(S, row, (unsigned)l, tag, cycle, step, prob, k));
+    z[0] = t.x; z[1] = t.y; z[2] = t.z; z[3] = t.w;
+  } else {
+    const uint4 w = rng_words(S, row, (unsigned)(l >> 1), tag, cycle, step, prob, k);
+    const unsigned wa = (l & 1) ? w.z : w.x, wb = (l & 1) ? w.w : w.y;
+    float sn, cs;
+    const float r = sqrtf(-2.0f * logf(u01f(wa)));
+    sincospif(2.0f * u01f(wb), &sn, &cs);
+    z[0] = r * cs;
+    z[1] = r * sn;
+  }
 }
 
 // ------------------------------------------------------------------ misc

@@ -2,70 +2,81 @@
 // the scale estimates at the start of Phases 5 and 6, Hands Like Clouds
 // (Eq. 5), anti-convergence (Eq. 6), the L-BFGS direction alone, and plain
 // objective evaluation.  Templated on objective kind, padded dimension DP
-// (lane group of DP/2 lanes per sample) and gradient mode.
+// (a group of DP/V lanes per sample, V = 4 coordinates per lane) and gradient
+// mode.
 #pragma once
 #include "objectives.cuh"
 
 namespace chisao {
 
-constexpr int NT_OBJ = 128;     // threads per block of the per-sample kernels
-constexpr int NT_SCALES = 256;  // threads per block of the scale reduction
+constexpr int VL = 4;              // coordinates per lane
+constexpr int NT_OBJ = 128;        // threads per block of the per-sample kernels
+constexpr int NT_SCALES = 256;     // threads per block of the scale reduction
 constexpr int SCALE_BLOCKS = 608;  // fixed grid of the scale reduction (4 x 152 SMs)
+
+template <int V>
+__device__ __forceinline__ float dotv(const float (&a)[V], const float (&b)[V]) {
+  float s = 0.f;
+#pragma unroll
+  for (int v = 0; v < V; ++v) s = fmaf(a[v], b[v], s);
+  return s;
+}
 
 // L-BFGS two-loop recursion (Nocedal & Wright, Algorithm 7.4) on F = -f with
 // the register-resident history (slot 0 newest), H0 = gam * I, in binary32
 // with group-sum dot products.
-template <int LPS>
-__device__ __forceinline__ void two_loop(const float (&s0)[MMAX], const float (&s1)[MMAX],
-                                         const float (&y0)[MMAX], const float (&y1)[MMAX],
-                                         const float (&rho)[MMAX], int len, float gam, float G0,
-                                         float G1, float& p0, float& p1, const Grp<LPS>& g) {
-  float q0 = G0, q1 = G1;
-  float al[MMAX];
+template <int V, int LPS>
+__device__ __forceinline__ void two_loop(const float (&s)[MMAX][V], const float (&y)[MMAX][V],
+                                         const float (&rho)[MMAX], int len, float gam, const float (&G)[V],
+                                         float (&p)[V], const Grp<LPS>& g) {
+  float q[V], al[MMAX];
+#pragma unroll
+  for (int v = 0; v < V; ++v) q[v] = G[v];
 #pragma unroll
   for (int k = 0; k < MMAX; ++k) {
     al[k] = 0.f;
     if (k < len) {
-      al[k] = rho[k] * g.sum(s0[k] * q0 + s1[k] * q1);
-      q0 = fmaf(-al[k], y0[k], q0);
-      q1 = fmaf(-al[k], y1[k], q1);
+      al[k] = rho[k] * g.sum(dotv<V>(s[k], q));
+#pragma unroll
+      for (int v = 0; v < V; ++v) q[v] = fmaf(-al[k], y[k][v], q[v]);
     }
   }
   const float gm = len > 0 ? gam : 1.f;
-  float r0 = gm * q0, r1 = gm * q1;
+#pragma unroll
+  for (int v = 0; v < V; ++v) q[v] *= gm;
 #pragma unroll
   for (int k = MMAX - 1; k >= 0; --k) {
     if (k < len) {
-      const float be = rho[k] * g.sum(y0[k] * r0 + y1[k] * r1);
-      r0 = fmaf(s0[k], al[k] - be, r0);
-      r1 = fmaf(s1[k], al[k] - be, r1);
+      const float be = rho[k] * g.sum(dotv<V>(y[k], q));
+#pragma unroll
+      for (int v = 0; v < V; ++v) q[v] = fmaf(s[k][v], al[k] - be, q[v]);
     }
   }
-  p0 = -r0;
-  p1 = -r1;
+#pragma unroll
+  for (int v = 0; v < V; ++v) p[v] = -q[v];
 }
 
 // History of sample i into registers; gam = s^T y / y^T y of the newest pair
 // (s^T y = 1 / rho).
-template <int DP, int LPS>
-__device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, int len, float (&s0)[MMAX],
-                                             float (&s1)[MMAX], float (&y0)[MMAX], float (&y1)[MMAX],
-                                             float (&rho)[MMAX], float& gam, const Grp<LPS>& g) {
+template <int DP, int V, int LPS>
+__device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, int len, float (&s)[MMAX][V],
+                                             float (&y)[MMAX][V], float (&rho)[MMAX], float& gam,
+                                             const Grp<LPS>& g) {
 #pragma unroll
   for (int k = 0; k < MMAX; ++k) {
     if (k < len) {
       const size_t o = ((size_t)i * MMAX + k) * DP + j0;
-      const float2 sv = *reinterpret_cast<const float2*>(P.hs + o);
-      const float2 yv = *reinterpret_cast<const float2*>(P.hy + o);
-      s0[k] = sv.x; s1[k] = sv.y; y0[k] = yv.x; y1[k] = yv.y;
+      ld_vec<V>(P.hs + o, s[k]);
+      ld_vec<V>(P.hy + o, y[k]);
       rho[k] = P.hrho[(size_t)i * MMAX + k];
     } else {
-      s0[k] = s1[k] = y0[k] = y1[k] = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) s[k][v] = y[k][v] = 0.f;
       rho[k] = 0.f;
     }
   }
   gam = 1.f;
-  if (len > 0) gam = (1.0f / rho[0]) / g.sum(y0[0] * y0[0] + y1[0] * y1[0]);
+  if (len > 0) gam = (1.0f / rho[0]) / g.sum(dotv<V>(y[0], y[0]));
 }
 
 // ------------------------------------------------------------------ Phase 1
@@ -78,71 +89,86 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 //   exact products in double-single.  A failed search clears the history.
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   using TE = EvalT<GM>;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   EvalCount ec;
   unsigned long long trials = 0, fails = 0;
   if (i < P.n) {
-    const int j0 = 2 * g.l;
-    const float2 xv = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + j0);
-    float x0 = xv.x, x1 = xv.y;
-    const float lo0 = P.lo[j0], lo1 = P.lo[j0 + 1], hi0 = P.hi[j0], hi1 = P.hi[j0 + 1];
+    const int j0 = V * g.l;
+    float x[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
     int len = P.hlen[i];
-    float s0[MMAX], s1[MMAX], y0[MMAX], y1[MMAX], gam;
-    float rho[MMAX];
+    float s[MMAX][V], y[MMAX][V], rho[MMAX], gam;
     const float curv_eps = (float)S.curv_eps;
-    load_history<DP, LPS>(P, i, j0, len, s0, s1, y0, y1, rho, gam, g);
+    load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
     TE F;
-    float G0, G1;
+    float G[V];
     if (fresh) {
-      float a0, a1;
-      const TE f = value_and_gradient<KIND, GM, LPS>(P.obj, S, P.d, x0, x1, a0, a1, g, ec);
-      F = -f;
-      G0 = -a0;
-      G1 = -a1;
+      float a[V];
+      F = -value_and_gradient<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
+#pragma unroll
+      for (int v = 0; v < V; ++v) G[v] = -a[v];
     } else {
       F = -(TE)P.f[i];
-      const float2 gv = *reinterpret_cast<const float2*>(P.g + (size_t)i * DP + j0);
-      G0 = -gv.x;
-      G1 = -gv.y;
+      ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+#pragma unroll
+      for (int v = 0; v < V; ++v) G[v] = -G[v];
     }
     for (int it = 0; it < n_iter; ++it) {
-      const float gn = g.maxf(fmaxf(fabsf(G0), fabsf(G1)));
+      float gl = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) gl = fmaxf(gl, fabsf(G[v]));
+      const float gn = g.maxf(gl);
       if (!(gn > 0.f)) break;                      // exactly stationary (or invalid): stays put
-      float p0, p1;
-      two_loop<LPS>(s0, s1, y0, y1, rho, len, gam, G0, G1, p0, p1, g);
+      float p[V];
+      two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
-      const float gp = g.sum(G0 * p0 + G1 * p1);
+      const float gp = g.sum(dotv<V>(G, p));
       if (!(gp < 0.f)) {                           // not a descent direction: restart
         len = 0;
-        p0 = -G0;
-        p1 = -G1;
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = -G[v];
         a0 = fminf(1.f, 1.f / gn);
       }
       bool acc = false;
-      float xt0 = x0, xt1 = x1, Gt0 = 0.f, Gt1 = 0.f;
+      float xt[V], Gt[V];
       TE Ft = F;
       for (int t = 0; t < S.T_ls; ++t) {
         const float a = ldexpf(a0, -t);
-        const float c0 = clampf(fmaf(a, p0, x0), lo0, hi0);
-        const float c1 = clampf(fmaf(a, p1, x1), lo1, hi1);
+        float c[V], ga[V];
+        TE dl = TE(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          c[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
+          dl += (TE)G[v] * ((TE)c[v] - (TE)x[v]);
+          ga[v] = 0.f;
+        }
         TE ft;
-        float ga0 = 0.f, ga1 = 0.f;
         if constexpr (GM == GRAD_ADJOINT) {
-          ft = value_grad_noisy<KIND>(P.obj, S, c0, c1, ga0, ga1, g);
+          ft = value_grad_noisy<KIND, V, LPS>(P.obj, S, c, ga, g);
           ec.evals += 1;
           ec.grads += 1;
         } else {
-          ft = value_noisy<KIND>(P.obj, params_of<GM>(P.obj), S, (TE)c0, (TE)c1, g);
+          TE ce[V];
+#pragma unroll
+          for (int v = 0; v < V; ++v) ce[v] = (TE)c[v];
+          ft = value_noisy<KIND, TE, V, LPS>(P.obj, params_of<GM>(P.obj), S, ce, g);
           ec.evals += 1;
         }
         ++trials;
-        const TE dec = g.sum((TE)G0 * ((TE)c0 - (TE)x0) + (TE)G1 * ((TE)c1 - (TE)x1));
+        const TE dec = g.sum(dl);
         if (-ft <= F + (TE)S.c1 * dec) {
           acc = true;
-          xt0 = c0; xt1 = c1; Ft = -ft; Gt0 = -ga0; Gt1 = -ga1;
+          Ft = -ft;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            xt[v] = c[v];
+            Gt[v] = -ga[v];
+          }
           break;
         }
       }
@@ -152,38 +178,63 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
         continue;
       }
       if constexpr (GM != GRAD_ADJOINT) {
-        float a0g, a1g;
-        gradient_only<KIND, GM, LPS>(P.obj, S, P.d, xt0, xt1, a0g, a1g, g, ec);
-        Gt0 = -a0g;
-        Gt1 = -a1g;
+        float ag[V];
+        gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xt, ag, g, ec);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Gt[v] = -ag[v];
       }
-      const float sv0 = xt0 - x0, sv1 = xt1 - x1, yv0 = Gt0 - G0, yv1 = Gt1 - G1;
-      float syh, syl;                                // s^T y, exact products + compensated sum
-      ff_dot2(sv0, yv0, sv1, yv1, syh, syl);
-      g.ff_sum(syh, syl);
+      float sv[V], yv[V];
+      float syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sv[v] = xt[v] - x[v];
+        yv[v] = Gt[v] - G[v];
+        const float pr = sv[v] * yv[v];             // exact product as pr + err
+        ff_add(syh, syl, pr, fmaf(sv[v], yv[v], -pr));
+        ss = fmaf(sv[v], sv[v], ss);
+        yy = fmaf(yv[v], yv[v], yy);
+      }
+      g.ff_sum(syh, syl);                            // s^T y, compensated
       const float sy = syh + syl;
-      const float ss = g.sum(sv0 * sv0 + sv1 * sv1);  // sums of squares: no cancellation
-      const float yy = g.sum(yv0 * yv0 + yv1 * yv1);
+      ss = g.sum(ss);                                // sums of squares: no cancellation
+      yy = g.sum(yy);
       if (sy > curv_eps * sqrtf(ss) * sqrtf(yy)) {
 #pragma unroll
         for (int k = MMAX - 1; k > 0; --k) {
-          s0[k] = s0[k - 1]; s1[k] = s1[k - 1]; y0[k] = y0[k - 1]; y1[k] = y1[k - 1]; rho[k] = rho[k - 1];
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            s[k][v] = s[k - 1][v];
+            y[k][v] = y[k - 1][v];
+          }
+          rho[k] = rho[k - 1];
         }
-        s0[0] = sv0; s1[0] = sv1; y0[0] = yv0; y1[0] = yv1;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          s[0][v] = sv[v];
+          y[0][v] = yv[v];
+        }
         rho[0] = 1.0f / sy;
         len = min(len + 1, S.m);
         gam = sy / yy;
       }
-      x0 = xt0; x1 = xt1; F = Ft; G0 = Gt0; G1 = Gt1;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        x[v] = xt[v];
+        G[v] = Gt[v];
+      }
+      F = Ft;
     }
-    *reinterpret_cast<float2*>(P.x + (size_t)i * DP + j0) = make_float2(x0, x1);
-    *reinterpret_cast<float2*>(P.g + (size_t)i * DP + j0) = make_float2(-G0, -G1);
+    float gout[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) gout[v] = -G[v];
+    st_vec<V>(P.x + (size_t)i * DP + j0, x);
+    st_vec<V>(P.g + (size_t)i * DP + j0, gout);
 #pragma unroll
     for (int k = 0; k < MMAX; ++k) {
       if (k < len) {
         const size_t o = ((size_t)i * MMAX + k) * DP + j0;
-        *reinterpret_cast<float2*>(P.hs + o) = make_float2(s0[k], s1[k]);
-        *reinterpret_cast<float2*>(P.hy + o) = make_float2(y0[k], y1[k]);
+        st_vec<V>(P.hs + o, s[k]);
+        st_vec<V>(P.hy + o, y[k]);
         if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = rho[k];
       }
     }
@@ -195,7 +246,6 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
       trials = fails = 0;
     }
   }
-  if (i >= P.n) { ec.evals = ec.grads = 0; trials = fails = 0; }
   block_add_u64<NT_OBJ>(ec.evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(ec.grads, &P.cnt->grads);
   block_add_u64<NT_OBJ>(trials, &P.cnt->ls_trials);
@@ -205,66 +255,68 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
 // Direction only (test hook): p = -H grad F written into g.
 template <int DP>
 __global__ void __launch_bounds__(NT_OBJ) k_direction(ProbDev P) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   if (i >= P.n) return;
-  const int j0 = 2 * g.l;
+  const int j0 = V * g.l;
   const int len = P.hlen[i];
-  float s0[MMAX], s1[MMAX], y0[MMAX], y1[MMAX], gam;
-  float rho[MMAX];
-  load_history<DP, LPS>(P, i, j0, len, s0, s1, y0, y1, rho, gam, g);
-  const float2 gv = *reinterpret_cast<const float2*>(P.g + (size_t)i * DP + j0);
-  float p0, p1;
-  two_loop<LPS>(s0, s1, y0, y1, rho, len, gam, -gv.x, -gv.y, p0, p1, g);
-  *reinterpret_cast<float2*>(P.g + (size_t)i * DP + j0) = make_float2(p0, p1);
+  float s[MMAX][V], y[MMAX][V], rho[MMAX], gam, G[V], p[V];
+  load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
+  ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+#pragma unroll
+  for (int v = 0; v < V; ++v) G[v] = -G[v];
+  two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
+  st_vec<V>(P.g + (size_t)i * DP + j0, p);
 }
 
 // ------------------------------------------------------------------ scales (Phase 5/6 start)
 // Gradient at every unfrozen sample (stored in g) and per-block partial sums
-// (sum x_j, sum x_j^2 per coordinate, sum |g|^2, count) in FP64, reduced in a
-// fixed order so the result is deterministic.
+// (sum x_j, sum x_j^2 per coordinate, sum |g|^2, count), accumulated in
+// double-single and reduced in a fixed order so the result is deterministic.
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   constexpr int GPB = NT_SCALES / LPS;             // groups per block
   constexpr int W = 2 * DP + 2;
-  __shared__ double buf[GPB][W];
+  __shared__ float2 buf[GPB][W];
   const Grp<LPS> g;
   const int grp = threadIdx.x / LPS;
-  const int j0 = 2 * g.l;
+  const int j0 = V * g.l;
   EvalCount ec;
-  // double-single running sums (exact squares via FMA), converted to FP64 once
-  float sx0h = 0.f, sx0l = 0.f, sx1h = 0.f, sx1l = 0.f, sq0h = 0.f, sq0l = 0.f, sq1h = 0.f, sq1l = 0.f;
-  float sgh = 0.f, sgl = 0.f;
+  float sxh[V], sxl[V], sqh[V], sql[V], sgh = 0.f, sgl = 0.f;
+#pragma unroll
+  for (int v = 0; v < V; ++v) sxh[v] = sxl[v] = sqh[v] = sql[v] = 0.f;
   int cnt = 0;
   for (int i = blockIdx.x * GPB + grp; i < P.n; i += gridDim.x * GPB) {
     if (bit_of(P.stuck, i)) continue;
-    const float2 xv = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + j0);
-    float a0, a1;
-    gradient_only<KIND, GM, LPS>(P.obj, S, P.d, xv.x, xv.y, a0, a1, g, ec);
-    *reinterpret_cast<float2*>(P.g + (size_t)i * DP + j0) = make_float2(a0, a1);
-    ff_add(sx0h, sx0l, xv.x, 0.f);
-    ff_add(sx1h, sx1l, xv.y, 0.f);
-    const float p0 = xv.x * xv.x, p1 = xv.y * xv.y;
-    ff_add(sq0h, sq0l, p0, fmaf(xv.x, xv.x, -p0));
-    ff_add(sq1h, sq1l, p1, fmaf(xv.y, xv.y, -p1));
-    ff_add(sgh, sgl, g.sum(a0 * a0 + a1 * a1), 0.f);   // sum of squares: no cancellation
+    float x[V], a[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
+    st_vec<V>(P.g + (size_t)i * DP + j0, a);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      ff_add(sxh[v], sxl[v], x[v], 0.f);
+      const float p2 = x[v] * x[v];
+      ff_add(sqh[v], sql[v], p2, fmaf(x[v], x[v], -p2));
+    }
+    ff_add(sgh, sgl, g.sum(dotv<V>(a, a)), 0.f);    // sum of squares: no cancellation
     ++cnt;
   }
-  buf[grp][j0] = (double)sx0h + (double)sx0l;
-  buf[grp][j0 + 1] = (double)sx1h + (double)sx1l;
-  buf[grp][DP + j0] = (double)sq0h + (double)sq0l;
-  buf[grp][DP + j0 + 1] = (double)sq1h + (double)sq1l;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    buf[grp][j0 + v] = make_float2(sxh[v], sxl[v]);
+    buf[grp][DP + j0 + v] = make_float2(sqh[v], sql[v]);
+  }
   if (g.l == 0) {
-    buf[grp][2 * DP] = (double)sgh + (double)sgl;
-    buf[grp][2 * DP + 1] = (double)cnt;
+    buf[grp][2 * DP] = make_float2(sgh, sgl);
+    buf[grp][2 * DP + 1] = make_float2((float)cnt, 0.f);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < W; t += blockDim.x) {
-    double acc = 0.0;
-    for (int q = 0; q < GPB; ++q) acc += buf[q][t];
-    P.partials[(size_t)blockIdx.x * W + t] = acc;
+    float h = 0.f, l = 0.f;
+    for (int q = 0; q < GPB; ++q) ff_add(h, l, buf[q][t].x, buf[q][t].y);
+    P.partials[(size_t)blockIdx.x * W + t] = make_float2(h, l);
   }
   if (g.l != 0) ec.evals = ec.grads = 0;
   block_add_u64<NT_SCALES>(ec.evals, &P.cnt->evals);
@@ -277,35 +329,37 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
 // step, k = perturbation).  History is cleared (the sample moved).
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   EvalCount ec;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
-    const int j0 = 2 * g.l;
+    const int j0 = V * g.l;
     const unsigned cyc = (unsigned)P.cnt->cycle + 1u;
     const float sigma = P.cnt->sc_sigma, alpha = P.cnt->sc_alpha;
-    const float2 xv = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + j0);
-    float x0 = xv.x, x1 = xv.y;
-    const float lo0 = P.lo[j0], lo1 = P.lo[j0 + 1], hi0 = P.hi[j0], hi1 = P.hi[j0 + 1];
-    const bool v0 = j0 < P.d, v1 = j0 + 1 < P.d;
+    float x[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
     const float invM = 1.0f / (float)S.M;
     for (int t = 0; t < S.n_cloud; ++t) {
-      float acc0 = 0.f, acc1 = 0.f;
+      float acc[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = 0.f;
       for (int k = 0; k < S.M; ++k) {
-        const float2 z = normals_pair(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.prob_index,
-                                      (unsigned)k);
-        const float xp0 = v0 ? fmaf(sigma, z.x, x0) : x0;
-        const float xp1 = v1 ? fmaf(sigma, z.y, x1) : x1;
-        float a0, a1;
-        gradient_only<KIND, GM, LPS>(P.obj, S, P.d, xp0, xp1, a0, a1, g, ec);
-        acc0 += a0;
-        acc1 += a1;
+        float z[V], xp[V], a[V];
+        normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index,
+                        (unsigned)k, z);
+#pragma unroll
+        for (int v = 0; v < V; ++v) xp[v] = (j0 + v < P.d) ? fmaf(sigma, z[v], x[v]) : x[v];
+        gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xp, a, g, ec);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += a[v];
       }
-      x0 = clampf(fmaf(alpha, acc0 * invM, x0), lo0, hi0);
-      x1 = clampf(fmaf(alpha, acc1 * invM, x1), lo1, hi1);
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v] = clampf(fmaf(alpha, acc[v] * invM, x[v]), lo[v], hi[v]);
     }
-    *reinterpret_cast<float2*>(P.x + (size_t)i * DP + j0) = make_float2(x0, x1);
+    st_vec<V>(P.x + (size_t)i * DP + j0, x);
     if (g.l == 0) P.hlen[i] = 0;
     else ec.evals = ec.grads = 0;
   }
@@ -319,29 +373,32 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
 // the scale pass stored.  History is cleared.
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_anti(ProbDev P, StepParams S) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   EvalCount ec;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
-    const int j0 = 2 * g.l;
+    const int j0 = V * g.l;
     const float alpha = P.cnt->sc_alpha, mu = S.mu;
-    const float2 xv = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + j0);
-    const float2 gv = *reinterpret_cast<const float2*>(P.g + (size_t)i * DP + j0);
-    float x0 = xv.x, x1 = xv.y, g0 = gv.x, g1 = gv.y, v0 = 0.f, v1 = 0.f;
-    const float lo0 = P.lo[j0], lo1 = P.lo[j0 + 1], hi0 = P.hi[j0], hi1 = P.hi[j0 + 1];
+    float x[V], gr[V], vel[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.g + (size_t)i * DP + j0, gr);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) vel[v] = 0.f;
     for (int t = 0; t < S.n_anti; ++t) {
-      if (t > 0) gradient_only<KIND, GM, LPS>(P.obj, S, P.d, x0, x1, g0, g1, g, ec);
-      v0 = mu * v0 - alpha * g0;
-      v1 = mu * v1 - alpha * g1;
-      const float n0 = x0 + v0, n1 = x1 + v1;
-      const float c0 = clampf(n0, lo0, hi0), c1 = clampf(n1, lo1, hi1);
-      if (c0 != n0) v0 = 0.f;
-      if (c1 != n1) v1 = 0.f;
-      x0 = c0;
-      x1 = c1;
+      if (t > 0) gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, gr, g, ec);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        vel[v] = mu * vel[v] - alpha * gr[v];
+        const float nx = x[v] + vel[v];
+        const float cx = clampf(nx, lo[v], hi[v]);
+        if (cx != nx) vel[v] = 0.f;
+        x[v] = cx;
+      }
     }
-    *reinterpret_cast<float2*>(P.x + (size_t)i * DP + j0) = make_float2(x0, x1);
+    st_vec<V>(P.x + (size_t)i * DP + j0, x);
     if (g.l == 0) P.hlen[i] = 0;
     else ec.evals = ec.grads = 0;
   }
@@ -354,23 +411,28 @@ __global__ void __launch_bounds__(NT_OBJ) k_anti(ProbDev P, StepParams S) {
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_eval(ProbDev P, StepParams S, const float* __restrict__ x,
                                                  int n, float* __restrict__ fout, float* __restrict__ gout) {
-  constexpr int LPS = DP / 2;
+  constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   if (i >= n) return;
-  const int d = P.d, j0 = 2 * g.l;
-  const float x0 = j0 < d ? x[(size_t)i * d + j0] : 0.f;
-  const float x1 = j0 + 1 < d ? x[(size_t)i * d + j0 + 1] : 0.f;
+  const int d = P.d, j0 = V * g.l;
+  float xv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) xv[v] = (j0 + v < d) ? x[(size_t)i * d + j0 + v] : 0.f;
   EvalCount ec;
   using TE = EvalT<GM>;
   if (gout) {
-    float a0, a1;
-    const TE f = value_and_gradient<KIND, GM, LPS>(P.obj, S, d, x0, x1, a0, a1, g, ec);
-    if (j0 < d) gout[(size_t)i * d + j0] = a0;
-    if (j0 + 1 < d) gout[(size_t)i * d + j0 + 1] = a1;
+    float a[V];
+    const TE f = value_and_gradient<KIND, GM, V, LPS>(P.obj, S, d, xv, a, g, ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (j0 + v < d) gout[(size_t)i * d + j0 + v] = a[v];
     if (fout && g.l == 0) fout[i] = (float)f;
   } else {
-    const TE f = value_noisy<KIND>(P.obj, params_of<GM>(P.obj), S, (TE)x0, (TE)x1, g);
+    TE xe[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) xe[v] = (TE)xv[v];
+    const TE f = value_noisy<KIND, TE, V, LPS>(P.obj, params_of<GM>(P.obj), S, xe, g);
     if (fout && g.l == 0) fout[i] = (float)f;
   }
 }
@@ -379,7 +441,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_eval(ProbDev P, StepParams S, const 
 template <int KIND, int DP, int GM>
 cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, int arg, const EvalArgs* ea,
                              cudaStream_t st) {
-  constexpr int LPS = DP / 2;
+  constexpr int LPS = DP / VL;
   const long long rows = (which == OKID_EVAL) ? ea->n : P.n;
   const unsigned blocks = (unsigned)((rows * LPS + NT_OBJ - 1) / NT_OBJ);
   if (rows <= 0) return cudaSuccess;
@@ -390,14 +452,9 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
     case OKID_DIRECTION:
       k_direction<DP><<<blocks, NT_OBJ, 0, st>>>(P);
       break;
-    case OKID_SCALES: {
-      constexpr int GPB = NT_SCALES / LPS;
-      long long nb = (P.n + GPB - 1) / GPB;
-      if (nb > SCALE_BLOCKS) nb = SCALE_BLOCKS;
-      if (nb > P.max_part_blocks) nb = P.max_part_blocks;
-      k_scales<KIND, DP, GM><<<(unsigned)nb, NT_SCALES, 0, st>>>(P, S);
+    case OKID_SCALES:
+      k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S);
       break;
-    }
     case OKID_HLC:
       k_hlc<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
       break;

@@ -12,9 +12,11 @@
 //    u = A (x - c), f = -(x - c)^T u, grad f = -2 u (one matrix-vector product
 //    gives both).
 //
-// The group's lanes each hold two coordinates; products with a d x d matrix
-// broadcast the other lanes' coordinates with register shuffles and read the
-// matrix as float2/double2 rows that are contiguous across the group.
+// Lane l of a group holds the V consecutive coordinates V l .. V l + V - 1.
+// A product with a d x d matrix walks the rows in blocks of V: the V values of
+// the block are broadcast from their owner lane with register shuffles, and
+// the matrix row is read as one V-wide vector contiguous across the group (all
+// groups of a warp read the same row, so the load is shared).
 #pragma once
 #include <type_traits>
 
@@ -32,19 +34,43 @@ __device__ __forceinline__ void lse_push(T& m, T& s, T lc) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void lse_push_grad(T& m, T& s, T& G0, T& G1, T lc, T sc0, T sc1) {
+template <typename T, int V>
+__device__ __forceinline__ void lse_push_grad(T& m, T& s, T (&G)[V], T lc, const T (&sc)[V]) {
   if (lc > m) {
     const T e = exp(m - lc);
     s = s * e + T(1);
-    G0 = G0 * e + sc0;
-    G1 = G1 * e + sc1;
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = G[v] * e + sc[v];
     m = lc;
   } else {
     const T e = exp(lc - m);
     s += e;
-    G0 = fma(e, sc0, G0);
-    G1 = fma(e, sc1, G1);
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = fma(e, sc[v], G[v]);
+  }
+}
+
+// out[w] = sum_j M[j][V l + w] * r_j over the rows j < d (M row-major, stride dp).
+// One accumulator per output: splitting the chains raised Phase 1's register
+// count from 168 to 205 and cost more in occupancy than it won in ILP
+// (measured: 2.46 vs 2.02 ms at d = 64, N = 65536).
+template <typename T, int V, int LPS>
+__device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&r)[V], T (&out)[V],
+                                           const Grp<LPS>& g) {
+#pragma unroll
+  for (int w = 0; w < V; ++w) out[w] = T(0);
+  const T* col = M + V * g.l;
+  const int nb = (d + V - 1) / V;
+#pragma unroll 2
+  for (int jb = 0; jb < nb; ++jb) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T rj = g.bcast(r[v], jb);
+      T a[V];
+      ldg_vec<T, V>(col + (size_t)(jb * V + v) * dp, a);
+#pragma unroll
+      for (int w = 0; w < V; ++w) out[w] = fma(a[w], rj, out[w]);
+    }
   }
 }
 
@@ -54,35 +80,46 @@ struct Obj;
 // ------------------------------------------------------------ diagonal mixture
 template <>
 struct Obj<OBJ_MIXTURE_DIAG> {
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value(const ObjParams<T>& o, T x0, T x1, const Grp<LPS>& g) {
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value(const ObjParams<T>& o, const T (&x)[V], const Grp<LPS>& g) {
     T m = -CUDART_INF, s = T(0);
-    const T* mu = o.p0 + 2 * g.l;
-    const T* a = o.p1 + 2 * g.l;
     for (int k = 0; k < o.K; ++k) {
-      const auto mk = ldg2(mu + (size_t)k * o.dp);
-      const auto ak = ldg2(a + (size_t)k * o.dp);
-      const T r0 = x0 - mk.x, r1 = x1 - mk.y;
-      const T q = g.sum(ak.x * r0 * r0 + ak.y * r1 * r1);
+      T mk[V], ak[V];
+      ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
+      ldg_vec<T, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
+      T q = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T r = x[v] - mk[v];
+        q = fma(ak[v] * r, r, q);
+      }
+      q = g.sum(q);
       lse_push(m, s, __ldg(o.p2 + k) - T(0.5) * q);
     }
     return m + log(s);
   }
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, T x0, T x1, T& g0, T& g1,
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, const T (&x)[V], T (&gr)[V],
                                                  const Grp<LPS>& g) {
-    T m = -CUDART_INF, s = T(0), G0 = T(0), G1 = T(0);
-    const T* mu = o.p0 + 2 * g.l;
-    const T* a = o.p1 + 2 * g.l;
+    T m = -CUDART_INF, s = T(0), G[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = T(0);
     for (int k = 0; k < o.K; ++k) {
-      const auto mk = ldg2(mu + (size_t)k * o.dp);
-      const auto ak = ldg2(a + (size_t)k * o.dp);
-      const T r0 = x0 - mk.x, r1 = x1 - mk.y;
-      const T q = g.sum(ak.x * r0 * r0 + ak.y * r1 * r1);
-      lse_push_grad(m, s, G0, G1, __ldg(o.p2 + k) - T(0.5) * q, -ak.x * r0, -ak.y * r1);
+      T mk[V], ak[V], sc[V];
+      ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
+      ldg_vec<T, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
+      T q = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T r = x[v] - mk[v];
+        q = fma(ak[v] * r, r, q);
+        sc[v] = -ak[v] * r;
+      }
+      q = g.sum(q);
+      lse_push_grad<T, V>(m, s, G, __ldg(o.p2 + k) - T(0.5) * q, sc);
     }
-    g0 = G0 / s;
-    g1 = G1 / s;
+#pragma unroll
+    for (int v = 0; v < V; ++v) gr[v] = G[v] / s;
     return m + log(s);
   }
 };
@@ -90,54 +127,48 @@ struct Obj<OBJ_MIXTURE_DIAG> {
 // ------------------------------------------------------------ full-covariance mixture
 template <>
 struct Obj<OBJ_MIXTURE_FULL> {
-  template <typename T, int LPS>
-  static __device__ __forceinline__ void whiten(const ObjParams<T>& o, int k, T x0, T x1, T& z0, T& z1,
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ void whiten(const ObjParams<T>& o, int k, const T (&x)[V], T (&z)[V],
                                                 const Grp<LPS>& g) {
-    const auto mk = ldg2(o.p0 + (size_t)k * o.dp + 2 * g.l);
-    const T r0 = x0 - mk.x, r1 = x1 - mk.y;
-    const T* LT = o.p3 + (size_t)k * o.dp * o.dp + 2 * g.l;   // LT[j][i] = L^-1[i][j]
-    z0 = T(0);
-    z1 = T(0);
-#pragma unroll 4
-    for (int j = 0; j < o.d; ++j) {
-      const T rj = g.bcast((j & 1) ? r1 : r0, j >> 1);
-      const auto lt = ldg2(LT + (size_t)j * o.dp);
-      z0 = fma(lt.x, rj, z0);
-      z1 = fma(lt.y, rj, z1);
-    }
+    T mk[V], r[V];
+    ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = x[v] - mk[v];
+    rows_times<T, V, LPS>(o.p3 + (size_t)k * o.dp * o.dp, o.dp, o.d, r, z, g);   // (L^-1)^T rows
   }
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value(const ObjParams<T>& o, T x0, T x1, const Grp<LPS>& g) {
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value(const ObjParams<T>& o, const T (&x)[V], const Grp<LPS>& g) {
     T m = -CUDART_INF, s = T(0);
     for (int k = 0; k < o.K; ++k) {
-      T z0, z1;
-      whiten(o, k, x0, x1, z0, z1, g);
-      const T q = g.sum(z0 * z0 + z1 * z1);
-      lse_push(m, s, __ldg(o.p2 + k) - T(0.5) * q);
+      T z[V];
+      whiten<T, V, LPS>(o, k, x, z, g);
+      T q = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) q = fma(z[v], z[v], q);
+      lse_push(m, s, __ldg(o.p2 + k) - T(0.5) * g.sum(q));
     }
     return m + log(s);
   }
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, T x0, T x1, T& g0, T& g1,
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, const T (&x)[V], T (&gr)[V],
                                                  const Grp<LPS>& g) {
-    T m = -CUDART_INF, s = T(0), G0 = T(0), G1 = T(0);
+    T m = -CUDART_INF, s = T(0), G[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = T(0);
     for (int k = 0; k < o.K; ++k) {
-      T z0, z1;
-      whiten(o, k, x0, x1, z0, z1, g);
-      const T q = g.sum(z0 * z0 + z1 * z1);
-      const T* L = o.p1 + (size_t)k * o.dp * o.dp + 2 * g.l;  // L^-1[i][2l..2l+1]
-      T s0 = T(0), s1 = T(0);
-#pragma unroll 4
-      for (int i = 0; i < o.d; ++i) {
-        const T zi = g.bcast((i & 1) ? z1 : z0, i >> 1);
-        const auto li = ldg2(L + (size_t)i * o.dp);
-        s0 = fma(li.x, zi, s0);
-        s1 = fma(li.y, zi, s1);
-      }
-      lse_push_grad(m, s, G0, G1, __ldg(o.p2 + k) - T(0.5) * q, -s0, -s1);
+      T z[V], sc[V];
+      whiten<T, V, LPS>(o, k, x, z, g);
+      T q = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) q = fma(z[v], z[v], q);
+      q = g.sum(q);
+      rows_times<T, V, LPS>(o.p1 + (size_t)k * o.dp * o.dp, o.dp, o.d, z, sc, g);  // L^-1 rows: (L^-T z)
+#pragma unroll
+      for (int v = 0; v < V; ++v) sc[v] = -sc[v];
+      lse_push_grad<T, V>(m, s, G, __ldg(o.p2 + k) - T(0.5) * q, sc);
     }
-    g0 = G0 / s;
-    g1 = G1 / s;
+#pragma unroll
+    for (int v = 0; v < V; ++v) gr[v] = G[v] / s;
     return m + log(s);
   }
 };
@@ -145,35 +176,30 @@ struct Obj<OBJ_MIXTURE_FULL> {
 // ------------------------------------------------------------ rotated quadratic
 template <>
 struct Obj<OBJ_QUADRATIC> {
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T form(const ObjParams<T>& o, T x0, T x1, T& u0, T& u1,
-                                           const Grp<LPS>& g) {
-    const auto c = ldg2(o.p0 + 2 * g.l);
-    const T r0 = x0 - c.x, r1 = x1 - c.y;
-    const T* A = o.p1 + 2 * g.l;                                // A symmetric: row j = column j
-    u0 = T(0);
-    u1 = T(0);
-#pragma unroll 8
-    for (int j = 0; j < o.d; ++j) {
-      const T rj = g.bcast((j & 1) ? r1 : r0, j >> 1);
-      const auto a = ldg2(A + (size_t)j * o.dp);
-      u0 = fma(a.x, rj, u0);
-      u1 = fma(a.y, rj, u1);
-    }
-    return -g.sum(r0 * u0 + r1 * u1);
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T form(const ObjParams<T>& o, const T (&x)[V], T (&u)[V], const Grp<LPS>& g) {
+    T c[V], r[V];
+    ldg_vec<T, V>(o.p0 + V * g.l, c);
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = x[v] - c[v];
+    rows_times<T, V, LPS>(o.p1, o.dp, o.d, r, u, g);                 // A symmetric: row j = column j
+    T acc = T(0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc = fma(r[v], u[v], acc);
+    return -g.sum(acc);
   }
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value(const ObjParams<T>& o, T x0, T x1, const Grp<LPS>& g) {
-    T u0, u1;
-    return form(o, x0, x1, u0, u1, g);
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value(const ObjParams<T>& o, const T (&x)[V], const Grp<LPS>& g) {
+    T u[V];
+    return form<T, V, LPS>(o, x, u, g);
   }
-  template <typename T, int LPS>
-  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, T x0, T x1, T& g0, T& g1,
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, const T (&x)[V], T (&gr)[V],
                                                  const Grp<LPS>& g) {
-    T u0, u1;
-    const T f = form(o, x0, x1, u0, u1, g);
-    g0 = T(-2) * u0;
-    g1 = T(-2) * u1;
+    T u[V];
+    const T f = form<T, V, LPS>(o, x, u, g);
+#pragma unroll
+    for (int v = 0; v < V; ++v) gr[v] = T(-2) * u[v];
     return f;
   }
 };
@@ -194,20 +220,18 @@ __device__ __forceinline__ unsigned lowbias32(unsigned v) {
   return v;
 }
 
-template <typename T, int LPS>
-__device__ __forceinline__ float point_noise(const ObjDev& O, const StepParams& S, int d, T x0, T x1,
+template <typename T, int V, int LPS>
+__device__ __forceinline__ float point_noise(const ObjDev& O, const StepParams& S, int d, const T (&x)[V],
                                              const Grp<LPS>& g) {
-  const unsigned j0 = 2u * (unsigned)g.l;
   unsigned h1 = 0u, h2 = 0u;
-  if ((int)j0 < d) {
-    const unsigned v = lowbias32(__float_as_uint((float)x0) ^ (j0 * 0x9E3779B9u));
-    h1 += v;
-    h2 ^= v * (2u * j0 + 1u);
-  }
-  if ((int)j0 + 1 < d) {
-    const unsigned v = lowbias32(__float_as_uint((float)x1) ^ ((j0 + 1u) * 0x9E3779B9u));
-    h1 += v;
-    h2 ^= v * (2u * j0 + 3u);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const unsigned j = (unsigned)(V * g.l + v);
+    if ((int)j < d) {
+      const unsigned w = lowbias32(__float_as_uint((float)x[v]) ^ (j * 0x9E3779B9u));
+      h1 += w;
+      h2 ^= w * (2u * j + 1u);
+    }
   }
   h1 = g.sum(h1);
   h2 = g.xor_all(h2);
@@ -217,20 +241,20 @@ __device__ __forceinline__ float point_noise(const ObjDev& O, const StepParams& 
 }
 
 // f (+ noise) at a point, in the precision T of the parameters o.
-template <int KIND, typename T, int LPS>
-__device__ __forceinline__ T value_noisy(const ObjDev& O, const ObjParams<T>& o, const StepParams& S, T x0, T x1,
-                                         const Grp<LPS>& g) {
-  T f = Obj<KIND>::value(o, x0, x1, g);
-  if (O.noise_sigma != 0.f) f += (T)point_noise(O, S, o.d, x0, x1, g);
+template <int KIND, typename T, int V, int LPS>
+__device__ __forceinline__ T value_noisy(const ObjDev& O, const ObjParams<T>& o, const StepParams& S,
+                                         const T (&x)[V], const Grp<LPS>& g) {
+  T f = Obj<KIND>::template value<T, V, LPS>(o, x, g);
+  if (O.noise_sigma != 0.f) f += (T)point_noise<T, V, LPS>(O, S, o.d, x, g);
   return f;
 }
 
 // f (+ noise) and the exact gradient of the noise-free f (the noise is constant in x).
-template <int KIND, int LPS>
-__device__ __forceinline__ float value_grad_noisy(const ObjDev& O, const StepParams& S, float x0, float x1,
-                                                  float& g0, float& g1, const Grp<LPS>& g) {
-  float f = Obj<KIND>::value_grad(O.f32, x0, x1, g0, g1, g);
-  if (O.noise_sigma != 0.f) f += point_noise(O, S, O.f32.d, x0, x1, g);
+template <int KIND, int V, int LPS>
+__device__ __forceinline__ float value_grad_noisy(const ObjDev& O, const StepParams& S, const float (&x)[V],
+                                                  float (&gr)[V], const Grp<LPS>& g) {
+  float f = Obj<KIND>::template value_grad<float, V, LPS>(O.f32, x, gr, g);
+  if (O.noise_sigma != 0.f) f += point_noise<float, V, LPS>(O, S, O.f32.d, x, g);
   return f;
 }
 
@@ -254,63 +278,72 @@ struct EvalCount {
 
 // Central differences on the coordinates j < d: g_j = (f(x + h_j e_j) - f(x - h_j e_j)) / (x+_j - x-_j),
 // the stencil points regenerated one at a time in registers.
-template <int KIND, int GM, int LPS>
-__device__ __forceinline__ void fd_gradient(const ObjDev& O, const StepParams& S, int d, float x0f, float x1f,
-                                            float& g0, float& g1, const Grp<LPS>& g, EvalCount& ec) {
+template <int KIND, int GM, int V, int LPS>
+__device__ __forceinline__ void fd_gradient(const ObjDev& O, const StepParams& S, int d, const float (&xf)[V],
+                                            float (&gr)[V], const Grp<LPS>& g, EvalCount& ec) {
   using TE = EvalT<GM>;
   const auto& o = params_of<GM>(O);
-  const TE x0 = (TE)x0f, x1 = (TE)x1f;
-  g0 = 0.f;
-  g1 = 0.f;
-  for (int j = 0; j < d; ++j) {
-    const int own = j >> 1, comp = j & 1;
-    const TE xj = g.bcast(comp ? x1 : x0, own);
-    const TE hj = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(xj)) : (TE)S.h;
-    const TE xp = xj + hj, xm = xj - hj;
-    const bool mine = (g.l == own);
-    const TE fp = value_noisy<KIND>(O, o, S, (mine && !comp) ? xp : x0, (mine && comp) ? xp : x1, g);
-    const TE fm = value_noisy<KIND>(O, o, S, (mine && !comp) ? xm : x0, (mine && comp) ? xm : x1, g);
-    const TE gj = (fp - fm) / (xp - xm);
-    if (mine) {
-      if (comp) g1 = (float)gj; else g0 = (float)gj;
+  TE x[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    x[v] = (TE)xf[v];
+    gr[v] = 0.f;
+  }
+  const int nb = (d + V - 1) / V;
+  for (int jl = 0; jl < nb; ++jl) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (jl * V + v < d) {
+        const TE xj = g.bcast(x[v], jl);
+        const TE hj = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(xj)) : (TE)S.h;
+        const TE xp = xj + hj, xm = xj - hj;
+        const bool mine = (g.l == jl);
+        TE y[V];
+#pragma unroll
+        for (int w = 0; w < V; ++w) y[w] = x[w];
+        if (mine) y[v] = xp;
+        const TE fp = value_noisy<KIND, TE, V, LPS>(O, o, S, y, g);
+        if (mine) y[v] = xm;
+        const TE fm = value_noisy<KIND, TE, V, LPS>(O, o, S, y, g);
+        if (mine) gr[v] = (float)((fp - fm) / (xp - xm));
+      }
     }
   }
   ec.evals += 2ull * d;
   ec.grads += 1ull;
 }
 
-// Value (in TE) and gradient of f at the float point (x0, x1).
-template <int KIND, int GM, int LPS>
-__device__ __forceinline__ EvalT<GM> value_and_gradient(const ObjDev& O, const StepParams& S, int d, float x0,
-                                                        float x1, float& g0, float& g1, const Grp<LPS>& g,
+// Value (in TE) and gradient of f at the float point x.
+template <int KIND, int GM, int V, int LPS>
+__device__ __forceinline__ EvalT<GM> value_and_gradient(const ObjDev& O, const StepParams& S, int d,
+                                                        const float (&x)[V], float (&gr)[V], const Grp<LPS>& g,
                                                         EvalCount& ec) {
   using TE = EvalT<GM>;
   if constexpr (GM == GRAD_ADJOINT) {
-    float a0, a1;
-    const float f = value_grad_noisy<KIND>(O, S, x0, x1, a0, a1, g);
-    g0 = a0;
-    g1 = a1;
     ec.evals += 1;
     ec.grads += 1;
-    return f;
+    return value_grad_noisy<KIND, V, LPS>(O, S, x, gr, g);
   } else {
-    const TE f = value_noisy<KIND>(O, params_of<GM>(O), S, (TE)x0, (TE)x1, g);
+    TE xe[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) xe[v] = (TE)x[v];
+    const TE f = value_noisy<KIND, TE, V, LPS>(O, params_of<GM>(O), S, xe, g);
     ec.evals += 1;
-    fd_gradient<KIND, GM, LPS>(O, S, d, x0, x1, g0, g1, g, ec);
+    fd_gradient<KIND, GM, V, LPS>(O, S, d, x, gr, g, ec);
     return f;
   }
 }
 
 // Gradient only (the value is not needed).
-template <int KIND, int GM, int LPS>
-__device__ __forceinline__ void gradient_only(const ObjDev& O, const StepParams& S, int d, float x0, float x1,
-                                              float& g0, float& g1, const Grp<LPS>& g, EvalCount& ec) {
+template <int KIND, int GM, int V, int LPS>
+__device__ __forceinline__ void gradient_only(const ObjDev& O, const StepParams& S, int d, const float (&x)[V],
+                                              float (&gr)[V], const Grp<LPS>& g, EvalCount& ec) {
   if constexpr (GM == GRAD_ADJOINT) {
-    Obj<KIND>::value_grad(O.f32, x0, x1, g0, g1, g);
+    Obj<KIND>::template value_grad<float, V, LPS>(O.f32, x, gr, g);
     ec.evals += 1;
     ec.grads += 1;
   } else {
-    fd_gradient<KIND, GM, LPS>(O, S, d, x0, x1, g0, g1, g, ec);
+    fd_gradient<KIND, GM, V, LPS>(O, S, d, x, gr, g, ec);
   }
 }
 

@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
       const uint4 w = rng_words(S, (unsigned)r, 0u, TAG_RM, cyc, 0u, pid, 0u);
       const unsigned U = (unsigned)P.cnt->n_unfrozen;
       const int parent = P.l_unf[(unsigned)(((unsigned long long)w.x * U) >> 32)];
-      const float2 z = normals_pair(S, (unsigned)r, g.l, TAG_RM_DIR, cyc, 0u, pid, 0u);
-      const float z0 = v0 ? z.x : 0.f, z1 = v1 ? z.y : 0.f;
+      float z[2];
+      normals_lane<2>(S, (unsigned)r, g.l, TAG_RM_DIR, cyc, 0u, pid, 0u, z);
+      const float z0 = v0 ? z[0] : 0.f, z1 = v1 ? z[1] : 0.f;
       const float nz = sqrtf(g.sum(z0 * z0 + z1 * z1));
       u0 = z0 / nz;
       u1 = z1 / nz;
@@ -369,39 +370,51 @@ __global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
 //   s = sqrt(mean_j var_j), sigma = c_sigma s, g_rms = sqrt(sum g^2 / (U d)),
 //   alpha = alpha_scale s / max(g_rms, 1e-30)   (fixed values when supplied).
 // 1024 threads = 8 row groups x 128 columns: row group q sums the partial
-// blocks b = q (mod 8) with four independent accumulators, then the 8 row-group
-// sums are added in order q = 0..7 -- a fixed order, so the result does not
-// depend on timing.
+// blocks b = q (mod 8) in double-single arithmetic (on the FP32 pipe: one SM's
+// FP64 rate would make this single block the slowest kernel of the cycle),
+// then the 8 row-group sums are added in order q = 0..7 -- a fixed order, so
+// the result does not depend on timing -- and converted to FP64.
 constexpr int FIN_NT = 1024, FIN_RG = 8, FIN_COLS = FIN_NT / FIN_RG;
 __global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
   const int W = 2 * P.dp + 2;
   extern __shared__ double tot[];                   // [W]
-  __shared__ double part[FIN_RG][FIN_COLS];
+  __shared__ float2 part[FIN_RG][FIN_COLS];
   const int q = threadIdx.x / FIN_COLS, cl = threadIdx.x % FIN_COLS;
   for (int c0 = 0; c0 < W; c0 += FIN_COLS) {
     const int col = c0 + cl;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    float h = 0.f, l = 0.f;
     if (col < W) {
-      int b = q;
-      for (; b + 3 * FIN_RG < nblocks; b += 4 * FIN_RG) {
-        a0 += P.partials[(size_t)b * W + col];
-        a1 += P.partials[(size_t)(b + FIN_RG) * W + col];
-        a2 += P.partials[(size_t)(b + 2 * FIN_RG) * W + col];
-        a3 += P.partials[(size_t)(b + 3 * FIN_RG) * W + col];
+#pragma unroll 4
+      for (int b = q; b < nblocks; b += FIN_RG) {
+        const float2 v = P.partials[(size_t)b * W + col];
+        ff_add(h, l, v.x, v.y);
       }
-      for (; b < nblocks; b += FIN_RG) a0 += P.partials[(size_t)b * W + col];
     }
-    part[q][cl] = (a0 + a1) + (a2 + a3);
+    part[q][cl] = make_float2(h, l);
     __syncthreads();
     if (q == 0 && col < W) {
-      double s = 0.0;
-      for (int r = 0; r < FIN_RG; ++r) s += part[r][cl];
-      tot[col] = s;
+      float sh = 0.f, sl = 0.f;
+      for (int r = 0; r < FIN_RG; ++r) ff_add(sh, sl, part[r][cl].x, part[r][cl].y);
+      tot[col] = (double)sh + (double)sl;
     }
     __syncthreads();
   }
+  // per-coordinate variances by one thread each (warp 0 holds d <= 64 lanes' worth in two passes),
+  // summed in a fixed butterfly order
+  const double U = tot[2 * P.dp + 1];
+  if (threadIdx.x < 32) {
+    const double invU = U > 0.0 ? 1.0 / U : 0.0;
+    double v = 0.0;
+    for (int j = threadIdx.x; j < P.d; j += 32) {
+      const double m = tot[j] * invU;
+      v += fmax(tot[P.dp + j] * invU - m * m, 0.0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) tot[0] = v;                 // column 0 is no longer needed
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double U = tot[2 * P.dp + 1];
     Counters* c = P.cnt;
     if (U <= 0.0) {
       c->sc_count = 0;
@@ -409,11 +422,7 @@ __global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParam
       c->sc_alpha = 0.f;
       return;
     }
-    double vs = 0.0;
-    for (int j = 0; j < P.d; ++j) {
-      const double m = tot[j] / U;
-      vs += fmax(tot[P.dp + j] / U - m * m, 0.0);
-    }
+    const double vs = tot[0];
     const double s = sqrt(vs / P.d);
     const double grms = sqrt(tot[2 * P.dp] / (U * P.d));
     const double sigma = S.sigma_fixed > 0.f ? (double)S.sigma_fixed : (double)S.c_sigma * s;
@@ -527,7 +536,7 @@ cudaError_t launch_reseed(const ProbDev& P, const StepParams& S, cudaStream_t st
 }
 
 int scale_blocks(const ProbDev& P) {
-  const int gpb = 256 / (P.dp / 2);
+  const int gpb = 256 / (P.dp / 4);          // groups per block of k_scales (4 coordinates per lane)
   long long nb = (P.n + gpb - 1) / gpb;
   if (nb > 608) nb = 608;
   if (nb > P.max_part_blocks) nb = P.max_part_blocks;
