@@ -65,7 +65,12 @@ typedef enum {
   /* central differences at h_j = h_rel * max(1, |x_j|), evaluations FP32   */
   CHISAO_GRAD_FD32 = 1,
   /* exact gradient from the objective's hand-written adjoint, FP32         */
-  CHISAO_GRAD_ADJOINT = 2
+  CHISAO_GRAD_ADJOINT = 2,
+  /* full-covariance mixtures: value and exact gradient of the mixture whose
+   * precision factors are L_k^-1 rounded to BF16, on the tcgen05 tensor
+   * cores (BF16 operands, FP32 accumulation and log-sum-exp; the input split
+   * into two BF16 terms; component centres kept exact).  chisao_eval only. */
+  CHISAO_GRAD_ADJOINT_TC = 3
 } chisao_grad_mode;
 
 /* Objective description.  All arrays are host FP64, row-major, read during

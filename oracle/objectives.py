@@ -18,8 +18,33 @@ from scipy.linalg import solve_triangular
 OBJ_MIXTURE_DIAG = 1
 OBJ_MIXTURE_FULL = 2
 OBJ_QUADRATIC = 3
+OBJ_MIXTURE_PREC = 4      # mixture given by precision factors W_k (Sigma_k^-1 = W_k^T W_k)
 
 LOG2PI = np.log(2.0 * np.pi)
+
+
+def bf16_round(a):
+    """Round to bfloat16 (round to nearest, ties to even), returned as float64."""
+    u = np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32)).view(np.uint32).astype(np.uint64)
+    u = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return (u.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def bf16_split(X):
+    """x_hi + x_lo with x_hi = bf16(x), x_lo = bf16(x - x_hi) (x taken in binary32)."""
+    x32 = np.asarray(X, dtype=np.float32).astype(np.float64)
+    hi = bf16_round(x32)
+    return hi + bf16_round(x32 - hi)
+
+
+def tensor_core_objective(obj):
+    """The full-covariance mixture with each precision factor L_k^-1 rounded to
+    bfloat16: the objective the BF16 tensor-core path evaluates (its modes stay
+    at the component centres)."""
+    from paper_2606_26164_gb300.inputs import Objective
+    A = obj.arrays
+    W = np.stack([bf16_round(np.linalg.inv(L)) for L in A["chol"]])
+    return Objective(OBJ_MIXTURE_PREC, obj.d, {"weights": A["weights"], "means": A["means"], "linv": W})
 
 
 def _component_logdens(obj, X):
@@ -34,6 +59,11 @@ def _component_logdens(obj, X):
         Z = R / sig[None]
         logdet = np.log(sig).sum(axis=1)                   # log |Sigma_k|^(1/2)
         score = -R / (sig[None] ** 2)
+    elif obj.kind == OBJ_MIXTURE_PREC:
+        W = A["linv"]
+        Z = np.einsum("kij,nkj->nki", W, R)                # W_k (x - mu_k)
+        score = -np.einsum("kji,nkj->nki", W, Z)           # -W_k^T z_k
+        logdet = -np.log(np.abs(np.einsum("kii->ki", W))).sum(axis=1)
     else:
         L = A["chol"]
         Z = np.empty_like(R)
@@ -82,6 +112,8 @@ def _precisions(obj):
         A = obj.arrays
         if obj.kind == OBJ_MIXTURE_DIAG:
             cache["prec"] = np.stack([np.diag(1.0 / s ** 2) for s in A["sigmas"]])
+        elif obj.kind == OBJ_MIXTURE_PREC:
+            cache["prec"] = np.einsum("kji,kjl->kil", A["linv"], A["linv"])
         else:
             P = []
             for L in A["chol"]:

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libchisao.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE = 0, 1, 2, 3, 4, 5
-GRAD_FD64, GRAD_FD32, GRAD_ADJOINT = 0, 1, 2
+GRAD_FD64, GRAD_FD32, GRAD_ADJOINT, GRAD_ADJOINT_TC = 0, 1, 2, 3
 FIELD_X, FIELD_G, FIELD_F, FIELD_HS, FIELD_HY, FIELD_HRHO, FIELD_HLEN, FIELD_STUCK, FIELD_REMOVED = range(9)
 PHASE_LBFGS, PHASE_FREEZE, PHASE_DEDUP, PHASE_RESEED, PHASE_HLC, PHASE_ANTI, PHASE_DIRECTION, PHASE_LISTS = range(1, 9)
 MMAX = 10

@@ -29,6 +29,7 @@ struct ProbHost {
   StepParams sp{};
   float* gather_x = nullptr;
   float* gather_f = nullptr;
+  uint8_t* tc_weights = nullptr;     // tensor-core operand tiles (full-covariance mixtures)
 };
 
 // Bump allocator over the arena; with a null base it only measures.
@@ -181,11 +182,12 @@ void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
   P.obj.f64.p3 = n3 ? b.take<double>(n3) : nullptr;
   ph.gather_x = b.take<float>(n * d);
   ph.gather_f = b.take<float>(n);
+  if (pr.objective.kind == CHISAO_OBJ_MIXTURE_FULL) ph.tc_weights = b.take<uint8_t>(tc_weight_bytes(pr.objective.n_comp));
 }
 
 // FP64 objective constants on the host, padded to dp (zeros in the padding).
 void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0, std::vector<double>& a1,
-                       std::vector<double>& a2, std::vector<double>& a3) {
+                       std::vector<double>& a2, std::vector<double>& a3, std::vector<double>& linv_all) {
   const int d = pr.d;
   const chisao_objective& o = pr.objective;
   size_t n0, n1, n2, n3;
@@ -208,6 +210,7 @@ void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0
     }
   } else if (o.kind == CHISAO_OBJ_MIXTURE_FULL) {
     std::vector<double> inv((size_t)d * d);
+    linv_all.assign((size_t)o.n_comp * d * d, 0.0);
     for (int k = 0; k < o.n_comp; ++k) {
       const double* L = o.chol + (size_t)k * d * d;
       // inverse of the lower-triangular L by forward substitution, column by column
@@ -227,6 +230,7 @@ void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
           a1[((size_t)k * dp + i) * dp + j] = inv[(size_t)i * d + j];
+          linv_all[((size_t)k * d + i) * d + j] = inv[(size_t)i * d + j];
           a3[((size_t)k * dp + j) * dp + i] = inv[(size_t)i * d + j];
         }
       a2[k] = std::log(o.weights[k]) - ld - d * half_log2pi;
@@ -388,7 +392,7 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
 
   chisao_ctx* c = new chisao_ctx();
   c->params = *params;
-  if (prepare_kernel_attributes() != cudaSuccess) {
+  if (prepare_kernel_attributes() != cudaSuccess || tc_prepare_attributes() != cudaSuccess) {
     delete c;
     return CHISAO_ERR_CUDA;
   }
@@ -418,7 +422,8 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
   Bump b;
   b.base = c->arena;
   c->probs.resize(n_probs);
-  std::vector<double> a0, a1, a2, a3;
+  std::vector<double> a0, a1, a2, a3, linv_all, logw;
+  std::vector<uint8_t> tcw;
   std::vector<float> f0, f1, f2, f3, box;
   auto to32 = [](const std::vector<double>& v, std::vector<float>& o) {
     o.resize(v.size());
@@ -448,7 +453,14 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     P.obj.f32.d = P.obj.f64.d = ph.d;
     P.obj.f32.dp = P.obj.f64.dp = ph.dp;
     ph.sp = make_step_params(*params, ph.d);
-    prepare_objective(pr, ph.dp, a0, a1, a2, a3);
+    prepare_objective(pr, ph.dp, a0, a1, a2, a3, linv_all);
+    if (ph.kind == CHISAO_OBJ_MIXTURE_FULL) {
+      logw.resize(ph.K);
+      for (int k = 0; k < ph.K; ++k) logw[k] = std::log(pr.objective.weights[k]);
+      tc_build_weights(ph.K, ph.d, linv_all.data(), pr.objective.means, logw.data(), tcw);
+      if (cudaMemcpy(ph.tc_weights, tcw.data(), tcw.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = cuda_fail(c, cudaGetLastError(), "tensor-core weight upload");
+    }
     to32(a0, f0); to32(a1, f1); to32(a2, f2); to32(a3, f3);
     auto up = [&](const void* dst, const void* src, size_t bytes) {
       if (bytes && cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -588,8 +600,15 @@ chisao_status chisao_eval(chisao_ctx* c, int32_t prob, const float* x_dev, int64
   chisao_status s = check_prob(c, prob);
   if (s != CHISAO_OK) return s;
   if (n < 0 || n > MAX_N || (n > 0 && !x_dev)) return fail(c, CHISAO_ERR_ARG, "bad points");
-  if (grad_mode < 0 || grad_mode > 2) return fail(c, CHISAO_ERR_ARG, "unknown grad_mode");
+  if (grad_mode < 0 || grad_mode > 3) return fail(c, CHISAO_ERR_ARG, "unknown grad_mode");
   if (n == 0 || (!f_dev && !g_dev)) return CHISAO_OK;
+  const ProbHost& ph = c->probs[prob];
+  if (grad_mode == CHISAO_GRAD_ADJOINT_TC) {
+    if (ph.kind != CHISAO_OBJ_MIXTURE_FULL) return fail(c, CHISAO_ERR_ARG, "tensor-core mode needs a full-covariance mixture");
+    CK(tc_launch_mixfull(x_dev, ph.d, (int)n, ph.d, ph.K, ph.tc_weights, f_dev, g_dev, ph.d, &ph.dev.cnt->err,
+                         c->stream));
+    return CHISAO_OK;
+  }
   EvalArgs ea{x_dev, (int)n, f_dev, g_dev};
   CK(launch_objective(OKID_EVAL, c->probs[prob], grad_mode, 0, &ea, c->stream));
   return CHISAO_OK;

@@ -1,5 +1,8 @@
 // Internal host-side declarations shared by the C ABI and the kernel files.
 #pragma once
+#include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "dev_common.cuh"
@@ -26,6 +29,15 @@ cudaError_t launch_reseed(const ProbDev& P, const StepParams& S, cudaStream_t st
 cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int which, cudaStream_t st);
 cudaError_t launch_gather_modes(const ProbDev& P, float* xo, float* fo, cudaStream_t st);
 cudaError_t prepare_kernel_attributes();
+
+// tensor-core (tcgen05, BF16) full-covariance mixture objective
+cudaError_t tc_prepare_attributes();
+size_t tc_weight_bytes(int K);     // operand tiles of all component groups
+size_t tc_vt_offset(int K);        // byte offset of the V tiles within them
+void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
+                      std::vector<uint8_t>& out);
+cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights,
+                              float* f, float* g, int ldg, int* err, cudaStream_t st);
 int scale_blocks(const ProbDev& P);
 size_t gr_qr_smem(int d);
 

@@ -342,3 +342,58 @@ def test_noisy_objective(sigma):
     assert_grad_close(ga.cpu().numpy(), OB.grad(prob.objective, x64), grad_term_scale(prob, x64), 1e-5,
                       softmax_error_scale(prob, x64))
     model.close()
+
+
+def tc_error_bounds(tco, Xs):
+    """Absolute error bounds of the tensor-core evaluation of f and grad f at the
+    split inputs Xs, against the FP64 evaluation of the same rounded objective:
+    z = W x' - W mu accumulates 128 exact BF16 products in FP32 and subtracts an
+    FP32 bias (|dz| <= 130 u (|W||x'| + |W||mu|)); q, lc, f follow; the gradient
+    adds the BF16 rounding of y = r z (2^-9 relative), the FP32 accumulation of
+    K d products, and the responsibilities' sensitivity to the lc errors."""
+    A = tco.arrays
+    W, mu = A["linv"], A["means"]
+    K, d = mu.shape
+    Wa = np.abs(W)
+    R = Xs[:, None, :] - mu[None]
+    Z = np.einsum("kij,nkj->nki", W, R)
+    lc, score = OB._component_logdens(tco, Xs)
+    r = np.exp(lc - OB._lse(lc)[:, None])
+    f = OB._lse(lc)
+    dz = 130 * U32 * (np.einsum("kij,nj->nki", Wa, np.abs(Xs)) + np.einsum("kij,kj->ki", Wa, np.abs(mu))[None])
+    q = (Z * Z).sum(axis=2)
+    E = (np.abs(Z) * dz).sum(axis=2) + 0.5 * (d + 2) * U32 * q + U32 * (np.abs(lc) + 1.0)
+    tol_f = (r * E).sum(axis=1) + 4 * U32 * (np.abs(f) + 1.0)
+    Wz = np.einsum("kji,nkj->nki", Wa, np.abs(Z))
+    Wdz = np.einsum("kji,nkj->nki", Wa, dz)
+    g = np.einsum("nk,nkd->nd", r, score)
+    tol_g = (np.einsum("nk,nkd->nd", r, (2.0 ** -8 + 4 * K * d * U32) * Wz + Wdz)
+             + np.einsum("nk,nkd->nd", r * E, np.abs(score - g[:, None, :])))
+    return tol_f, tol_g
+
+
+@pytest.mark.parametrize("which", ["k256_d64", "k6_d33"])
+def test_tensor_core_mixture_objective(which):
+    """tcgen05 BF16 evaluation (value and adjoint gradient) of the full-covariance
+    mixture = the FP64 value and gradient of the mixture with BF16-rounded
+    precision factors at the BF16-split input, within FP32 accumulation and the
+    BF16 rounding of the gradient weights; far from and near the modes."""
+    prob = (I.mixture256_d64(n=1031) if which == "k256_d64" else I.small_full_mixture(33, 6, 1031, seed=16))
+    model = U.open_ctx(prob, M.Params(grad_mode=M.GRAD_ADJOINT))
+    rng = np.random.default_rng(11)
+    mu = prob.objective.arrays["means"]
+    near = (mu[rng.integers(0, mu.shape[0], 500)] + rng.normal(0, 0.05, (500, prob.d))).astype(np.float32)
+    x = np.concatenate([prob.x0[:531] * np.float32(0.7), near]).astype(np.float32)
+    f, g = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT_TC)
+    f, g = f.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    assert model.counters(0) is not None
+    tco = OB.tensor_core_objective(prob.objective)
+    Xs = OB.bf16_split(x)
+    f_ref, g_ref = OB.value(tco, Xs), OB.grad(tco, Xs)
+    tol_f, tol_g = tc_error_bounds(tco, Xs)
+    assert np.all(np.abs(f - f_ref) <= tol_f), (np.abs(f - f_ref) / tol_f).max()
+    assert np.all(np.abs(g - g_ref) <= tol_g), (np.abs(g - g_ref) / tol_g).max()
+    # value-only launch agrees with the value of the value+gradient launch
+    fv, _ = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT_TC, want_grad=False)
+    np.testing.assert_array_equal(fv.cpu().numpy(), f.astype(np.float32))
+    model.close()

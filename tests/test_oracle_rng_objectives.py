@@ -126,6 +126,31 @@ def test_point_noise_draws():
     assert abs(np.corrcoef(z, PX.point_noise(1, 0, X))[0, 1]) < 0.05
 
 
+def test_bf16_rounding_and_split():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    a = np.concatenate([rng.normal(0, 10, 5000), [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(OB.bf16_round(a), ref)
+    assert OB.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0            # tie goes to even
+    x = rng.uniform(-20, 20, 5000).astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(OB.bf16_split(x) - x) <= 2.0 ** -17 * np.abs(x))
+
+
+def test_precision_factor_mixture_matches_cholesky_form():
+    p = I.small_full_mixture(5, 4, 30, seed=12)
+    A = p.objective.arrays
+    W = np.stack([np.linalg.inv(L) for L in A["chol"]])
+    pobj = I.Objective(OB.OBJ_MIXTURE_PREC, 5, {"weights": A["weights"], "means": A["means"], "linv": W})
+    X = p.x0.astype(np.float64)
+    np.testing.assert_allclose(OB.value(pobj, X), OB.value(p.objective, X), rtol=1e-12)
+    np.testing.assert_allclose(OB.grad(pobj, X), OB.grad(p.objective, X), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(OB.hessian(pobj, X[0]), OB.hessian(p.objective, X[0]), rtol=1e-9, atol=1e-12)
+    # the rounded factors keep every component's peak at its centre
+    tco = OB.tensor_core_objective(p.objective)
+    np.testing.assert_allclose(OB.grad(tco, A["means"][:1]), OB.grad(p.objective, A["means"][:1]), atol=1e-6)
+
+
 def test_noisy_evaluation_adds_scaled_draw():
     from oracle import method as M
     p = I.small_mixture(3, 2, 50, seed=4, noise_sigma=0.5)
