@@ -133,7 +133,8 @@ typedef struct {
   int32_t rm_min_unfrozen; /* Repulse Monkey iff >= this many unfrozen (5)    */
   int32_t gr_patience;     /* Golden Rooster off after this many idle generations (2) */
   int32_t use_graph;       /* 1: capture each cycle in a CUDA graph           */
-  int32_t reserved;
+  int32_t n_refine;        /* CHISAO_GRAD_ADJOINT_TC: FP32 L-BFGS steps on the
+                              survivors after the last cycle (exact objective) */
 } chisao_params;
 
 /* Per-problem counters accumulated on the device since create. */
@@ -239,8 +240,10 @@ typedef enum {
   CHISAO_PHASE_HLC = 5,       /* Phase 5 for cycle number arg                 */
   CHISAO_PHASE_ANTI = 6,      /* Phase 6                                       */
   CHISAO_PHASE_DIRECTION = 7, /* write the L-BFGS direction p into G         */
-  CHISAO_PHASE_LISTS = 8      /* stuck &= ~removed, then the free / unfrozen /
+  CHISAO_PHASE_LISTS = 8,     /* stuck &= ~removed, then the free / unfrozen /
                                  survivor lists from the two masks            */
+  CHISAO_PHASE_REFINE = 9     /* arg FP32 L-BFGS steps (exact objective) on the
+                                 survivor list                                */
 } chisao_phase;
 
 /* Padded row length dp and m_max used by the raw fields of problem prob. */

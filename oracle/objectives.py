@@ -19,6 +19,7 @@ OBJ_MIXTURE_DIAG = 1
 OBJ_MIXTURE_FULL = 2
 OBJ_QUADRATIC = 3
 OBJ_MIXTURE_PREC = 4      # mixture given by precision factors W_k (Sigma_k^-1 = W_k^T W_k)
+OBJ_MIXTURE_PREC_SPLIT = 5   # the same, evaluated at the BF16-split input x_hi + x_lo
 
 LOG2PI = np.log(2.0 * np.pi)
 
@@ -37,14 +38,16 @@ def bf16_split(X):
     return hi + bf16_round(x32 - hi)
 
 
-def tensor_core_objective(obj):
+def tensor_core_objective(obj, split=True):
     """The full-covariance mixture with each precision factor L_k^-1 rounded to
-    bfloat16: the objective the BF16 tensor-core path evaluates (its modes stay
-    at the component centres)."""
+    bfloat16 (its modes stay at the component centres); with ``split`` it is
+    evaluated at the BF16-split input -- the objective the BF16 tensor-core path
+    evaluates, value and gradient."""
     from paper_2606_26164_gb300.inputs import Objective
     A = obj.arrays
     W = np.stack([bf16_round(np.linalg.inv(L)) for L in A["chol"]])
-    return Objective(OBJ_MIXTURE_PREC, obj.d, {"weights": A["weights"], "means": A["means"], "linv": W})
+    kind = OBJ_MIXTURE_PREC_SPLIT if split else OBJ_MIXTURE_PREC
+    return Objective(kind, obj.d, {"weights": A["weights"], "means": A["means"], "linv": W})
 
 
 def _component_logdens(obj, X):
@@ -53,13 +56,15 @@ def _component_logdens(obj, X):
     A = obj.arrays
     w, mu = A["weights"], A["means"]
     K, d = mu.shape
+    if obj.kind == OBJ_MIXTURE_PREC_SPLIT:
+        X = bf16_split(X)
     R = X[:, None, :] - mu[None, :, :]                     # (N, K, d)
     if obj.kind == OBJ_MIXTURE_DIAG:
         sig = A["sigmas"]
         Z = R / sig[None]
         logdet = np.log(sig).sum(axis=1)                   # log |Sigma_k|^(1/2)
         score = -R / (sig[None] ** 2)
-    elif obj.kind == OBJ_MIXTURE_PREC:
+    elif obj.kind in (OBJ_MIXTURE_PREC, OBJ_MIXTURE_PREC_SPLIT):
         W = A["linv"]
         Z = np.einsum("kij,nkj->nki", W, R)                # W_k (x - mu_k)
         score = -np.einsum("kji,nkj->nki", W, Z)           # -W_k^T z_k
@@ -112,7 +117,7 @@ def _precisions(obj):
         A = obj.arrays
         if obj.kind == OBJ_MIXTURE_DIAG:
             cache["prec"] = np.stack([np.diag(1.0 / s ** 2) for s in A["sigmas"]])
-        elif obj.kind == OBJ_MIXTURE_PREC:
+        elif obj.kind in (OBJ_MIXTURE_PREC, OBJ_MIXTURE_PREC_SPLIT):
             cache["prec"] = np.einsum("kji,kjl->kil", A["linv"], A["linv"])
         else:
             P = []

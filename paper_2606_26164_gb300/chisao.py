@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libchisao.so")
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE = 0, 1, 2, 3, 4, 5
 GRAD_FD64, GRAD_FD32, GRAD_ADJOINT, GRAD_ADJOINT_TC = 0, 1, 2, 3
 FIELD_X, FIELD_G, FIELD_F, FIELD_HS, FIELD_HY, FIELD_HRHO, FIELD_HLEN, FIELD_STUCK, FIELD_REMOVED = range(9)
-PHASE_LBFGS, PHASE_FREEZE, PHASE_DEDUP, PHASE_RESEED, PHASE_HLC, PHASE_ANTI, PHASE_DIRECTION, PHASE_LISTS = range(1, 9)
+(PHASE_LBFGS, PHASE_FREEZE, PHASE_DEDUP, PHASE_RESEED, PHASE_HLC, PHASE_ANTI, PHASE_DIRECTION, PHASE_LISTS,
+ PHASE_REFINE) = range(1, 10)
 MMAX = 10
 
 EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chisao_step",
@@ -37,7 +38,7 @@ class CParams(C.Structure):
                 ("alpha", C.c_double), ("sigma", C.c_double), ("c_sigma", C.c_double),
                 ("alpha_scale", C.c_double), ("h", C.c_double), ("h_rel", C.c_double), ("c1", C.c_double),
                 ("curv_eps", C.c_double), ("seed", C.c_uint64), ("rm_min_unfrozen", C.c_int32),
-                ("gr_patience", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+                ("gr_patience", C.c_int32), ("use_graph", C.c_int32), ("n_refine", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)

@@ -30,6 +30,8 @@ struct ProbHost {
   float* gather_x = nullptr;
   float* gather_f = nullptr;
   uint8_t* tc_weights = nullptr;     // tensor-core operand tiles (full-covariance mixtures)
+  bool tc = false;                   // the cycle runs on the tensor-core objective
+  ExtBuf ext{};                      // its buffers
 };
 
 // Bump allocator over the arena; with a null base it only measures.
@@ -91,7 +93,8 @@ chisao_status validate_params(const chisao_params* p, std::string& why) {
   if (p->m < 1 || p->m > CHISAO_MAX_MEMORY) { why = "m must be in [1, 10]"; return CHISAO_ERR_ARG; }
   if (p->T_ls < 1 || p->T_ls > 126) { why = "T_ls must be in [1, 126]"; return CHISAO_ERR_ARG; }
   if (p->n_cloud > 255) { why = "n_cloud must be <= 255"; return CHISAO_ERR_ARG; }
-  if (p->grad_mode < 0 || p->grad_mode > 2) { why = "unknown grad_mode"; return CHISAO_ERR_ARG; }
+  if (p->grad_mode < 0 || p->grad_mode > 3) { why = "unknown grad_mode"; return CHISAO_ERR_ARG; }
+  if (p->n_refine < 0) { why = "n_refine must be >= 0"; return CHISAO_ERR_ARG; }
   if (!(p->eps_grad > 0) || !(p->eps_dup > 0)) { why = "eps_grad and eps_dup must be > 0"; return CHISAO_ERR_ARG; }
   if (!(p->delta > 0 && p->delta < 1)) { why = "delta must be in (0, 1)"; return CHISAO_ERR_ARG; }
   if (!(p->h > 0) || !(p->h_rel > 0) || !(p->c1 > 0 && p->c1 < 1)) { why = "h, h_rel > 0 and c1 in (0,1) required"; return CHISAO_ERR_ARG; }
@@ -146,7 +149,7 @@ size_t obj_elems(const chisao_problem& pr, int dp, size_t* n0, size_t* n1, size_
 }
 
 // Carve one problem's buffers (measure-only when b.base is null).
-void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
+void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm, ProbHost& ph) {
   const int d = pr.d, dp = pad_dim(d);
   const size_t n = (size_t)pr.n, nw = (n + 31) / 32;
   ProbDev& P = ph.dev;
@@ -183,6 +186,21 @@ void layout_problem(Bump& b, const chisao_problem& pr, ProbHost& ph) {
   ph.gather_x = b.take<float>(n * d);
   ph.gather_f = b.take<float>(n);
   if (pr.objective.kind == CHISAO_OBJ_MIXTURE_FULL) ph.tc_weights = b.take<uint8_t>(tc_weight_bytes(pr.objective.n_comp));
+  ph.tc = prm.grad_mode == CHISAO_GRAD_ADJOINT_TC;
+  if (ph.tc) {
+    ExtBuf& E = ph.ext;
+    E.p = b.take<float>(n * dp);
+    E.xt = b.take<float>(n * dp);
+    E.ft = b.take<float>(n);
+    E.gt = b.take<float>(n * dp);
+    E.a0 = b.take<float>(n);
+    E.list[0] = b.take<int>(n);
+    E.list[1] = b.take<int>(n);
+    E.cnt = b.take<int>((size_t)prm.T_ls + 1);
+    E.xp = b.take<float>((size_t)prm.M * n * dp);
+    E.gp = b.take<float>((size_t)prm.M * n * dp);
+    E.vel = b.take<float>(n * dp);
+  }
 }
 
 // FP64 objective constants on the host, padded to dp (zeros in the padding).
@@ -271,6 +289,7 @@ StepParams make_step_params(const chisao_params& p, int d) {
   s.curv_eps = p.curv_eps;
   s.seed_lo = (unsigned)(p.seed & 0xffffffffu);
   s.seed_hi = (unsigned)(p.seed >> 32);
+  s.n_refine = p.n_refine;
   return s;
 }
 
@@ -302,10 +321,91 @@ cudaError_t enqueue_explore(const ProbHost& ph, cudaStream_t st) {
   return launch_objective(OKID_ANTI, ph, ph.sp.grad_mode, 0, nullptr, st);
 }
 
+// ---- the tensor-core objective: batched evaluations around per-sample kernels
+cudaError_t tc_eval_rows(const ProbHost& ph, const float* x, float* f, float* g, int rows, const int* idx,
+                         const int* count, cudaStream_t st) {
+  return tc_launch_mixfull(x, ph.dp, rows, ph.d, ph.K, ph.tc_weights, f, g, ph.dp, &ph.dev.cnt->err, st, idx,
+                           count);
+}
+
+// n_iter L-BFGS iterations (Phase 1) with T_ls line-search rounds each.
+cudaError_t enqueue_phase1_tc(const ProbHost& ph, int n_iter, bool fresh, cudaStream_t st) {
+  const ProbDev& P = ph.dev;
+  const ExtBuf& E = ph.ext;
+  cudaError_t e;
+  if (fresh && (e = tc_eval_rows(ph, P.x, P.f, P.g, P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
+  for (int it = 0; it < n_iter; ++it) {
+    if ((e = cudaMemsetAsync(E.cnt, 0, sizeof(int) * (ph.sp.T_ls + 1), st)) != cudaSuccess) return e;
+    if ((e = launch_ext(EXT_DIR, P, ph.sp, E, (fresh && it == 0) ? 1 : 0, st)) != cudaSuccess) return e;
+    for (int t = 0; t < ph.sp.T_ls; ++t) {
+      if ((e = tc_eval_rows(ph, E.xt, E.ft, E.gt, P.n, E.list[t & 1], E.cnt + t, st)) != cudaSuccess) return e;
+      if ((e = launch_ext(EXT_ACCEPT, P, ph.sp, E, t, st)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Phase 5 (scale pass + HLC) with all M perturbations evaluated in one launch.
+cudaError_t enqueue_hlc_tc(const ProbHost& ph, cudaStream_t st) {
+  const ProbDev& P = ph.dev;
+  const ExtBuf& E = ph.ext;
+  cudaError_t e;
+  if ((e = tc_eval_rows(ph, P.x, nullptr, P.g, P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_ext(EXT_SCALES, P, ph.sp, E, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_scales(P, ph.sp, 0, st)) != cudaSuccess) return e;
+  for (int t = 0; t < ph.sp.n_cloud; ++t) {
+    if ((e = launch_ext(EXT_HLC_POINTS, P, ph.sp, E, t, st)) != cudaSuccess) return e;
+    if ((e = tc_eval_rows(ph, E.xp, nullptr, E.gp, ph.sp.M * P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_ext(EXT_HLC_STEP, P, ph.sp, E, t, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Phase 6 (scale pass + momentum steps).
+cudaError_t enqueue_anti_tc(const ProbHost& ph, cudaStream_t st) {
+  const ProbDev& P = ph.dev;
+  const ExtBuf& E = ph.ext;
+  cudaError_t e;
+  if ((e = tc_eval_rows(ph, P.x, nullptr, P.g, P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_ext(EXT_SCALES, P, ph.sp, E, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_scales(P, ph.sp, 1, st)) != cudaSuccess) return e;
+  for (int t = 0; t < ph.sp.n_anti; ++t) {
+    if (t > 0 && (e = tc_eval_rows(ph, P.x, nullptr, P.g, P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_ext(EXT_ANTI_STEP, P, ph.sp, E, t, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// FP32 polish of the survivors with the exact objective (after the last cycle).
+cudaError_t enqueue_refine(const ProbHost& ph, int n_iter, cudaStream_t st) {
+  if (n_iter <= 0) return cudaSuccess;
+  return launch_objective(OKID_REFINE, ph, GRAD_ADJOINT, n_iter, nullptr, st);
+}
+
+cudaError_t enqueue_cycle_tc(const ProbHost& ph, bool last, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_cycle_begin(ph.dev, st)) != cudaSuccess) return e;
+  if ((e = enqueue_phase1_tc(ph, ph.sp.n_conv, true, st)) != cudaSuccess) return e;
+  if ((e = launch_freeze(ph.dev, ph.sp, st)) != cudaSuccess) return e;
+  if ((e = launch_dedup(ph.dev, ph.sp, st)) != cudaSuccess) return e;
+  if (!last) {
+    if ((e = launch_reseed(ph.dev, ph.sp, st)) != cudaSuccess) return e;
+    if ((e = enqueue_hlc_tc(ph, st)) != cudaSuccess) return e;
+    if ((e = enqueue_anti_tc(ph, st)) != cudaSuccess) return e;
+  } else if ((e = enqueue_refine(ph, ph.sp.n_refine, st)) != cudaSuccess) {
+    return e;
+  }
+  return launch_cycle_end(ph.dev, st);
+}
+
 // One oscillation cycle (Algorithm 1) of every problem.
 cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
   cudaError_t e;
   for (const ProbHost& ph : c->probs) {
+    if (ph.tc) {
+      if ((e = enqueue_cycle_tc(ph, last, c->stream)) != cudaSuccess) return e;
+      continue;
+    }
     if ((e = launch_cycle_begin(ph.dev, c->stream)) != cudaSuccess) return e;                  // release all
     if ((e = launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, ph.sp.n_conv, nullptr, c->stream)) != cudaSuccess)
       return e;                                                                                 // Phase 1
@@ -354,6 +454,7 @@ void chisao_default_params(chisao_params* p) {
   p->rm_min_unfrozen = 5;
   p->gr_patience = 2;
   p->use_graph = 1;
+  p->n_refine = 10;
 }
 
 chisao_status chisao_arena_bytes(const chisao_problem* probs, int32_t n_probs, const chisao_params* params,
@@ -365,7 +466,9 @@ chisao_status chisao_arena_bytes(const chisao_problem* probs, int32_t n_probs, c
   for (int q = 0; q < n_probs; ++q) {
     if (validate_problem(&probs[q], why) != CHISAO_OK) return CHISAO_ERR_ARG;
     ProbHost ph;
-    layout_problem(b, probs[q], ph);
+    if (params->grad_mode == CHISAO_GRAD_ADJOINT_TC && probs[q].objective.kind != CHISAO_OBJ_MIXTURE_FULL)
+      return CHISAO_ERR_ARG;                     // the tensor-core mode needs full-covariance mixtures
+    layout_problem(b, probs[q], *params, ph);
   }
   *bytes = (b.off + ALIGN - 1) / ALIGN * ALIGN;
   return CHISAO_OK;
@@ -438,7 +541,7 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     ph.n = pr.n;
     ph.kind = pr.objective.kind;
     ph.K = pr.objective.n_comp;
-    layout_problem(b, pr, ph);
+    layout_problem(b, pr, *params, ph);
     ProbDev& P = ph.dev;
     P.d = ph.d;
     P.dp = ph.dp;
@@ -684,7 +787,13 @@ chisao_status chisao_run_phase(chisao_ctx* c, int32_t prob, int32_t phase, int32
   cudaStream_t st = c->stream;
   switch (phase) {
     case CHISAO_PHASE_LBFGS:
-      CK(launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, arg, nullptr, st));
+      if (ph.tc)
+        CK(enqueue_phase1_tc(ph, arg < 0 ? -arg : arg, arg >= 0, st));
+      else
+        CK(launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, arg, nullptr, st));
+      break;
+    case CHISAO_PHASE_REFINE:
+      CK(enqueue_refine(ph, arg, st));
       break;
     case CHISAO_PHASE_FREEZE:
       CK(launch_cycle_begin(ph.dev, st));
@@ -703,11 +812,19 @@ chisao_status chisao_run_phase(chisao_ctx* c, int32_t prob, int32_t phase, int32
       break;
     case CHISAO_PHASE_HLC:
       CK(launch_set_cycle(ph.dev, arg - 1, st));
+      if (ph.tc) {
+        CK(enqueue_hlc_tc(ph, st));
+        break;
+      }
       CK(launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st));
       CK(launch_finalize_scales(ph.dev, ph.sp, 0, st));
       CK(launch_objective(OKID_HLC, ph, ph.sp.grad_mode, 0, nullptr, st));
       break;
     case CHISAO_PHASE_ANTI:
+      if (ph.tc) {
+        CK(enqueue_anti_tc(ph, st));
+        break;
+      }
       CK(launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st));
       CK(launch_finalize_scales(ph.dev, ph.sp, 1, st));
       CK(launch_objective(OKID_ANTI, ph, ph.sp.grad_mode, 0, nullptr, st));

@@ -107,13 +107,34 @@ struct ProbDev {
 };
 
 struct StepParams {
-  int n_conv, n_anti, n_cloud, M, m, T_ls, grad_mode, rm_min, gr_patience;
+  int n_conv, n_anti, n_cloud, M, m, T_ls, grad_mode, rm_min, gr_patience, n_refine;
   float eps_grad, eps_dup, log_delta, mu, alpha_fixed, sigma_fixed, c_sigma, alpha_scale;
   double h, h_rel, c1, curv_eps;
   unsigned seed_lo, seed_hi;
 };
 
-enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5 };
+enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5,
+                   OKID_REFINE = 6 };
+
+// Gradient mode of the scale pass when the gradient was computed by a batched
+// evaluator and is already in g.
+constexpr int GRAD_GIVEN = 9;
+
+// Buffers of the batched-evaluator (tensor-core) path.
+struct ExtBuf {
+  float* p;        // [n][dp] search directions
+  float* xt;       // [n][dp] trial points
+  float* ft;       // [n] trial values
+  float* gt;       // [n][dp] trial gradients
+  float* a0;       // [n] initial steps
+  int* list[2];    // pending samples of the current / next line-search round
+  int* cnt;        // [T_ls + 1] pending count of each round
+  float* xp;       // [M n][dp] HLC perturbed points
+  float* gp;       // [M n][dp] their gradients
+  float* vel;      // [n][dp] anti-convergence velocity
+};
+enum ExtKernelId { EXT_DIR = 0, EXT_ACCEPT = 1, EXT_HLC_POINTS = 2, EXT_HLC_STEP = 3, EXT_ANTI_STEP = 4,
+                   EXT_SCALES = 5 };
 
 // Caller points for plain objective evaluation.
 struct EvalArgs {

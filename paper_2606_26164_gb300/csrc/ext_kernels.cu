@@ -1,0 +1,293 @@
+// Phases 1, 5 and 6 around a *batched* objective evaluator (the tensor-core
+// mixture objective): the objective cannot run inside a per-sample kernel (a
+// CTA-wide GEMM needs 128 points in lockstep), so each phase is split into
+// per-sample kernels that write the points to evaluate and consume the values
+// and gradients the evaluator returns.
+//
+// Phase 1 per L-BFGS iteration (same rules as the fused k_phase1):
+//   k_ext_dir     two-loop direction from the history in HBM, descent check,
+//                 first trial point x + alpha0 p (box-projected), pending list;
+//   T_ls rounds of [evaluator on the pending trial points -> k_ext_accept]:
+//                 Armijo test; accepted samples take the point, value and
+//                 gradient and push (s, y, rho) into the history; the others
+//                 get the next, halved trial point on the next round's list.
+//   Lists are filled with atomics; every result is per sample, so the order of
+//   a list changes nothing.
+// Phase 5: k_ext_hlc_points writes x + sigma z_k for all M perturbations, the
+//   evaluator returns their gradients, k_ext_hlc_step averages and steps.
+// Phase 6: k_ext_anti_step applies the momentum step to the gradient the
+//   evaluator returned for the current points.
+#include "host.h"
+#include "obj_kernels.cuh"
+
+namespace chisao {
+
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, ExtBuf E, int count_start) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  unsigned long long ev = 0;
+  if (i < P.n) {
+    const int j0 = V * g.l;
+    float G[V], x[V], lo[V], hi[V];
+    ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = -G[v];
+    float gl = 0.f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) gl = fmaxf(gl, fabsf(G[v]));
+    const float gn = g.maxf(gl);
+    if (gn > 0.f) {
+      int len = P.hlen[i];
+      float s[MMAX][V], y[MMAX][V], rho[MMAX], gam, p[V];
+      load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
+      two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
+      float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
+      if (!(g.sum(dotv<V>(G, p)) < 0.f)) {           // not a descent direction: restart
+        len = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = -G[v];
+        a0 = fminf(1.f, 1.f / gn);
+        if (g.l == 0) P.hlen[i] = 0;
+      }
+      ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+      ld_vec<V>(P.lo + j0, lo);
+      ld_vec<V>(P.hi + j0, hi);
+      float c[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) c[v] = clampf(fmaf(a0, p[v], x[v]), lo[v], hi[v]);
+      st_vec<V>(E.p + (size_t)i * DP + j0, p);
+      st_vec<V>(E.xt + (size_t)i * DP + j0, c);
+      if (g.l == 0) {
+        E.a0[i] = a0;
+        E.list[0][atomicAdd(&E.cnt[0], 1)] = i;
+      }
+    }
+    if (g.l == 0 && count_start) ev = 1;
+  }
+  block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
+}
+
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, ExtBuf E, int t) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int cur = t & 1;
+  unsigned long long tr = 0, fl = 0;
+  if (jj < E.cnt[t]) {
+    const int i = E.list[cur][jj];
+    const int j0 = V * g.l;
+    float x[V], G[V], c[V], Gt[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+    ld_vec<V>(E.xt + (size_t)i * DP + j0, c);
+    ld_vec<V>(E.gt + (size_t)i * DP + j0, Gt);
+    float dl = 0.f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      G[v] = -G[v];
+      Gt[v] = -Gt[v];
+      dl += G[v] * (c[v] - x[v]);
+    }
+    const float F = -P.f[i], Ft = -E.ft[i];
+    const float dec = g.sum(dl);
+    if (g.l == 0) tr = 1;
+    if (Ft <= F + (float)S.c1 * dec) {
+      float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sv[v] = c[v] - x[v];
+        yv[v] = Gt[v] - G[v];
+        const float pr = sv[v] * yv[v];
+        ff_add(syh, syl, pr, fmaf(sv[v], yv[v], -pr));
+        ss = fmaf(sv[v], sv[v], ss);
+        yy = fmaf(yv[v], yv[v], yy);
+      }
+      g.ff_sum(syh, syl);
+      const float sy = syh + syl;
+      ss = g.sum(ss);
+      yy = g.sum(yy);
+      if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy)) {
+        const int len = P.hlen[i];
+        for (int k = min(len, S.m - 1); k > 0; --k) {      // shift the pairs one slot back
+          const size_t o = ((size_t)i * MMAX + k) * DP + j0;
+          float a[V], b[V];
+          ld_vec<V>(P.hs + o - DP, a);
+          ld_vec<V>(P.hy + o - DP, b);
+          st_vec<V>(P.hs + o, a);
+          st_vec<V>(P.hy + o, b);
+          if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = P.hrho[(size_t)i * MMAX + k - 1];
+        }
+        const size_t o0 = (size_t)i * MMAX * DP + j0;
+        st_vec<V>(P.hs + o0, sv);
+        st_vec<V>(P.hy + o0, yv);
+        if (g.l == 0) {
+          P.hrho[(size_t)i * MMAX] = 1.0f / sy;
+          P.hlen[i] = min(len + 1, S.m);
+        }
+      }
+      float gout[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) gout[v] = -Gt[v];
+      st_vec<V>(P.x + (size_t)i * DP + j0, c);
+      st_vec<V>(P.g + (size_t)i * DP + j0, gout);
+      if (g.l == 0) P.f[i] = -Ft;
+    } else if (t + 1 < S.T_ls) {
+      float p[V], lo[V], hi[V];
+      ld_vec<V>(E.p + (size_t)i * DP + j0, p);
+      ld_vec<V>(P.lo + j0, lo);
+      ld_vec<V>(P.hi + j0, hi);
+      const float a = ldexpf(E.a0[i], -(t + 1));
+#pragma unroll
+      for (int v = 0; v < V; ++v) c[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
+      st_vec<V>(E.xt + (size_t)i * DP + j0, c);
+      if (g.l == 0) E.list[cur ^ 1][atomicAdd(&E.cnt[t + 1], 1)] = i;
+    } else {
+      if (g.l == 0) {
+        P.hlen[i] = 0;
+        fl = 1;
+      }
+    }
+  }
+  block_add_u64<NT_OBJ>(tr, &P.cnt->ls_trials);
+  block_add_u64<NT_OBJ>(tr, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(tr, &P.cnt->grads);
+  block_add_u64<NT_OBJ>(fl, &P.cnt->ls_fail);
+}
+
+// x + sigma z_k for k < M (row k n + i of xp); frozen samples write x itself.
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_hlc_points(ProbDev P, StepParams S, ExtBuf E, int t) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  if (i >= P.n) return;
+  const int j0 = V * g.l;
+  float x[V];
+  ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+  const bool moving = !bit_of(P.stuck, i) && P.cnt->sc_count > 0;
+  const unsigned cyc = (unsigned)P.cnt->cycle + 1u;
+  const float sigma = P.cnt->sc_sigma;
+  for (int k = 0; k < S.M; ++k) {
+    float xp[V];
+    if (moving) {
+      float z[V];
+      normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index, (unsigned)k, z);
+#pragma unroll
+      for (int v = 0; v < V; ++v) xp[v] = (j0 + v < P.d) ? fmaf(sigma, z[v], x[v]) : x[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) xp[v] = x[v];
+    }
+    st_vec<V>(E.xp + ((size_t)k * P.n + i) * DP + j0, xp);
+  }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_hlc_step(ProbDev P, StepParams S, ExtBuf E) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  unsigned long long ev = 0;
+  if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
+    const int j0 = V * g.l;
+    const float alpha = P.cnt->sc_alpha, invM = 1.0f / (float)S.M;
+    float x[V], lo[V], hi[V], acc[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int k = 0; k < S.M; ++k) {
+      float a[V];
+      ld_vec<V>(E.gp + ((size_t)k * P.n + i) * DP + j0, a);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] += a[v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = clampf(fmaf(alpha, acc[v] * invM, x[v]), lo[v], hi[v]);
+    st_vec<V>(P.x + (size_t)i * DP + j0, x);
+    if (g.l == 0) {
+      P.hlen[i] = 0;
+      ev = (unsigned long long)S.M;
+    }
+  }
+  block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
+}
+
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_anti_step(ProbDev P, StepParams S, ExtBuf E, int t) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  unsigned long long ev = 0;
+  if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
+    const int j0 = V * g.l;
+    const float alpha = P.cnt->sc_alpha, mu = S.mu;
+    float x[V], gr[V], vel[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.g + (size_t)i * DP + j0, gr);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
+    if (t == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) vel[v] = 0.f;
+    } else {
+      ld_vec<V>(E.vel + (size_t)i * DP + j0, vel);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      vel[v] = mu * vel[v] - alpha * gr[v];
+      const float nx = x[v] + vel[v];
+      const float cx = clampf(nx, lo[v], hi[v]);
+      if (cx != nx) vel[v] = 0.f;
+      x[v] = cx;
+    }
+    st_vec<V>(P.x + (size_t)i * DP + j0, x);
+    st_vec<V>(E.vel + (size_t)i * DP + j0, vel);
+    if (g.l == 0) {
+      P.hlen[i] = 0;
+      ev = t > 0 ? 1ull : 0ull;
+    }
+  }
+  block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
+}
+
+// ------------------------------------------------------------------ launchers
+template <int DP>
+static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& S, const ExtBuf& E, int arg,
+                                 cudaStream_t st) {
+  constexpr int LPS = DP / VL;
+  const unsigned blocks = (unsigned)(((long long)P.n * LPS + NT_OBJ - 1) / NT_OBJ);
+  switch (which) {
+    case EXT_DIR: k_ext_dir<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
+    case EXT_ACCEPT: k_ext_accept<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
+    case EXT_HLC_POINTS: k_ext_hlc_points<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
+    case EXT_HLC_STEP: k_ext_hlc_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E); break;
+    case EXT_ANTI_STEP: k_ext_anti_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
+    case EXT_SCALES:
+      k_scales<OBJ_MIXTURE_FULL, DP, GRAD_GIVEN><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const ExtBuf& E, int arg,
+                       cudaStream_t st) {
+  switch (P.dp) {
+    case 4: return ext_launch_dp<4>(which, P, S, E, arg, st);
+    case 8: return ext_launch_dp<8>(which, P, S, E, arg, st);
+    case 16: return ext_launch_dp<16>(which, P, S, E, arg, st);
+    case 32: return ext_launch_dp<32>(which, P, S, E, arg, st);
+    case 64: return ext_launch_dp<64>(which, P, S, E, arg, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace chisao

@@ -30,14 +30,20 @@ cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int wh
 cudaError_t launch_gather_modes(const ProbDev& P, float* xo, float* fo, cudaStream_t st);
 cudaError_t prepare_kernel_attributes();
 
+// Phases 1, 5 and 6 around a batched evaluator (ext_kernels.cu)
+cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const ExtBuf& E, int arg,
+                       cudaStream_t st);
+
 // tensor-core (tcgen05, BF16) full-covariance mixture objective
 cudaError_t tc_prepare_attributes();
 size_t tc_weight_bytes(int K);     // operand tiles of all component groups
 size_t tc_vt_offset(int K);        // byte offset of the V tiles within them
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out);
+// n: rows (or the capacity when count is given); idx/count: optional row list and device count
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights,
-                              float* f, float* g, int ldg, int* err, cudaStream_t st);
+                              float* f, float* g, int ldg, int* err, cudaStream_t st,
+                              const int* idx = nullptr, const int* count = nullptr);
 int scale_blocks(const ProbDev& P);
 size_t gr_qr_smem(int d);
 

@@ -87,15 +87,20 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 //   wins (alpha0 = 1, or min(1, 1/|grad F|_inf) on an empty history); new
 //   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y|, s^T y summed from
 //   exact products in double-single.  A failed search clears the history.
+// With a row list (rows, *nrows on the device) only those samples iterate:
+// the final FP32 refinement of the survivors.
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh) {
+__global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
+                                                   const int* __restrict__ rows, const int* __restrict__ nrows) {
   constexpr int V = VL, LPS = DP / V;
   using TE = EvalT<GM>;
   const Grp<LPS> g;
-  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int gi = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const bool act = rows ? gi < *nrows : gi < P.n;
+  const int i = rows ? (act ? rows[gi] : 0) : gi;
   EvalCount ec;
   unsigned long long trials = 0, fails = 0;
-  if (i < P.n) {
+  if (act) {
     const int j0 = V * g.l;
     float x[V], lo[V], hi[V];
     ld_vec<V>(P.x + (size_t)i * DP + j0, x);
@@ -292,8 +297,14 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
     if (bit_of(P.stuck, i)) continue;
     float x[V], a[V];
     ld_vec<V>(P.x + (size_t)i * DP + j0, x);
-    gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
-    st_vec<V>(P.g + (size_t)i * DP + j0, a);
+    if constexpr (GM == GRAD_GIVEN) {
+      ld_vec<V>(P.g + (size_t)i * DP + j0, a);          // computed by the batched evaluator
+      ec.evals += 1;
+      ec.grads += 1;
+    } else {
+      gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
+      st_vec<V>(P.g + (size_t)i * DP + j0, a);
+    }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       ff_add(sxh[v], sxl[v], x[v], 0.f);
@@ -447,7 +458,11 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
   if (rows <= 0) return cudaSuccess;
   switch (which) {
     case OKID_PHASE1:
-      k_phase1<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S, arg < 0 ? -arg : arg, arg >= 0 ? 1 : 0);
+      k_phase1<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S, arg < 0 ? -arg : arg, arg >= 0 ? 1 : 0, nullptr,
+                                                        nullptr);
+      break;
+    case OKID_REFINE:
+      k_phase1<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S, arg, 1, P.l_surv, &P.cnt->n_surv);
       break;
     case OKID_DIRECTION:
       k_direction<DP><<<blocks, NT_OBJ, 0, st>>>(P);

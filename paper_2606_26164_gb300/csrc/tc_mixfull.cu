@@ -135,9 +135,11 @@ __device__ __forceinline__ uint16_t f2bf(float f) {  // round to nearest even
 __device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
 struct TcArgs {
-  const float* x;         // [n][ldx] points (FP32, first 64 columns used, zero padded)
+  const float* x;         // [.][ldx] points (FP32, first d columns used)
   int ldx;
-  int n;
+  int n;                  // rows when count is null
+  const int* idx;         // optional row list: launch row i is x row idx[i] (outputs too)
+  const int* count;       // optional device row count (overrides n; CTAs past it exit)
   int d;
   int ngroups;            // component groups of 4
   const uint8_t* wblk;    // [ngroups][WBLK_BYTES]  W tile (canonical), bias [4][64] f32, c [4] f32
@@ -159,8 +161,11 @@ __global__ void __launch_bounds__(TM, 1) k_tc_mixfull(TcArgs a) {
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int t = threadIdx.x, warp = t >> 5;
-  const int row = blockIdx.x * TM + t;
-  const bool live = row < a.n;
+  const int nrows = a.count ? *a.count : a.n;
+  if ((int)blockIdx.x * TM >= nrows) return;          // whole CTA past the rows: nothing to do
+  const int lrow = blockIdx.x * TM + t;
+  const bool live = lrow < nrows;
+  const int row = live ? (a.idx ? a.idx[lrow] : lrow) : 0;
 
   // ---- set-up: barriers, tensor memory, the split BF16 input tile
   if (t == 0) {
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(TM, 1) k_tc_mixfull(TcArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   {
-    const float* xr = a.x + (size_t)(live ? row : 0) * a.ldx;
+    const float* xr = a.x + (size_t)row * a.ldx;
     for (int k8 = 0; k8 < DK / 8; ++k8) {
       uint16_t hi[8], lo[8];
 #pragma unroll
@@ -397,9 +402,9 @@ void tc_build_weights(int K, int d, const double* linv, const double* mu, const 
 }
 
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights, float* f,
-                              float* g, int ldg, int* err, cudaStream_t st) {
+                              float* g, int ldg, int* err, cudaStream_t st, const int* idx, const int* count) {
   if (n <= 0) return cudaSuccess;
-  tc::TcArgs a{x, ldx, n, d, (K + 3) / 4, weights, weights + tc_vt_offset(K), f, g, ldg, err};
+  tc::TcArgs a{x, ldx, n, idx, count, d, (K + 3) / 4, weights, weights + tc_vt_offset(K), f, g, ldg, err};
   const unsigned grid = (unsigned)((n + tc::TM - 1) / tc::TM);
   if (g)
     tc::k_tc_mixfull<true><<<grid, tc::TM, tc::SMEM_BYTES, st>>>(a);

@@ -195,3 +195,18 @@ def test_noisy_mixture_modes_adjoint(sigma):
     frac, worst, _ = MD.recovery(fx, mx, negH)
     assert frac == 1.0 and fx.shape[0] == 4
     model.close()
+
+
+def test_tensor_core_cycle_with_fp32_refinement():
+    """d=64, K=256 full-covariance mixture on the BF16 tensor-core objective
+    (Phases 1, 5, 6), then n_refine FP32 L-BFGS steps with the exact objective on
+    the survivors after the last cycle: every returned point is a local maximum
+    of the exact objective to 1e-3 local sigmas."""
+    prob = I.mixture256_d64(n=8192)
+    P = M.Params(n_osc=2, n_conv=100, m=10, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=4)
+    model = U.open_ctx(prob, P, grad_mode=CH.GRAD_ADJOINT_TC, n_refine=10)
+    fx, ff = _run(model, P.n_osc)
+    c = model.counters(0)
+    assert fx.shape[0] >= 3 and c["cycles"] == 2 and c["evals"] > 0
+    assert np.all(_local_mode_errors(prob, fx) <= 1e-3)
+    model.close()

@@ -387,9 +387,9 @@ def test_tensor_core_mixture_objective(which):
     f, g = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT_TC)
     f, g = f.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
     assert model.counters(0) is not None
-    tco = OB.tensor_core_objective(prob.objective)
+    tco = OB.tensor_core_objective(prob.objective)          # evaluated at the BF16-split input
     Xs = OB.bf16_split(x)
-    f_ref, g_ref = OB.value(tco, Xs), OB.grad(tco, Xs)
+    f_ref, g_ref = OB.value(tco, x.astype(np.float64)), OB.grad(tco, x.astype(np.float64))
     tol_f, tol_g = tc_error_bounds(tco, Xs)
     assert np.all(np.abs(f - f_ref) <= tol_f), (np.abs(f - f_ref) / tol_f).max()
     assert np.all(np.abs(g - g_ref) <= tol_g), (np.abs(g - g_ref) / tol_g).max()

@@ -12,6 +12,8 @@ import pytest
 
 import gpu_util as U
 from oracle import method as M
+from oracle import objectives as OB
+from oracle import philox as PX
 from paper_2606_26164_gb300 import chisao as CH
 from paper_2606_26164_gb300 import inputs as I
 
@@ -145,3 +147,80 @@ def test_anti_convergence(mode, d, n_anti):
     _check_moves(got, ref, st, sens, 1e-5)
     np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
     model.close()
+
+
+# ----------------------------------------------------------------------- tensor-core mode
+# The tensor-core path evaluates the mixture with BF16-rounded precision factors
+# at the BF16-split input (oracle: objectives.tensor_core_objective); its
+# gradients carry the error bound test_gpu_kernels.tc_error_bounds.
+
+def _tc_problem(N, seed):
+    prob = I.small_full_mixture(24, 10, N, seed=seed, box=6.0)
+    tprob = I.Problem(prob.d, prob.n, prob.lo, prob.hi, OB.tensor_core_objective(prob.objective), prob.x0,
+                      prob.eps_grad, prob.sigma_mode)
+    return prob, tprob
+
+
+def _tc_grad_bound(tprob, X):
+    from test_gpu_kernels import tc_error_bounds
+    return tc_error_bounds(tprob.objective, OB.bf16_split(X))[1].max(axis=1)
+
+
+def test_tc_lbfgs_iteration():
+    prob, tprob = _tc_problem(700, 31)
+    P = M.Params(m=6, grad_mode=M.GRAD_ADJOINT)
+    st = M.new_state(prob.x0, P.m)
+    M.lbfgs_iterations(tprob, st, P, 3)
+    st = U.rounded(st)
+    st.f = M.evaluate(tprob, st.x)
+    st.g = M.gradient(tprob, st.x, P)
+    st = U.rounded(st)
+    model = U.open_ctx(prob, P, grad_mode=CH.GRAD_ADJOINT_TC)
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_LBFGS, -1)
+    got = U.read_state(model, prob, P.m)
+    ref = _copy(st)
+    M.lbfgs_iterations(tprob, ref, P, 1, fresh_gradient=False)
+    step = np.abs(ref.x - st.x).max(axis=1)
+    err = np.abs(got.x - ref.x).max(axis=1)
+    ok = err <= 1e-5 * step + 4e-7 * np.abs(st.x).max(axis=1)
+    assert (~ok).sum() <= 0.02 * prob.n, ((~ok).sum(), err[~ok][:5], step[~ok][:5])
+    gerr = np.abs(got.g - OB.grad(tprob.objective, got.x)).max(axis=1)
+    assert np.all(gerr <= _tc_grad_bound(tprob, got.x))
+    assert np.all(got.hlen[ok] == ref.hlen[ok])
+    model.close()
+
+
+def test_tc_hlc_and_anti_single_steps():
+    prob, tprob = _tc_problem(901, 32)
+    rng = np.random.default_rng(5)
+    for phase in ("hlc", "anti"):
+        P = M.Params(n_cloud=1, n_anti=1, M=8, grad_mode=M.GRAD_ADJOINT, seed=7)
+        st = M.new_state(prob.x0 * np.float32(0.7), P.m)
+        st.stuck = rng.random(prob.n) < 0.3
+        st = U.rounded(st)
+        model = U.open_ctx(prob, P, grad_mode=CH.GRAD_ADJOINT_TC)
+        U.write_state(model, prob, st)
+        ref = _copy(st)
+        unf = np.flatnonzero(~st.stuck)
+        # the step size alpha = 0.1 s / g_rms uses the tensor-core gradient at x: relative error <= rms(bound)/g_rms
+        g_rms = np.sqrt(np.mean(OB.grad(tprob.objective, st.x[unf]) ** 2))
+        rel_alpha = np.sqrt(np.mean(_tc_grad_bound(tprob, st.x[unf]) ** 2)) / g_rms
+        if phase == "hlc":
+            model.run_phase(0, CH.PHASE_HLC, 2)
+            sigma, alpha = M.hlc(tprob, ref, P, cycle=2)
+            bound = np.zeros(prob.n)
+            for k in range(8):
+                zk = PX.normal_rows(7, unf, prob.d, PX.TAG_HLC, 2, 0, 0, k)
+                bound[unf] += _tc_grad_bound(tprob, st.x[unf] + sigma * zk) / 8.0
+        else:
+            model.run_phase(0, CH.PHASE_ANTI)
+            alpha = M.anti_converge(tprob, ref, P)
+            bound = _tc_grad_bound(tprob, st.x)
+        got = U.read_state(model, prob, P.m)
+        move = np.abs(ref.x - st.x).max(axis=1)
+        err = np.abs(got.x - ref.x).max(axis=1)
+        tol = 1.01 * alpha * bound + (1e-5 + 1.01 * rel_alpha) * move + 2e-6 * np.abs(st.x).max(axis=1)
+        assert np.all(err <= tol), (phase, (err / tol).max())
+        np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
+        model.close()
