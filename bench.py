@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--grad", default="adjoint", choices=["adjoint", "fd64", "fd32"])
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override the population size (profiling cases)")
+    ap.add_argument("--tc-steps", type=int, default=2, help="cycles of the full-covariance tensor-core leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -226,6 +227,39 @@ def gpu_timed(model, steps, warmup):
     return e0.elapsed_time(e1) / 1e3, c0, c1
 
 
+def full_covariance_leg(CH, steps, n_osc):
+    import torch
+    prob = make_problem("mixture256_d64", 0)
+    N, d, K = prob.n, prob.d, prob.objective.n_comp
+    res = {"N": N, "d": d, "K": K}
+    for mode, label, nsteps in ((CH.GRAD_ADJOINT_TC, "bf16_tensor_core", steps), (CH.GRAD_ADJOINT, "fp32", 1)):
+        prm = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=mode, seed=0)
+        m4 = CH.Chisao([prob], prm)
+        t, c0, c1 = gpu_timed(m4, nsteps, 1)
+        res[label] = {"value": N * nsteps / t, "unit": "sample-cycles/s", "ms_per_step": 1e3 * t / nsteps,
+                      "evals_per_s": (c1["evals"] - c0["evals"]) / t, "steps": nsteps}
+        if mode == CH.GRAD_ADJOINT_TC:
+            x = torch.from_numpy(prob.x0).cuda()
+            m4.eval(0, x, mode)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(m4._stream)
+            reps = 5
+            for _ in range(reps):
+                m4.eval(0, x, mode)
+            e1.record(m4._stream)
+            e1.synchronize()
+            tk = e0.elapsed_time(e1) / 1e3 / reps
+            # value pass (split input: K = 2d) + gradient pass (recomputed forward + backward GEMM)
+            flop = N * (2 * (2 * d) * (d * K) * 2 + 2 * (d * K) * d)
+            _, bf16_peak, src = peaks()
+            res["roofline_tc"] = {"kernel": "k_tc_mixfull<true>", "bound": "tensor", "achieved": flop / tk / 1e12,
+                                  "peak": bf16_peak, "unit": "TFLOP/s", "frac": flop / tk / 1e12 / bf16_peak,
+                                  "peak_source": f"{src} bf16 dense (MEASURED_PEAKS.json burst)",
+                                  "launch_ms": 1e3 * tk, "points_per_launch": N}
+        m4.close()
+    return res
+
+
 def main():
     args = parse()
     if args.cpu_leg:
@@ -312,6 +346,10 @@ def main():
                        "evals_per_s": (f1["evals"] - f0["evals"]) / tf, "ms_per_step": 1e3 * tf / args.fd_steps,
                        "steps": args.fd_steps}
         mfd.close()
+        # --- the d=64, K=256 full-covariance mixture at N=65536: BF16 tensor-core cycle vs FP32 cycle,
+        #     and the tensor-core objective kernel against the measured BF16 peak
+        if args.workload == "quadratic_d64" and args.tc_steps > 0:
+            out["mixture256_d64"] = full_covariance_leg(CH, args.tc_steps, n_osc)
         # --- end to end through the C ABI: pinned host population in, modes out, every step
         xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
         xh.copy_(torch.from_numpy(prob.x0))
