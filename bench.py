@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="quadratic_d64")
-    ap.add_argument("--grad", default="adjoint", choices=["adjoint", "fd64", "fd32"])
+    ap.add_argument("--grad", default="adjoint", choices=["adjoint", "fd64", "fd32", "adjoint_tc"])
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override the population size (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=2, help="cycles of the full-covariance tensor-core leg")
@@ -50,7 +50,19 @@ def parse():
     return ap.parse_args()
 
 
-GRAD = {"fd64": 0, "fd32": 1, "adjoint": 2}
+GRAD = {"fd64": 0, "fd32": 1, "adjoint": 2, "adjoint_tc": 3}
+
+
+def launches_per_step(params, tc, d):
+    """Kernel launches in one non-final cycle of one problem."""
+    if not tc:
+        return KERNELS_PER_STEP
+    n_conv = params.n_conv or max(10, int(np.ceil(3 * np.log2(d))))
+    # cycle begin + first evaluation, per L-BFGS iteration one direction kernel and T_ls
+    # (evaluation, acceptance) pairs, freeze/dedup/reseed (9), HLC and anti with their scale
+    # passes, cycle end
+    return (2 + n_conv * (1 + 2 * params.T_ls) + 9 + (3 + 3 * params.n_cloud)
+            + (2 + 2 * params.n_anti) + 1)
 
 
 def make_problem(name, seed):
@@ -227,6 +239,12 @@ def gpu_timed(model, steps, warmup):
     return e0.elapsed_time(e1) / 1e3, c0, c1
 
 
+def tc_executed_flop_per_point(d, K):
+    """Tensor-core flop the kernel issues per point: the value pass over the split input
+    (K = 2 x 64) and the gradient pass's recomputed forward plus G = Y V."""
+    return 2 * (2 * 64) * (64 * K) * 2 + 2 * (64 * K) * 64
+
+
 def full_covariance_leg(CH, steps, n_osc):
     import torch
     prob = make_problem("mixture256_d64", 0)
@@ -249,11 +267,14 @@ def full_covariance_leg(CH, steps, n_osc):
             e1.record(m4._stream)
             e1.synchronize()
             tk = e0.elapsed_time(e1) / 1e3 / reps
-            # value pass (split input: K = 2d) + gradient pass (recomputed forward + backward GEMM)
-            flop = N * (2 * (2 * d) * (d * K) * 2 + 2 * (d * K) * d)
+            # algorithmic: the dense forward contraction (d x dK per point) and the adjoint's
+            # backward contraction (dK x d), 2 flop per multiply-add
+            flop = N * (2 * d * (d * K) + 2 * (d * K) * d)
+            executed = N * tc_executed_flop_per_point(d, K)
             _, bf16_peak, src = peaks()
             res["roofline_tc"] = {"kernel": "k_tc_mixfull<true>", "bound": "tensor", "achieved": flop / tk / 1e12,
                                   "peak": bf16_peak, "unit": "TFLOP/s", "frac": flop / tk / 1e12 / bf16_peak,
+                                  "executed_tflops": executed / tk / 1e12,
                                   "peak_source": f"{src} bf16 dense (MEASURED_PEAKS.json burst)",
                                   "launch_ms": 1e3 * tk, "points_per_launch": N}
         m4.close()
@@ -308,9 +329,12 @@ def main():
                       "grad": args.grad, "parallelism": f"replicas x{world}",
                       "l2": "inputs larger than L2: per-step state (x, g, m=10 history) "
                             f"{(2 * N * d * 4 + 2 * N * 10 * d * 4 + N * 80) / 1e6:.0f} MB > 129 MB"},
-           "evals_per_s": evals, "grads_per_s": grads, "gpu_launches": KERNELS_PER_STEP * args.steps,
+           "evals_per_s": evals, "grads_per_s": grads,
+           "gpu_launches": launches_per_step(params, gm == GRAD["adjoint_tc"], d) * args.steps,
            "clocks": clocks}
 
+    if gm == GRAD["adjoint_tc"]:
+        args.no_extras = True            # the kernel, FD, e2e and CPU legs time the FP32 path
     if not args.no_extras and rank == 0:
         # --- dominant kernel: Phase 1 (fused L-BFGS) alone, CUDA events on the context stream
         reps = 5
