@@ -240,9 +240,9 @@ def gpu_timed(model, steps, warmup):
 
 
 def tc_executed_flop_per_point(d, K):
-    """Tensor-core flop the kernel issues per point: the value pass over the split input
-    (K = 2 x 64) and the gradient pass's recomputed forward plus G = Y V."""
-    return 2 * (2 * 64) * (64 * K) * 2 + 2 * (64 * K) * 64
+    """Tensor-core flop the kernel issues per point: Z over the split input (K = 2 x 64)
+    and G = Y V, both over the padded dimension 64."""
+    return 2 * (2 * 64) * (64 * K) + 2 * (64 * K) * 64
 
 
 def full_covariance_leg(CH, steps, n_osc):

@@ -37,7 +37,6 @@ cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const E
 // tensor-core (tcgen05, BF16) full-covariance mixture objective
 cudaError_t tc_prepare_attributes();
 size_t tc_weight_bytes(int K);     // operand tiles of all component groups
-size_t tc_vt_offset(int K);        // byte offset of the V tiles within them
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out);
 // n: rows (or the capacity when count is given); idx/count: optional row list and device count

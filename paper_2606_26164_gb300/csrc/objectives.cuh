@@ -54,9 +54,36 @@ __device__ __forceinline__ void lse_push_grad(T& m, T& s, T (&G)[V], T lc, const
 // One accumulator per output: splitting the chains raised Phase 1's register
 // count from 168 to 205 and cost more in occupancy than it won in ILP
 // (measured: 2.46 vs 2.02 ms at d = 64, N = 65536).
+// In binary32 the pairs of outputs use the packed two-lane FMA (each half an
+// ordinary round-to-nearest FMA, so the results equal the scalar chain's).
 template <typename T, int V, int LPS>
 __device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&r)[V], T (&out)[V],
                                            const Grp<LPS>& g) {
+  if constexpr (std::is_same<T, float>::value && V % 2 == 0) {
+    float2 acc[V / 2];
+#pragma unroll
+    for (int w = 0; w < V / 2; ++w) acc[w] = make_float2(0.f, 0.f);
+    const float* col = M + V * g.l;
+    const int nb = (d + V - 1) / V;
+#pragma unroll 2
+    for (int jb = 0; jb < nb; ++jb) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float rj = g.bcast(r[v], jb);
+        float a[V];
+        ldg_vec<float, V>(col + (size_t)(jb * V + v) * dp, a);
+        const float2 r2 = make_float2(rj, rj);
+#pragma unroll
+        for (int w = 0; w < V / 2; ++w) acc[w] = __ffma2_rn(make_float2(a[2 * w], a[2 * w + 1]), r2, acc[w]);
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < V / 2; ++w) {
+      out[2 * w] = acc[w].x;
+      out[2 * w + 1] = acc[w].y;
+    }
+    return;
+  }
 #pragma unroll
   for (int w = 0; w < V; ++w) out[w] = T(0);
   const T* col = M + V * g.l;

@@ -1,30 +1,34 @@
 // Full-covariance Gaussian-mixture objective on the 5th-generation tensor cores
 // (tcgen05, BF16 operands, FP32 accumulators in tensor memory).
 //
-// For a tile of 128 points x (one CTA, one point per TMEM lane / thread):
+// For a tile of 128 points x (one CTA, one point per TMEM lane):
 //   Z = X W^T, W = [L_1^-1; ...; L_K^-1] rounded to BF16, as an M=128 x N=256
 //   GEMM per group of four components (N = 4 x 64), K = 128 with the input split
 //   x = x_hi + x_lo into two BF16 terms (relative residual ~2^-17);
 //   z_k = Z_k - b_k with b_k = W_k mu_k formed from the *rounded* W_k, so each
 //   component's density peaks exactly at mu_k;
 //   lc_k = c_k - |z_k|^2 / 2 with c_k = log w_k + log|det W_k| - (d/2) log 2 pi,
-//   f = log sum_k exp(lc_k) as an online log-sum-exp in the epilogue.
+//   f = log sum_k exp(lc_k).
 // The result is exactly the log-density of the mixture whose precision factors
 // are the BF16-rounded L_k^-1 (evaluated at the split input) up to FP32
-// accumulation.  The gradient is grad f = -sum_k r_k W_k^T z_k, r = softmax(lc):
-// a second pass recomputes Z, writes Y = r_k z_k (BF16) to shared memory and
-// accumulates G = Y V on the tensor cores (V = the same rows of W, laid out with
-// the output coordinate as the N dimension).
+// accumulation.  The gradient is grad f = -sum_k r_k W_k^T z_k, r = softmax(lc),
+// formed in the same pass: the weights Y = e^(lc_k - m_ref) z_k (BF16) go to
+// shared memory and G += Y V accumulates on the tensor cores (V = the same rows
+// of W with the output coordinate as the N dimension); G is rescaled when the
+// reference m_ref rises, and normalised by the final sum.
 //
 // Operand tiles are stored in global memory already in the canonical K-major,
 // non-swizzled shared-memory layout (8 x 16-byte core matrices), so each one
 // arrives with a single cp.async.bulk.  Every mbarrier wait is bounded by a
-// clock budget; on timeout the kernel raises the device error flag, stops
-// issuing work and still releases its tensor memory.
+// clock budget; on timeout the kernel raises the device error flag, every role
+// stops issuing work, waits for its copies and MMAs in flight, and the tensor
+// memory is still released.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "../../include/chisao.h"
 #include "host.h"
@@ -34,16 +38,15 @@ namespace chisao {
 namespace tc {
 
 constexpr int TM = 128;                    // points per CTA (MMA M)
-constexpr int TN = 256;                    // columns per component group (4 x 64)
+constexpr int CG = 2;                      // components per group
+constexpr int TN = CG * 64;                // GEMM1 columns per group (MMA N)
 constexpr int DK = 64;                     // padded dimension (MMA K per half of the split input)
-constexpr int A_BYTES = TM * DK * 2;       // 16 KB per BF16 input half
-constexpr int W_BYTES = TN * DK * 2;       // 32 KB
-constexpr int BIAS_BYTES = 4 * DK * 4;     // 1 KB
-constexpr int C_BYTES = 16;                // 4 floats
-constexpr int WBLK_BYTES = W_BYTES + BIAS_BYTES + C_BYTES;   // one bulk copy per group
-constexpr int VT_BYTES = DK * TN * 2;      // 32 KB
-constexpr int Y_BYTES = TM * TN * 2;       // 64 KB
-constexpr int SMEM_BYTES = 2 * A_BYTES + WBLK_BYTES + VT_BYTES + Y_BYTES + 64;
+constexpr int W_BYTES = TN * DK * 2;       // 16 KB factor tile of a group
+constexpr int BT_BYTES = TN * 16 * 2;      // 4 KB bias tile: K block [-b_hi, -b_mid, -b_lo, 0 ...] per output row
+constexpr int C_BYTES = 1024;              // c [CG] f32, zero padding
+constexpr int WC_BYTES = W_BYTES + BT_BYTES + C_BYTES;     // one stage of the factor-tile ring
+constexpr int VT_BYTES = DK * TN * 2;      // 16 KB V tile of a group
+constexpr int GBLK_BYTES = WC_BYTES + VT_BYTES;            // one group in global memory
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s at 2 GHz
 
@@ -102,37 +105,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t b
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
+// The same MMA with the A operand read from tensor memory (M rows = lanes, two BF16
+// K-elements per 32-bit column, K ascending along the columns).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bd, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(dtmem),
+      "r"(atmem), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
-
 // Byte offset of element (row, k) in a canonical K-major non-swizzled tile
 // whose rows hold `kdim` elements: core matrix (row/8, k/8), 16 bytes per row.
 __host__ __device__ constexpr uint32_t canon_off(uint32_t row, uint32_t k, uint32_t kdim) {
   return (row >> 3) * (kdim / 8) * 128u + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
-
-__device__ __forceinline__ uint16_t f2bf(float f) {  // round to nearest even
-  const uint32_t u = __float_as_uint(f);
-  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
-}
-__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
 struct TcArgs {
   const float* x;         // [.][ldx] points (FP32, first d columns used)
@@ -141,195 +132,467 @@ struct TcArgs {
   const int* idx;         // optional row list: launch row i is x row idx[i] (outputs too)
   const int* count;       // optional device row count (overrides n; CTAs past it exit)
   int d;
-  int ngroups;            // component groups of 4
-  const uint8_t* wblk;    // [ngroups][WBLK_BYTES]  W tile (canonical), bias [4][64] f32, c [4] f32
-  const uint8_t* vt;      // [ngroups][VT_BYTES]    V tile (canonical, N = 64 output coordinates)
+  int ngroups;            // component groups of CG
+  const uint8_t* gblk;    // [ngroups][GBLK_BYTES]: W tile | bias tile | c | V tile (canonical layouts)
   float* f;               // [n] or null
   float* g;               // [n][ldg] or null
   int ldg;
   int* err;               // device error flag
 };
 
+constexpr int NW = 4;                      // stages of the factor-tile ring (W, bias tile, constants)
+constexpr int NV = 3;                      // stages of the V-tile ring
+// Barriers in shared memory (index into the array after the tiles).
+enum : int {
+  B_WFULL = 0,                 // [NW] factor tile, bias tile and constants of a group landed
+  B_WEMPTY = B_WFULL + NW,     // [NW] read by the Z MMAs and the constants by the epilogue
+  B_VFULL = B_WEMPTY + NW,     // [NV] V tile of a group landed
+  B_VEMPTY = B_VFULL + NV,     // [NV] read by the gradient MMAs
+  B_ZFULL = B_VEMPTY + NV,     // Z of the current group in TMEM
+  B_ZEMPTY = B_ZFULL + 1,      // [2] Z of a group of parity b read into registers by all eight epilogue
+                               //     warps (one barrier per parity: each Z issuer then waits at most one
+                               //     phase past one it has seen, so a parity wait cannot alias)
+  B_YFULL = B_ZEMPTY + 2,      // [2] Y buffer b written (eight warps)
+  B_G2DONE = B_YFULL + 2,      // [2] gradient MMAs reading Y buffer b finished
+  B_XREADY = B_G2DONE + 2,     // split input tile written (eight warps)
+  B_DRAIN = B_XREADY + 1,      // [3] every MMA of issuer i finished
+  NBARS = B_DRAIN + 3
+};
+constexpr int NTHREADS = 384;              // warp 0 copies, warps 1-3 issue MMAs, warps 4-11 epilogue
+constexpr int A_BYTES = TM * DK * 2;                      // 16 KB per BF16 input half
+constexpr int ONES_BYTES = TM * 16 * 2;                   // 4 KB: the K block [1, 1, 1, 0 ...] of every point
+constexpr int OFF_ONES = 2 * A_BYTES;
+constexpr int OFF_W = OFF_ONES + ONES_BYTES;              // [NW] factor tile | bias tile | constants
+constexpr int OFF_V = OFF_W + NW * WC_BYTES;              // [NV] V tiles
+constexpr int OFF_XCH = OFF_V + NV * VT_BYTES;            // exchange of the two warpgroups at the end
+constexpr int XCH_BYTES = TM * 64 * 4 + 8 * TM * 4;       // [64][TM] gradient half, [2][2][TM] max, [2][2][TM] sum
+constexpr int OFF_BAR = OFF_XCH + XCH_BYTES;
+constexpr int SMEM2_BYTES = OFF_BAR + NBARS * 8 + 8;      // + TMEM address, abort flag
+static_assert(WC_BYTES % 1024 == 0 && VT_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned tiles");
+static_assert(SMEM2_BYTES <= 232448, "shared memory per block");
+// TMEM columns: Z, the gradient accumulator of component h for the groups of parity b
+// at COL_G + 64 (2b + h), and Y buffer b (BF16 weights, two K-elements per column)
+constexpr uint32_t COL_Z = 0, COL_G = TN, COL_Y = TN + 256;
+static_assert(COL_Y + 2 * 64 <= TMEM_COLS, "tensor memory columns");
+constexpr float TAU = 16.f;                // lazy rescale: Y weights stay below e^TAU
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t parity, int* err, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicExch(err, 2);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// Every lane waits; the warp proceeds only if all of them saw the phase complete.
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err, volatile int* abort_flag) {
+  const bool w = mbar_wait_ab(b, parity, err, abort_flag);
+  return __all_sync(0xffffffffu, w);
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane, without the completion wait.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// Makes the registers of an asynchronous TMEM load depend on the completion wait.
+__device__ __forceinline__ void tmem_pin32(uint32_t (&r)[32]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),
+      "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]),
+      "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// 64 accumulator columns of this thread's lane, multiplied in place by s.
+__device__ __forceinline__ void tmem_scale64(uint32_t taddr, float s) {
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r[32];
+    tmem_ld32_async(taddr + 32u * half, r);
+    tmem_wait_ld();
+    tmem_pin32(r);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) * s);
+    tmem_st32(taddr + 32u * half, r);
+  }
+}
+
+// One CTA = one tile of 128 points; the components go in groups of two (parity b = g & 1):
+//   warp 0 (one thread) bulk-copies each group's factor tile, bias tile and constants
+//   into a ring of NW stages and its V tile into a ring of NV stages;
+//   warp 1 (one thread) issues Z = [x_hi|x_lo|1] [W|W|-b]^T into TMEM (the bias enters
+//   the contraction through a K block of ones against the exact three-term BF16 split
+//   of -b, so z leaves the tensor cores centred);
+//   warps 2 and 3 (one thread each, groups of parity 0 and 1) issue
+//   G_{h,b} += Y_h V_h (h = the group's first or second component), Y read from TMEM
+//   buffer b.  Spreading the issue over three threads matters: a thread that issued
+//   MMAs finds its next barrier operation held until they ran, so each gradient issuer
+//   only waits on barriers whose MMAs finished long ago, and the gradient MMAs fill the
+//   tensor pipe while the next Z waits for its buffer.  Within a parity the gradient
+//   MMAs stay in group order (group g's weights are written only after those of g - 2
+//   were consumed), so the sums are deterministic;
+//   warps 4-11 are two warpgroups, one per component of the group, each covering the
+//   four TMEM lane quadrants (one point per thread): they read z, fold the component
+//   into a log-sum-exp and write the gradient weights e^(lc - m_ref) z as BF16 into
+//   TMEM.  Each warpgroup keeps one reference m_ref, sum and pair of accumulators per
+//   group parity: m_ref is raised only when a component exceeds it by TAU, the rows of
+//   that parity's accumulator then being rescaled in place, which needs only the
+//   gradient MMAs of the same parity two groups back (also what frees the Y buffer).
+//   The four partial results are combined at the end.
 template <bool GRAD>
-__global__ void __launch_bounds__(TM, 1) k_tc_mixfull(TcArgs a) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t* sA = sm;                                   // x_hi, then x_lo
-  uint8_t* sW = sm + 2 * A_BYTES;                     // W tile | bias | c
-  uint8_t* sV = sW + WBLK_BYTES;                      // V tile
-  uint8_t* sY = sV + VT_BYTES;                        // Y tile
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + Y_BYTES);   // [0] loads, [1] mma
-  __shared__ uint32_t s_tmem;
-  __shared__ int s_fail;
-  const int t = threadIdx.x, warp = t >> 5;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+  uint32_t& s_tmem = *reinterpret_cast<uint32_t*>(sm + OFF_BAR + NBARS * 8);
+  int& s_abort = *reinterpret_cast<int*>(sm + OFF_BAR + NBARS * 8 + 4);
+  volatile int* abort_flag = &s_abort;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nrows = a.count ? *a.count : a.n;
   if ((int)blockIdx.x * TM >= nrows) return;          // whole CTA past the rows: nothing to do
-  const int lrow = blockIdx.x * TM + t;
-  const bool live = lrow < nrows;
-  const int row = live ? (a.idx ? a.idx[lrow] : lrow) : 0;
+  const int ng = a.ngroups;
 
-  // ---- set-up: barriers, tensor memory, the split BF16 input tile
   if (t == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    s_fail = 0;
+    for (int i = 0; i < NW; ++i) {
+      mbar_init(&bars[B_WFULL + i], 1);
+      mbar_init(&bars[B_WEMPTY + i], 1 + 8);
+    }
+    for (int i = 0; i < NV; ++i) {
+      mbar_init(&bars[B_VFULL + i], 1);
+      mbar_init(&bars[B_VEMPTY + i], 1);
+    }
+    mbar_init(&bars[B_ZFULL], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars[B_ZEMPTY + b], 8);
+      mbar_init(&bars[B_YFULL + b], 8);
+      mbar_init(&bars[B_G2DONE + b], 1);
+    }
+    for (int i = 0; i < 3; ++i) mbar_init(&bars[B_DRAIN + i], 1);
+    mbar_init(&bars[B_XREADY], 8);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  {
-    const float* xr = a.x + (size_t)row * a.ldx;
-    for (int k8 = 0; k8 < DK / 8; ++k8) {
-      uint16_t hi[8], lo[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = k8 * 8 + e;
-        const float v = (live && j < a.d) ? xr[j] : 0.f;
-        hi[e] = f2bf(v);
-        lo[e] = f2bf(v - bf2f(hi[e]));
-      }
-      uint4 ph, pl;
-      ph.x = hi[0] | ((uint32_t)hi[1] << 16); ph.y = hi[2] | ((uint32_t)hi[3] << 16);
-      ph.z = hi[4] | ((uint32_t)hi[5] << 16); ph.w = hi[6] | ((uint32_t)hi[7] << 16);
-      pl.x = lo[0] | ((uint32_t)lo[1] << 16); pl.y = lo[2] | ((uint32_t)lo[3] << 16);
-      pl.z = lo[4] | ((uint32_t)lo[5] << 16); pl.w = lo[6] | ((uint32_t)lo[7] << 16);
-      *reinterpret_cast<uint4*>(sA + canon_off(t, k8 * 8, DK)) = ph;
-      *reinterpret_cast<uint4*>(sA + A_BYTES + canon_off(t, k8 * 8, DK)) = pl;
-    }
-  }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t idF = idesc_bf16(TM, TN), idB = idesc_bf16(TM, DK);
-  uint32_t ph_ld = 0, ph_mma = 0;
 
-  // one component group: load its operands, Z = X W^T into TMEM columns [0, 256)
-  auto forward = [&](int grp, bool with_v) -> bool {
-    if (t == 0) {
-      mbar_expect_tx(&bars[0], (uint32_t)(WBLK_BYTES + (with_v ? VT_BYTES : 0)));
-      bulk_g2s(sW, a.wblk + (size_t)grp * WBLK_BYTES, WBLK_BYTES, &bars[0]);
-      if (with_v) bulk_g2s(sV, a.vt + (size_t)grp * VT_BYTES, VT_BYTES, &bars[0]);
-    }
-    if (!mbar_wait(&bars[0], ph_ld, a.err)) s_fail = 1;
-    ph_ld ^= 1u;
-    __syncthreads();
-    if (s_fail) return false;
-    if (t == 0) {
-      tc_fence_after();
-      const uint32_t aH = smem_u32(sA), aL = aH + A_BYTES, bW = smem_u32(sW);
-#pragma unroll
-      for (int s = 0; s < DK / 16; ++s)
-        mma_bf16(tmem, sdesc(aH + s * 256, 128, 1024), sdesc(bW + s * 256, 128, 1024), idF, s > 0);
-#pragma unroll
-      for (int s = 0; s < DK / 16; ++s)
-        mma_bf16(tmem, sdesc(aL + s * 256, 128, 1024), sdesc(bW + s * 256, 128, 1024), idF, 1u);
-      mma_commit(&bars[1]);
-    }
-    if (!mbar_wait(&bars[1], ph_mma, a.err)) s_fail = 1;
-    ph_mma ^= 1u;
-    __syncthreads();
-    tc_fence_after();
-    return !s_fail;
-  };
-
-  // q_k of component kl of the current group for this thread's point
-  auto comp_q = [&](int kl, float (&z)[64]) -> float {
-    const float* bias = reinterpret_cast<const float*>(sW + W_BYTES) + kl * DK;
-    float v[32];
-    float q = 0.f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld32(tlane + (uint32_t)(kl * DK + h * 32), v);
-#pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        z[h * 32 + e] = v[e] - bias[h * 32 + e];
-        q = fmaf(z[h * 32 + e], z[h * 32 + e], q);
-      }
-    }
-    return q;
-  };
-
-  // ---- pass 1: f = log sum_k exp(lc_k)
-  float m = -CUDART_INF_F, s = 0.f;
-  for (int grp = 0; grp < a.ngroups; ++grp) {
-    if (!forward(grp, false)) break;
-    const float* cst = reinterpret_cast<const float*>(sW + W_BYTES + BIAS_BYTES);
-    for (int kl = 0; kl < 4; ++kl) {
-      float z[64];
-      const float lc = cst[kl] - 0.5f * comp_q(kl, z);
-      if (lc > m) {
-        s = s * expf(m - lc) + 1.f;
-        m = lc;
-      } else {
-        s += expf(lc - m);
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-  }
-  const float fval = m + logf(s);
-
-  // ---- pass 2: G = sum_k (r_k z_k)^T W_k on the tensor cores (TMEM columns [256, 320))
-  if (GRAD && !s_fail) {
-    for (int grp = 0; grp < a.ngroups; ++grp) {
-      if (!forward(grp, true)) break;
-      const float* cst = reinterpret_cast<const float*>(sW + W_BYTES + BIAS_BYTES);
-      for (int kl = 0; kl < 4; ++kl) {
-        float z[64];
-        const float lc = cst[kl] - 0.5f * comp_q(kl, z);
-        const float r = expf(lc - fval);
-#pragma unroll
-        for (int k8 = 0; k8 < 8; ++k8) {
-          uint4 p;
-          p.x = f2bf(r * z[k8 * 8 + 0]) | ((uint32_t)f2bf(r * z[k8 * 8 + 1]) << 16);
-          p.y = f2bf(r * z[k8 * 8 + 2]) | ((uint32_t)f2bf(r * z[k8 * 8 + 3]) << 16);
-          p.z = f2bf(r * z[k8 * 8 + 4]) | ((uint32_t)f2bf(r * z[k8 * 8 + 5]) << 16);
-          p.w = f2bf(r * z[k8 * 8 + 6]) | ((uint32_t)f2bf(r * z[k8 * 8 + 7]) << 16);
-          *reinterpret_cast<uint4*>(sY + canon_off(t, kl * DK + k8 * 8, TN)) = p;
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int lastW[NW], lastV[NV];
+      for (int s = 0; s < NW; ++s) lastW[s] = -1;
+      for (int s = 0; s < NV; ++s) lastV[s] = -1;
+      // the V tile of a group is needed one group after its factor tile: it trails by two
+      for (int g = 0; g < ng + (GRAD ? 2 : 0); ++g) {
+        if (g < ng) {
+          const int s = g % NW, u = g / NW;
+          if (u > 0 && !mbar_wait_ab(&bars[B_WEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
+          mbar_expect_tx(&bars[B_WFULL + s], (uint32_t)WC_BYTES);
+          bulk_g2s(sm + OFF_W + s * WC_BYTES, a.gblk + (size_t)g * GBLK_BYTES, WC_BYTES, &bars[B_WFULL + s]);
+          lastW[s] = u;
+        }
+        const int gv = g - 2;
+        if (GRAD && gv >= 0) {
+          const int s = gv % NV, u = gv / NV;
+          if (u > 0 && !mbar_wait_ab(&bars[B_VEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
+          mbar_expect_tx(&bars[B_VFULL + s], (uint32_t)VT_BYTES);
+          bulk_g2s(sm + OFF_V + s * VT_BYTES, a.gblk + (size_t)gv * GBLK_BYTES + WC_BYTES, VT_BYTES,
+                   &bars[B_VFULL + s]);
+          lastV[s] = u;
         }
       }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (t == 0) {
-        tc_fence_after();
-        const uint32_t aY = smem_u32(sY), bV = smem_u32(sV);
+      // copies still in flight land before the CTA may exit (bounded)
+      for (int s = 0; s < NW; ++s)
+        if (lastW[s] >= 0) mbar_wait(&bars[B_WFULL + s], lastW[s] & 1, a.err);
+      for (int s = 0; s < NV; ++s)
+        if (lastV[s] >= 0) mbar_wait(&bars[B_VFULL + s], lastV[s] & 1, a.err);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ Z issuer
+    if (lane == 0) {
+      const uint32_t idF = idesc_bf16(TM, TN);
+      const uint32_t aX = smem_u32(sm), aOnes = smem_u32(sm + OFF_ONES);
+      bool issued = false;
+      if (mbar_wait_ab(&bars[B_XREADY], 0, a.err, abort_flag)) {
+        for (int g = 0; g < ng; ++g) {
+          const int s = g % NW;
+          if (!mbar_wait_ab(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) break;
+          if (g >= 1 && !mbar_wait_ab(&bars[B_ZEMPTY + ((g - 1) & 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) break;
+          tc_fence_after();
+          const uint32_t bW = smem_u32(sm + OFF_W + s * WC_BYTES);
 #pragma unroll
-        for (int s2 = 0; s2 < TN / 16; ++s2)
-          mma_bf16(tmem + TN, sdesc(aY + s2 * 256, 128, 4096), sdesc(bV + s2 * 256, 128, 4096), idB,
-                   (grp > 0 || s2 > 0) ? 1u : 0u);
-        mma_commit(&bars[1]);
+          for (int k = 0; k < 2 * DK / 16; ++k)     // x_hi then x_lo against the same factor tile
+            mma_bf16(tmem + COL_Z, sdesc(aX + (k >> 2) * A_BYTES + (k & 3) * 256, 128, 1024),
+                     sdesc(bW + (k & 3) * 256, 128, 1024), idF, k > 0);
+          mma_bf16(tmem + COL_Z, sdesc(aOnes, 128, 256), sdesc(bW + W_BYTES, 128, 256), idF, 1u);   // - b
+          mma_commit(&bars[B_ZFULL]);
+          mma_commit(&bars[B_WEMPTY + s]);
+          issued = true;
+        }
       }
-      if (!mbar_wait(&bars[1], ph_mma, a.err)) s_fail = 1;
-      ph_mma ^= 1u;
-      __syncthreads();
+      if (issued) {                                     // every issued MMA completes before exit
+        mma_commit(&bars[B_DRAIN]);
+        mbar_wait(&bars[B_DRAIN], 0, a.err);
+      }
+    }
+  } else if (warp <= 3) {
+    // ------------------------------------------------------------ gradient issuers (groups of parity j)
+    if (GRAD && lane == 0) {
+      const int j = warp - 2;
+      const uint32_t idB = idesc_bf16(TM, DK);
+      bool issued = false;
+      for (int g = j; g < ng; g += 2) {
+        const int b = g & 1, s = g % NV;
+        if (!mbar_wait_ab(&bars[B_YFULL + b], (g >> 1) & 1, a.err, abort_flag)) break;
+        if (!mbar_wait_ab(&bars[B_VFULL + s], (g / NV) & 1, a.err, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t bV = smem_u32(sm + OFF_V + s * VT_BYTES);
+        const uint32_t aY = tmem + COL_Y + 64u * (uint32_t)b;
+        const uint32_t dg = tmem + COL_G + 128u * (uint32_t)b;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16_ts(dg, aY + 8u * k, sdesc(bV + k * 256, 128, 2048), idB, (g >= 2 || k > 0) ? 1u : 0u);
+#pragma unroll
+        for (int k = 4; k < 8; ++k)
+          mma_bf16_ts(dg + 64u, aY + 8u * k, sdesc(bV + k * 256, 128, 2048), idB, (g >= 2 || k > 4) ? 1u : 0u);
+        mma_commit(&bars[B_G2DONE + b]);
+        mma_commit(&bars[B_VEMPTY + s]);
+        issued = true;
+      }
+      if (issued) {
+        mma_commit(&bars[B_DRAIN + 1 + j]);
+        mbar_wait(&bars[B_DRAIN + 1 + j], 0, a.err);
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ epilogue (warps 4-11)
+    const int h = (warp - 4) >> 2;                      // component of the group
+    const int quad = warp & 3;                          // TMEM lane quadrant of this warp
+    const int p = quad * 32 + lane;                     // point of the tile
+    const int lrow = blockIdx.x * TM + p;
+    const bool live = lrow < nrows;
+    const int row = live ? (a.idx ? a.idx[lrow] : lrow) : 0;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+
+    // split input: this thread converts columns [32h, 32h + 32) of its point; the first
+    // warpgroup also writes the point's ones block
+    {
+      const float* xr = a.x + (size_t)row * a.ldx;
+#pragma unroll
+      for (int k8 = 0; k8 < 4; ++k8) {
+        const int j0 = 32 * h + 8 * k8;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = j0 + 2 * e;
+          const float v0 = (live && j < a.d) ? xr[j] : 0.f;
+          const float v1 = (live && j + 1 < a.d) ? xr[j + 1] : 0.f;
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+          const float2 hf = __bfloat1622float2(hh);
+          hi[e] = *reinterpret_cast<const uint32_t*>(&hh);
+          lo[e] = pack_bf16x2(v0 - hf.x, v1 - hf.y);
+        }
+        *reinterpret_cast<uint4*>(sm + canon_off(p, j0, DK)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sm + A_BYTES + canon_off(p, j0, DK)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      if (h == 0) {
+        const uint32_t one = 0x3F80u;                   // BF16 1.0
+        *reinterpret_cast<uint4*>(sm + OFF_ONES + canon_off(p, 0, 16)) = make_uint4(one | (one << 16), one, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + OFF_ONES + canon_off(p, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[B_XREADY]);
+    }
+
+    float mref0 = -CUDART_INF_F, mref1 = -CUDART_INF_F, ssum0 = 0.f, ssum1 = 0.f;   // per group parity
+    bool ok = true;
+    for (int g = 0; g < ng; ++g) {
+      const int b = g & 1, s = g % NW;
+      if (!warp_wait(&bars[B_ZFULL], g & 1, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      if (s_fail) break;
+      float z[64];
+      {
+        uint32_t r0[32], r1[32];
+        const uint32_t c0 = tl + COL_Z + 64u * h;
+        tmem_ld32_async(c0, r0);
+        tmem_ld32_async(c0 + 32, r1);
+        tmem_wait_ld();
+        tmem_pin32(r0);
+        tmem_pin32(r1);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          z[e] = __uint_as_float(r0[e]);
+          z[32 + e] = __uint_as_float(r1[e]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[B_ZEMPTY + b]);   // Z may take the next group
+
+      // the constants landed with the factor tile; the stage cannot be refilled before
+      // this warp's arrival on B_WEMPTY below, so the phase waited for is still the current one
+      if (!warp_wait(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) { ok = false; break; }
+      const float cst = reinterpret_cast<const float*>(sm + OFF_W + s * WC_BYTES + W_BYTES + BT_BYTES)[h];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[B_WEMPTY + s]);   // constants of this stage read
+      float2 qa = make_float2(0.f, 0.f), qb = qa;        // two packed chains: four partial sums
+#pragma unroll
+      for (int e = 0; e < 64; e += 4) {
+        const float2 z0 = make_float2(z[e], z[e + 1]), z1 = make_float2(z[e + 2], z[e + 3]);
+        qa = __ffma2_rn(z0, z0, qa);
+        qb = __ffma2_rn(z1, z1, qb);
+      }
+      const float lc = cst - 0.5f * ((qa.x + qa.y) + (qb.x + qb.y));
+
+      if (!GRAD) {
+        if (lc > mref0) {
+          ssum0 = ssum0 * expf(mref0 - lc) + 1.f;
+          mref0 = lc;
+        } else if (lc > -CUDART_INF_F) {
+          ssum0 += expf(lc - mref0);
+        }
+        continue;
+      }
+      float mr = b ? mref1 : mref0, ss = b ? ssum1 : ssum0;
+      float scale = 1.f;
+      bool resc = false;
+      if (lc > mr + TAU) {
+        if (mr > -CUDART_INF_F) {
+          scale = expf(mr - lc);
+          resc = true;
+          ss *= scale;
+        }
+        mr = lc;
+      }
+      // Y buffer b and the parity-b accumulators are free once the gradient MMAs of group
+      // g - 2 finished
+      if (g >= 2 && !warp_wait(&bars[B_G2DONE + b], ((g - 2) >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      if (__any_sync(0xffffffffu, resc)) tmem_scale64(tl + COL_G + 128u * b + 64u * h, scale);
+      const float r = lc > -CUDART_INF_F ? expf(lc - mr) : 0.f;
+      ss += r;
+      if (b) {
+        mref1 = mr;
+        ssum1 = ss;
+      } else {
+        mref0 = mr;
+        ssum0 = ss;
+      }
+      {
+        uint32_t y[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) y[e] = pack_bf16x2(r * z[2 * e], r * z[2 * e + 1]);
+        tmem_st32(tl + COL_Y + 64u * (uint32_t)b + 32u * h, y);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[B_YFULL + b]);
+    }
+
+    // ---- combine the two warpgroups and the two parities, write f and g
+    float gacc[64];
+    if (GRAD && ok) {
+      // the last group of each parity completes that parity's accumulators
+      if (ng >= 2) ok = warp_wait(&bars[B_G2DONE + ((ng - 2) & 1)], ((ng - 2) >> 1) & 1, a.err, abort_flag);
+      if (ok) ok = warp_wait(&bars[B_G2DONE + ((ng - 1) & 1)], ((ng - 1) >> 1) & 1, a.err, abort_flag);
+    }
+    float* xch = reinterpret_cast<float*>(sm + OFF_XCH);            // [64][TM]
+    float* s_m = xch + 64 * TM;                                     // [h][b][TM]
+    float* s_s = s_m + 4 * TM;                                      // [h][b][TM]
+    s_m[(2 * h) * TM + p] = mref0;
+    s_m[(2 * h + 1) * TM + p] = mref1;
+    s_s[(2 * h) * TM + p] = ssum0;
+    s_s[(2 * h + 1) * TM + p] = ssum1;
+    epi_sync();
+    float m = -CUDART_INF_F;
+    for (int i = 0; i < 4; ++i) m = fmaxf(m, s_m[i * TM + p]);
+    float stot = 0.f, eb0 = 0.f, eb1 = 0.f;            // eb: weights of this warpgroup's two parities
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float mi = s_m[i * TM + p];
+      const float ei = mi > -CUDART_INF_F ? expf(mi - m) : 0.f;
+      stot += s_s[i * TM + p] * ei;
+      if (i == 2 * h) eb0 = ei;
+      if (i == 2 * h + 1) eb1 = ei;
+    }
+    const bool fine = ok && !*abort_flag;
+    if (h == 0 && live && fine && a.f) a.f[row] = m + logf(stot);
+    if (GRAD) {
+      if (fine) {
+        tc_fence_after();
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {                    // parity 0, then parity 1 (fixed order)
+          const float sc = -(b ? eb1 : eb0) / stot;
+          uint32_t r0[32], r1[32];
+          const uint32_t c0 = tl + COL_G + 128u * b + 64u * h;
+          tmem_ld32_async(c0, r0);
+          tmem_ld32_async(c0 + 32, r1);
+          tmem_wait_ld();
+          tmem_pin32(r0);
+          tmem_pin32(r1);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            gacc[e] = b ? fmaf(__uint_as_float(r0[e]), sc, gacc[e]) : __uint_as_float(r0[e]) * sc;
+            gacc[32 + e] = b ? fmaf(__uint_as_float(r1[e]), sc, gacc[32 + e]) : __uint_as_float(r1[e]) * sc;
+          }
+        }
+        if (h == 1) {
+#pragma unroll
+          for (int e = 0; e < 64; ++e) xch[e * TM + p] = gacc[e];
+        }
+      }
+      epi_sync();
+      if (h == 0 && live && fine) {
+        float* gr = a.g + (size_t)row * a.ldg;
+#pragma unroll
+        for (int e = 0; e < 64; ++e)
+          if (e < a.d) gr[e] = gacc[e] + xch[e * TM + p];
+      }
     }
   }
 
-  // ---- outputs
-  if (live && !s_fail) {
-    if (a.f) a.f[row] = fval;
-  }
-  if (GRAD && !s_fail) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float v[32];
-      tmem_ld32(tlane + (uint32_t)(TN + h * 32), v);
-      if (live)
-        for (int e = 0; e < 32; ++e)
-          if (h * 32 + e < a.d) a.g[(size_t)row * a.ldg + h * 32 + e] = -v[e];
-    }
-  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
@@ -340,16 +603,12 @@ __global__ void __launch_bounds__(TM, 1) k_tc_mixfull(TcArgs a) {
 // ------------------------------------------------------------------ host side
 cudaError_t tc_prepare_attributes() {
   cudaError_t e = cudaFuncSetAttribute(tc::k_tc_mixfull<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc::SMEM_BYTES);
+                                       tc::SMEM2_BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc::k_tc_mixfull<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  return cudaFuncSetAttribute(tc::k_tc_mixfull<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM2_BYTES);
 }
 
-size_t tc_weight_bytes(int K) {
-  const size_t ng = (size_t)(K + 3) / 4;
-  return ng * (tc::WBLK_BYTES + tc::VT_BYTES);
-}
-size_t tc_vt_offset(int K) { return (size_t)((K + 3) / 4) * tc::WBLK_BYTES; }
+size_t tc_weight_bytes(int K) { return (size_t)((K + tc::CG - 1) / tc::CG) * tc::GBLK_BYTES; }
 
 static uint16_t host_f2bf(float f) {
   uint32_t u;
@@ -363,21 +622,25 @@ static double host_bf2d(uint16_t h) {
   return (double)f;
 }
 
-// Operand tiles of the tensor-core objective from the FP64 inverse Cholesky
-// factors linv[K][d][d] (lower-triangular), means mu[K][d] and log-weights.
+// Operand blocks of the tensor-core objective from the FP64 inverse Cholesky
+// factors linv[K][d][d] (lower-triangular), means mu[K][d] and log-weights: per
+// group of CG components the BF16 factor tile (rows = component-major output
+// coordinates, K = input coordinate), the bias tile holding -W mu (from the rounded W,
+// in binary32) as three BF16 terms whose sum is exact, the log-constants, and the V
+// tile (rows = input coordinate, K = component-major output coordinate).
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out) {
   using namespace tc;
-  const int ng = (K + 3) / 4;
+  const int ng = (K + CG - 1) / CG;
   out.assign(tc_weight_bytes(K), 0);
   const double half_log2pi = 0.5 * std::log(2.0 * M_PI);
   for (int grp = 0; grp < ng; ++grp) {
-    uint8_t* W = out.data() + (size_t)grp * WBLK_BYTES;
-    float* bias = reinterpret_cast<float*>(W + W_BYTES);
-    float* cst = reinterpret_cast<float*>(W + W_BYTES + BIAS_BYTES);
-    uint8_t* Vt = out.data() + tc_vt_offset(K) + (size_t)grp * VT_BYTES;
-    for (int kl = 0; kl < 4; ++kl) {
-      const int k = grp * 4 + kl;
+    uint8_t* W = out.data() + (size_t)grp * GBLK_BYTES;
+    uint8_t* Bt = W + W_BYTES;
+    float* cst = reinterpret_cast<float*>(W + W_BYTES + BT_BYTES);
+    uint8_t* Vt = W + WC_BYTES;
+    for (int kl = 0; kl < CG; ++kl) {
+      const int k = grp * CG + kl;
       if (k >= K) {
         cst[kl] = -INFINITY;
         continue;
@@ -394,7 +657,13 @@ void tc_build_weights(int K, int d, const double* linv, const double* mu, const 
           b += host_bf2d(h) * mu[(size_t)k * d + j];
           if (i == j) ldet += std::log(host_bf2d(h));
         }
-        bias[kl * DK + i] = (float)b;
+        // -b in binary32 = t0 + t1 + t2 exactly, each term a BF16 value
+        float r = (float)(-b);
+        for (int e = 0; e < 3; ++e) {
+          const uint16_t te = host_f2bf(r);
+          *reinterpret_cast<uint16_t*>(Bt + canon_off(kl * DK + i, e, 16)) = te;
+          r -= (float)host_bf2d(te);
+        }
       }
       cst[kl] = (float)(logw[k] + ldet - d * half_log2pi);
     }
@@ -404,12 +673,12 @@ void tc_build_weights(int K, int d, const double* linv, const double* mu, const 
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights, float* f,
                               float* g, int ldg, int* err, cudaStream_t st, const int* idx, const int* count) {
   if (n <= 0) return cudaSuccess;
-  tc::TcArgs a{x, ldx, n, idx, count, d, (K + 3) / 4, weights, weights + tc_vt_offset(K), f, g, ldg, err};
+  tc::TcArgs a{x, ldx, n, idx, count, d, (K + tc::CG - 1) / tc::CG, weights, f, g, ldg, err};
   const unsigned grid = (unsigned)((n + tc::TM - 1) / tc::TM);
   if (g)
-    tc::k_tc_mixfull<true><<<grid, tc::TM, tc::SMEM_BYTES, st>>>(a);
+    tc::k_tc_mixfull<true><<<grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
   else
-    tc::k_tc_mixfull<false><<<grid, tc::TM, tc::SMEM_BYTES, st>>>(a);
+    tc::k_tc_mixfull<false><<<grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
   return cudaGetLastError();
 }
 
