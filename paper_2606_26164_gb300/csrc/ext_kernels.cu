@@ -76,8 +76,11 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
   const Grp<LPS> g;
   const int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   const int cur = t & 1;
+  const int pending = E.cnt[t];
+  // the grid covers every sample; blocks past the round's list have nothing to count
+  if ((int)(((size_t)blockIdx.x * blockDim.x) / LPS) >= pending) return;
   unsigned long long tr = 0, fl = 0;
-  if (jj < E.cnt[t]) {
+  if (jj < pending) {
     const int i = E.list[cur][jj];
     const int j0 = V * g.l;
     float x[V], G[V], c[V], Gt[V];
