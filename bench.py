@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override the population size (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=2, help="cycles of the full-covariance tensor-core leg")
+    ap.add_argument("--batched-steps", type=int, default=3, help="cycles of the 512-problem leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -281,6 +282,20 @@ def full_covariance_leg(CH, steps, n_osc):
     return res
 
 
+def batched_leg(CH, steps):
+    """512 independent diagonal-mixture problems (d in {2..64}, N log-uniform in
+    [256, 16384], K in [4, 128]) in one context: one step = one non-final cycle of all."""
+    from paper_2606_26164_gb300 import inputs as I
+    probs = I.batched512()
+    prm = CH.default_params(n_osc=10 ** 6, m=10, eps_grad=1e-3, grad_mode=GRAD["adjoint"], seed=0)
+    model = CH.Chisao(probs, prm)
+    t, _, _ = gpu_timed(model, steps, 1)
+    n_total = sum(p.n for p in probs)
+    model.close()
+    return {"problems": len(probs), "samples": n_total, "value": n_total * steps / t, "unit": "sample-cycles/s",
+            "ms_per_step": 1e3 * t / steps, "steps": steps, "grad": "adjoint"}
+
+
 def main():
     args = parse()
     if args.cpu_leg:
@@ -374,6 +389,9 @@ def main():
         #     and the tensor-core objective kernel against the measured BF16 peak
         if args.workload == "quadratic_d64" and args.tc_steps > 0:
             out["mixture256_d64"] = full_covariance_leg(CH, args.tc_steps, n_osc)
+        # --- 512 problems of uneven size in one context (cycle graph with one branch per stream)
+        if args.workload == "quadratic_d64" and args.batched_steps > 0:
+            out["batched512"] = batched_leg(CH, args.batched_steps)
         # --- end to end through the C ABI: pinned host population in, modes out, every step
         xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
         xh.copy_(torch.from_numpy(prob.x0))

@@ -5,6 +5,7 @@
 // inverses, A = Q^T diag(lam) Q), enqueueing the per-cycle kernel sequence of
 // Algorithm 1 and capturing it in CUDA graphs.  Every phase itself runs in the
 // kernels of phase_kernels.cu and obj_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -65,6 +66,13 @@ struct chisao_ctx {
   bool own_arena = false;
   int cycles_done = 0;
   cudaGraphExec_t g_mid = nullptr, g_last = nullptr;
+  // several problems: each cycle forks onto branch streams (problems spread over them,
+  // largest first, to the least-loaded branch) and joins back, so a captured cycle is a
+  // graph whose per-problem chains run concurrently
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> joined;
+  cudaEvent_t forked = nullptr;
+  std::vector<int> branch_of;              // problem -> branch
   std::string err;
 };
 
@@ -398,21 +406,65 @@ cudaError_t enqueue_cycle_tc(const ProbHost& ph, bool last, cudaStream_t st) {
   return launch_cycle_end(ph.dev, st);
 }
 
-// One oscillation cycle (Algorithm 1) of every problem.
+// One oscillation cycle (Algorithm 1) of one problem.
+cudaError_t enqueue_problem_cycle(const ProbHost& ph, bool last, cudaStream_t st) {
+  if (ph.tc) return enqueue_cycle_tc(ph, last, st);
+  cudaError_t e;
+  if ((e = launch_cycle_begin(ph.dev, st)) != cudaSuccess) return e;                          // release all
+  if ((e = launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, ph.sp.n_conv, nullptr, st)) != cudaSuccess)
+    return e;                                                                                  // Phase 1
+  if ((e = launch_freeze(ph.dev, ph.sp, st)) != cudaSuccess) return e;                        // Phase 2
+  if ((e = launch_dedup(ph.dev, ph.sp, st)) != cudaSuccess) return e;                         // Phase 3
+  if (!last && (e = enqueue_explore(ph, st)) != cudaSuccess) return e;                        // Phases 4-6
+  return launch_cycle_end(ph.dev, st);
+}
+
+// One oscillation cycle of every problem: independent problems on the branch streams.
 cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
   cudaError_t e;
-  for (const ProbHost& ph : c->probs) {
-    if (ph.tc) {
-      if ((e = enqueue_cycle_tc(ph, last, c->stream)) != cudaSuccess) return e;
-      continue;
-    }
-    if ((e = launch_cycle_begin(ph.dev, c->stream)) != cudaSuccess) return e;                  // release all
-    if ((e = launch_objective(OKID_PHASE1, ph, ph.sp.grad_mode, ph.sp.n_conv, nullptr, c->stream)) != cudaSuccess)
-      return e;                                                                                 // Phase 1
-    if ((e = launch_freeze(ph.dev, ph.sp, c->stream)) != cudaSuccess) return e;                // Phase 2
-    if ((e = launch_dedup(ph.dev, ph.sp, c->stream)) != cudaSuccess) return e;                 // Phase 3
-    if (!last && (e = enqueue_explore(ph, c->stream)) != cudaSuccess) return e;                // Phases 4-6
-    if ((e = launch_cycle_end(ph.dev, c->stream)) != cudaSuccess) return e;
+  if (c->branch.empty()) {
+    for (const ProbHost& ph : c->probs)
+      if ((e = enqueue_problem_cycle(ph, last, c->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  if ((e = cudaEventRecord(c->forked, c->stream)) != cudaSuccess) return e;
+  for (cudaStream_t s : c->branch)
+    if ((e = cudaStreamWaitEvent(s, c->forked, 0)) != cudaSuccess) return e;
+  for (size_t q = 0; q < c->probs.size(); ++q)
+    if ((e = enqueue_problem_cycle(c->probs[q], last, c->branch[c->branch_of[q]])) != cudaSuccess) return e;
+  for (size_t b = 0; b < c->branch.size(); ++b) {
+    if ((e = cudaEventRecord(c->joined[b], c->branch[b])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->stream, c->joined[b], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Branch streams for a context of several problems; each problem goes, largest first,
+// to the branch with the least work so far (work ~ samples x padded dimension).
+cudaError_t make_branches(chisao_ctx* c) {
+  const int nq = (int)c->probs.size();
+  if (nq < 2) return cudaSuccess;
+  const int nb = std::min(nq, 32);
+  cudaError_t e;
+  if ((e = cudaEventCreateWithFlags(&c->forked, cudaEventDisableTiming)) != cudaSuccess) return e;
+  for (int b = 0; b < nb; ++b) {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    c->branch.push_back(s);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    c->joined.push_back(ev);
+  }
+  std::vector<int> order(nq);
+  for (int q = 0; q < nq; ++q) order[q] = q;
+  auto work = [&](int q) { return (double)c->probs[q].n * c->probs[q].dp; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  std::vector<double> load(nb, 0.0);
+  c->branch_of.assign(nq, 0);
+  for (int q : order) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    c->branch_of[q] = b;
+    load[b] += work(q);
   }
   return cudaSuccess;
 }
@@ -583,6 +635,7 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     for (int j = 0; j < ph.d; ++j) box[j] = (float)pr.hi[j];
     up(P.hi, box.data(), box.size() * 4);
   }
+  if (st == CHISAO_OK && make_branches(c) != cudaSuccess) st = cuda_fail(c, cudaGetLastError(), "branch streams");
   if (st != CHISAO_OK) {
     chisao_destroy(c);
     return st;
@@ -724,6 +777,12 @@ void chisao_destroy(chisao_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->g_mid) cudaGraphExecDestroy(c->g_mid);
   if (c->g_last) cudaGraphExecDestroy(c->g_last);
+  for (cudaStream_t s : c->branch) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t ev : c->joined) cudaEventDestroy(ev);
+  if (c->forked) cudaEventDestroy(c->forked);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -128,6 +128,31 @@ def test_batched_problems_in_one_context():
     model.close()
 
 
+def test_batched_problems_match_separate_contexts():
+    """Problems of one context are independent (the cycle forks them onto branch
+    streams): problem q's state after two cycles is bit-identical in a context of
+    six problems and in one of the first q + 1 (same problem index, hence the same
+    Philox streams; different branch assignment), with and without graph capture."""
+    probs = I.batched512(n_problems=6, n_scale=0.1, seed=3)
+    P = M.Params(n_osc=4, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=2)
+    U.ensure_built()
+    fields = (CH.FIELD_X, CH.FIELD_F, CH.FIELD_STUCK)
+    for use_graph in (1, 0):
+        prm = U.lib_params(P)
+        prm.use_graph = use_graph
+        together = CH.Chisao(probs, prm)
+        for _ in range(2):
+            together.step()
+        for q in range(len(probs)):
+            part = CH.Chisao(probs[:q + 1], prm)
+            for _ in range(2):
+                part.step()
+            for fld in fields:
+                np.testing.assert_array_equal(part.get(q, fld), together.get(q, fld))
+            part.close()
+        together.close()
+
+
 def test_determinism_and_graph_equivalence():
     prob = I.small_mixture(5, 6, 3000, seed=20)
     P = M.Params(n_osc=4, m=6, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=9)
