@@ -6,6 +6,7 @@
   computed as a log-sum-exp over the component log-densities.
 * Rotated quadratic f(x) = -(x-c)^T Q^T Lambda Q (x-c) (a log-concave target
   with the single mode c, the setting of Proposition 1).
+* The benchmark functions of Appendix D (``oracle.benchmarks``).
 
 The optional additive noise of Section 5.6 (f~ = f + eps, eps ~ N(0, s^2)) is
 applied by ``method.evaluate``, which knows the evaluation's stream position.
@@ -14,6 +15,8 @@ from __future__ import annotations
 
 import numpy as np
 from scipy.linalg import solve_triangular
+
+from . import benchmarks as BENCH
 
 OBJ_MIXTURE_DIAG = 1
 OBJ_MIXTURE_FULL = 2
@@ -89,6 +92,8 @@ def _lse(lc):
 
 def value(obj, X):
     X = np.asarray(X, dtype=np.float64)
+    if obj.kind in BENCH.BENCH_KINDS:
+        return BENCH.value(obj.kind, X)
     if obj.kind == OBJ_QUADRATIC:
         A = obj.arrays
         Z = (X - A["center"][None, :]) @ A["Q"].T
@@ -100,6 +105,8 @@ def value(obj, X):
 def grad(obj, X):
     """Analytic gradient of f (the exact gradient the adjoint path computes)."""
     X = np.asarray(X, dtype=np.float64)
+    if obj.kind in BENCH.BENCH_KINDS:
+        return BENCH.grad(obj.kind, X)
     if obj.kind == OBJ_QUADRATIC:
         A = obj.arrays
         Q, lam = A["Q"], A["lam"]
@@ -131,6 +138,8 @@ def _precisions(obj):
 def hessian(obj, x):
     """Hessian of f at one point x (d,), for the Newton mode finder:
     sum_k r_k (a_k a_k^T - Sigma_k^-1) - gbar gbar^T."""
+    if obj.kind in BENCH.BENCH_KINDS:
+        return BENCH.hessian(obj.kind, x)
     x = np.asarray(x, dtype=np.float64)[None, :]
     if obj.kind == OBJ_QUADRATIC:
         A = obj.arrays
