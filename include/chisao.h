@@ -53,7 +53,26 @@ typedef enum {
   /* log sum_k w_k N(x; mu_k, L_k L_k^T), L_k lower-triangular Cholesky     */
   CHISAO_OBJ_MIXTURE_FULL = 2,
   /* -(x - c)^T Q^T diag(lam) Q (x - c), a log-concave target (Prop. 1)     */
-  CHISAO_OBJ_QUADRATIC = 3
+  CHISAO_OBJ_QUADRATIC = 3,
+  /* Appendix D benchmark functions, negated for maximisation; no parameter
+   * arrays.  Coordinates i = 1..d.  Where a function is not differentiable
+   * the adjoint gradient takes the zero subgradient of the offending term.  */
+  /* -sum_i (x_i^2 - 10 cos(2 pi x_i) + 10), App. D domain [-5.12, 5.12]^d   */
+  CHISAO_OBJ_RASTRIGIN = 10,
+  /* 20 exp(-0.2 sqrt(sum x_i^2 / d)) + exp(sum cos(2 pi x_i) / d) - 20 - e,
+   * domain [-32.768, 32.768]^d                                              */
+  CHISAO_OBJ_ACKLEY = 11,
+  /* sum_i x_i sin(sqrt|x_i|) - 418.9829 d, domain [-500, 500]^d              */
+  CHISAO_OBJ_SCHWEFEL = 12,
+  /* -(1/2) sum_i (x_i^4 - 16 x_i^2 + 5 x_i), domain [-5, 5]^d                */
+  CHISAO_OBJ_STYBLINSKI_TANG = 13,
+  /* sum_i sin(x_i) sin(i x_i^2 / pi)^20, domain [0, pi]^d                    */
+  CHISAO_OBJ_MICHALEWICZ = 14,
+  /* -sum_i (x_i - 1)^2 + sum_{i>=2} x_i x_{i-1}, domain [-d^2, d^2]^d        */
+  CHISAO_OBJ_TRID = 15,
+  /* -100 sqrt|x_2 - x_1^2 / 100| - |x_1 + 10| / 100, d = 2,
+   * domain [-15, -5] x [-3, 3]                                              */
+  CHISAO_OBJ_BUKIN6 = 16
 } chisao_objective_kind;
 
 /* How gradients are obtained (Section 3.1: "by finite differences, or
@@ -77,7 +96,8 @@ typedef enum {
  * chisao_create only.  Unused fields may be NULL.
  *   MIXTURE_DIAG: weights[K], means[K][d], sigmas[K][d]  (sigma > 0)
  *   MIXTURE_FULL: weights[K], means[K][d], chol[K][d][d] (lower, diag > 0)
- *   QUADRATIC:    center[d], Q[d][d], lam[d]             (K ignored)        */
+ *   QUADRATIC:    center[d], Q[d][d], lam[d]             (K ignored)
+ *   RASTRIGIN .. BUKIN6: no arrays (K ignored; BUKIN6 requires d = 2)      */
 typedef struct {
   int32_t kind;            /* chisao_objective_kind                          */
   int32_t n_comp;          /* K for mixtures                                 */

@@ -111,6 +111,8 @@ chisao_status validate_params(const chisao_params* p, std::string& why) {
   return CHISAO_OK;
 }
 
+bool is_bench_kind(int kind) { return kind >= CHISAO_OBJ_RASTRIGIN && kind <= CHISAO_OBJ_BUKIN6; }
+
 chisao_status validate_problem(const chisao_problem* pr, std::string& why) {
   if (pr->d < 1 || pr->d > CHISAO_MAX_DIM) { why = "d must be in [1, 64]"; return CHISAO_ERR_ARG; }
   if (pr->n < 1 || pr->n > MAX_N) { why = "n must be in [1, 2^27]"; return CHISAO_ERR_ARG; }
@@ -139,6 +141,8 @@ chisao_status validate_problem(const chisao_problem* pr, std::string& why) {
     }
   } else if (o.kind == CHISAO_OBJ_QUADRATIC) {
     if (!o.center || !o.Q || !o.lam) { why = "quadratic needs center, Q and lam"; return CHISAO_ERR_ARG; }
+  } else if (is_bench_kind(o.kind)) {
+    if (o.kind == CHISAO_OBJ_BUKIN6 && pr->d != 2) { why = "Bukin N.6 needs d = 2"; return CHISAO_ERR_ARG; }
   } else {
     why = "unknown objective kind";
     return CHISAO_ERR_ARG;
@@ -151,7 +155,8 @@ size_t obj_elems(const chisao_problem& pr, int dp, size_t* n0, size_t* n1, size_
   switch (pr.objective.kind) {
     case CHISAO_OBJ_MIXTURE_DIAG: *n0 = K * dp; *n1 = K * dp; *n2 = K; *n3 = 0; break;
     case CHISAO_OBJ_MIXTURE_FULL: *n0 = K * dp; *n1 = K * dp * dp; *n2 = K; *n3 = K * dp * dp; break;
-    default: *n0 = dp; *n1 = (size_t)dp * dp; *n2 = 0; *n3 = 0; break;
+    case CHISAO_OBJ_QUADRATIC: *n0 = dp; *n1 = (size_t)dp * dp; *n2 = 0; *n3 = 0; break;
+    default: *n0 = *n1 = *n2 = *n3 = 0; break;                 // benchmark functions: no constants
   }
   return *n0 + *n1 + *n2 + *n3;
 }
@@ -261,7 +266,7 @@ void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0
         }
       a2[k] = std::log(o.weights[k]) - ld - d * half_log2pi;
     }
-  } else {
+  } else if (o.kind == CHISAO_OBJ_QUADRATIC) {
     for (int j = 0; j < d; ++j) a0[j] = o.center[j];
     for (int a = 0; a < d; ++a)
       for (int b = 0; b < d; ++b) {
@@ -304,8 +309,9 @@ StepParams make_step_params(const chisao_params& p, int d) {
 cudaError_t launch_objective(int which, const ProbHost& ph, int gm, int arg, const EvalArgs* ea, cudaStream_t st) {
   switch (ph.kind) {
     case CHISAO_OBJ_MIXTURE_DIAG: return launch_obj_mixdiag(which, gm, ph.dev, ph.sp, arg, ea, st);
+    case CHISAO_OBJ_QUADRATIC: return launch_obj_quad(which, gm, ph.dev, ph.sp, arg, ea, st);
     case CHISAO_OBJ_MIXTURE_FULL: return launch_obj_mixfull(which, gm, ph.dev, ph.sp, arg, ea, st);
-    default: return launch_obj_quad(which, gm, ph.dev, ph.sp, arg, ea, st);
+    default: return launch_obj_bench(which, gm, ph.dev, ph.sp, arg, ea, st);
   }
 }
 
@@ -601,10 +607,11 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     P.nwords = (int)((ph.n + 31) / 32);
     P.prob_index = q;
     P.m = params->m;
-    P.obj.kind = ph.kind;
+    P.obj.kind = is_bench_kind(ph.kind) ? OBJ_BENCH : ph.kind;
+    P.obj.f32.fn = P.obj.f64.fn = is_bench_kind(ph.kind) ? ph.kind - CHISAO_OBJ_RASTRIGIN : 0;
     P.obj.prob_index = q;
     P.obj.noise_sigma = (float)pr.objective.noise_sigma;
-    P.obj.f32.K = P.obj.f64.K = (ph.kind == CHISAO_OBJ_QUADRATIC) ? 0 : ph.K;
+    P.obj.f32.K = P.obj.f64.K = (ph.kind == CHISAO_OBJ_MIXTURE_DIAG || ph.kind == CHISAO_OBJ_MIXTURE_FULL) ? ph.K : 0;
     P.obj.f32.d = P.obj.f64.d = ph.d;
     P.obj.f32.dp = P.obj.f64.dp = ph.dp;
     ph.sp = make_step_params(*params, ph.d);

@@ -27,6 +27,10 @@ namespace chisao {
 constexpr int MMAX = 10;                 // register-resident L-BFGS memory
 constexpr int GRAD_FD64 = 0, GRAD_FD32 = 1, GRAD_ADJOINT = 2;
 constexpr int OBJ_MIXTURE_DIAG = 1, OBJ_MIXTURE_FULL = 2, OBJ_QUADRATIC = 3;
+// the Appendix D benchmark functions share one kind; ObjParams::fn selects the function
+constexpr int OBJ_BENCH = 10;
+constexpr int FN_RASTRIGIN = 0, FN_ACKLEY = 1, FN_SCHWEFEL = 2, FN_STYBLINSKI_TANG = 3, FN_MICHALEWICZ = 4,
+              FN_TRID = 5, FN_BUKIN6 = 6;
 constexpr int RESEED_NONE = 0, RESEED_RM = 1, RESEED_GR = 2, RESEED_UNIFORM = 3;
 // Philox stream tags (same layout as the paper-side definition of the method's
 // random draws; see the stream description in the library documentation).
@@ -42,6 +46,7 @@ constexpr unsigned TAG_RM = 1, TAG_RM_DIR = 2, TAG_GR_MAT = 3, TAG_GR_T = 4,
 template <typename T>
 struct ObjParams {
   int K, d, dp;
+  int fn;                       // benchmark function (OBJ_BENCH)
   const T* p0;
   const T* p1;
   const T* p2;
@@ -195,6 +200,15 @@ struct Grp {
   template <typename T>
   __device__ __forceinline__ T bcast(T v, int src) const {
     return __shfl_sync(mask, v, src, LPS);
+  }
+  // the value held by the previous / next lane of the group (the first / last lane gets its own)
+  template <typename T>
+  __device__ __forceinline__ T from_prev(T v) const {
+    return __shfl_up_sync(mask, v, 1, LPS);
+  }
+  template <typename T>
+  __device__ __forceinline__ T from_next(T v) const {
+    return __shfl_down_sync(mask, v, 1, LPS);
   }
   __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
   __device__ __forceinline__ unsigned xor_all(unsigned v) const {

@@ -16,6 +16,18 @@ cudaError_t launch_obj_mixfull(int which, int gm, const ProbDev& P, const StepPa
                                const EvalArgs* ea, cudaStream_t st);
 cudaError_t launch_obj_quad(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
                             const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                             const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench_4(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                                 const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench_8(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                                 const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench_16(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                                 const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench_32(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                                 const EvalArgs* ea, cudaStream_t st);
+cudaError_t launch_obj_bench_64(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
+                                 const EvalArgs* ea, cudaStream_t st);
 
 // objective-independent kernels
 cudaError_t launch_cycle_begin(const ProbDev& P, cudaStream_t st);

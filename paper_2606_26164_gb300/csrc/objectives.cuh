@@ -11,6 +11,8 @@
 //  * Rotated quadratic f = -(x - c)^T A (x - c), A = Q^T diag(lam) Q:
 //    u = A (x - c), f = -(x - c)^T u, grad f = -2 u (one matrix-vector product
 //    gives both).
+//  * The Appendix D benchmark functions (separable sums, Ackley's two group
+//    sums, Trid's neighbour products), one kind with a runtime function id.
 //
 // Lane l of a group holds the V consecutive coordinates V l .. V l + V - 1.
 // A product with a d x d matrix walks the rows in blocks of V: the V values of
@@ -82,21 +84,21 @@ __device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&
       out[2 * w] = acc[w].x;
       out[2 * w + 1] = acc[w].y;
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int w = 0; w < V; ++w) out[w] = T(0);
-  const T* col = M + V * g.l;
-  const int nb = (d + V - 1) / V;
+    for (int w = 0; w < V; ++w) out[w] = T(0);
+    const T* col = M + V * g.l;
+    const int nb = (d + V - 1) / V;
 #pragma unroll 2
-  for (int jb = 0; jb < nb; ++jb) {
+    for (int jb = 0; jb < nb; ++jb) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T rj = g.bcast(r[v], jb);
-      T a[V];
-      ldg_vec<T, V>(col + (size_t)(jb * V + v) * dp, a);
+      for (int v = 0; v < V; ++v) {
+        const T rj = g.bcast(r[v], jb);
+        T a[V];
+        ldg_vec<T, V>(col + (size_t)(jb * V + v) * dp, a);
 #pragma unroll
-      for (int w = 0; w < V; ++w) out[w] = fma(a[w], rj, out[w]);
+        for (int w = 0; w < V; ++w) out[w] = fma(a[w], rj, out[w]);
+      }
     }
   }
 }
@@ -228,6 +230,147 @@ struct Obj<OBJ_QUADRATIC> {
 #pragma unroll
     for (int v = 0; v < V; ++v) gr[v] = T(-2) * u[v];
     return f;
+  }
+};
+
+// ------------------------------------------------------------ Appendix D benchmark functions
+// Negated (maximisation) forms, coordinate i = j + 1 for the lane's coordinate j;
+// padded coordinates (j >= d) contribute nothing.  Non-differentiable points take
+// the zero subgradient of the offending term (Ackley at x = 0, Bukin N.6 on its
+// ridge and at x_1 = -10).
+template <typename T>
+__device__ __forceinline__ T cospi_t(T v) {
+  if constexpr (std::is_same<T, float>::value) return cospif(v); else return cospi(v);
+}
+template <typename T>
+__device__ __forceinline__ T sinpi_t(T v) {
+  if constexpr (std::is_same<T, float>::value) return sinpif(v); else return sinpi(v);
+}
+template <typename T>
+__device__ __forceinline__ T sgn(T v) {
+  return (T)((v > T(0)) - (v < T(0)));
+}
+
+template <>
+struct Obj<OBJ_BENCH> {
+  // f, and with GR the gradient, at the lane group's point
+  template <bool GR, typename T, int V, int LPS>
+  static __device__ __forceinline__ T eval(const ObjParams<T>& o, const T (&x)[V], T (&gr)[V], const Grp<LPS>& g) {
+    const int d = o.d;
+    const int j0 = V * g.l;
+    T acc = T(0);
+    switch (o.fn) {
+      case FN_RASTRIGIN: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const bool in = j0 + v < d;
+          const T c = cospi_t(T(2) * x[v]);
+          if (in) acc -= x[v] * x[v] - T(10) * c + T(10);
+          if (GR) gr[v] = in ? -(T(2) * x[v] + T(2) * T(CUDART_PI) * T(10) * sinpi_t(T(2) * x[v])) : T(0);
+        }
+        return g.sum(acc);
+      }
+      case FN_ACKLEY: {
+        T s2 = T(0), sc = T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (j0 + v < d) {
+            s2 += x[v] * x[v];
+            sc += cospi_t(T(2) * x[v]);
+          }
+        s2 = g.sum(s2);
+        sc = g.sum(sc);
+        const T r = sqrt(s2 / T(d));
+        const T e1 = exp(T(-0.2) * r), e2 = exp(sc / T(d));
+        if (GR) {
+          const T radial = r > T(0) ? T(-20) * T(0.2) * e1 / (T(d) * r) : T(0);
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            gr[v] = (j0 + v < d) ? radial * x[v] - T(2) * T(CUDART_PI) / T(d) * e2 * sinpi_t(T(2) * x[v]) : T(0);
+        }
+        return T(20) * e1 + e2 - T(20) - T(2.718281828459045);
+      }
+      case FN_SCHWEFEL: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const bool in = j0 + v < d;
+          const T s = sqrt(fabs(x[v]));
+          const T sn = sin(s);
+          if (in) acc += x[v] * sn;
+          if (GR) gr[v] = in ? sn + T(0.5) * s * cos(s) : T(0);
+        }
+        return g.sum(acc) - T(418.9829) * T(d);
+      }
+      case FN_STYBLINSKI_TANG: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const bool in = j0 + v < d;
+          const T x2 = x[v] * x[v];
+          if (in) acc += x2 * x2 - T(16) * x2 + T(5) * x[v];
+          if (GR) gr[v] = in ? T(-0.5) * (T(4) * x2 * x[v] - T(32) * x[v] + T(5)) : T(0);
+        }
+        return T(-0.5) * g.sum(acc);
+      }
+      case FN_MICHALEWICZ: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const bool in = j0 + v < d;
+          const T i = T(j0 + v + 1);
+          const T u = i * x[v] * x[v] / T(CUDART_PI);
+          const T su = sin(u), s2 = su * su, s4 = s2 * s2, s8 = s4 * s4, s16 = s8 * s8;
+          const T s20 = s16 * s4, s19 = s16 * s2 * su;
+          const T sx = sin(x[v]);
+          if (in) acc += sx * s20;
+          if (GR)
+            gr[v] = in ? cos(x[v]) * s20 + sx * T(20) * s19 * cos(u) * (T(2) * i * x[v] / T(CUDART_PI)) : T(0);
+        }
+        return g.sum(acc);
+      }
+      case FN_TRID: {
+        // neighbours across the lane boundary come from the previous / next lane
+        const T prev_last = g.from_prev(x[V - 1]);
+        const T next_first = g.from_next(x[0]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int j = j0 + v;
+          const bool in = j < d;
+          const T prev = v > 0 ? x[v - 1] : prev_last;
+          const T next = v < V - 1 ? x[v + 1] : next_first;
+          const T dm = x[v] - T(1);
+          if (in) acc += -dm * dm + (j >= 1 ? x[v] * prev : T(0));
+          if (GR) gr[v] = in ? T(-2) * dm + (j >= 1 ? prev : T(0)) + (j + 1 < d ? next : T(0)) : T(0);
+        }
+        return g.sum(acc);
+      }
+      default: {                                    // FN_BUKIN6: d = 2, both coordinates in lane 0
+        T f = T(0);
+        if (GR) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) gr[v] = T(0);
+        }
+        if (g.l == 0) {
+          const T w = x[1] - T(0.01) * x[0] * x[0];
+          const T aw = fabs(w);
+          f = T(-100) * sqrt(aw) - T(0.01) * fabs(x[0] + T(10));
+          if (GR) {
+            const T dw = aw > T(0) ? T(-50) * sgn(w) / sqrt(aw) : T(0);
+            gr[0] = dw * (T(-0.02) * x[0]) - T(0.01) * sgn(x[0] + T(10));
+            gr[1] = dw;
+          }
+        }
+        return g.sum(f);
+      }
+    }
+  }
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value(const ObjParams<T>& o, const T (&x)[V], const Grp<LPS>& g) {
+    T unused[V];
+    return eval<false, T, V, LPS>(o, x, unused, g);
+  }
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ T value_grad(const ObjParams<T>& o, const T (&x)[V], T (&gr)[V],
+                                                 const Grp<LPS>& g) {
+    return eval<true, T, V, LPS>(o, x, gr, g);
   }
 };
 

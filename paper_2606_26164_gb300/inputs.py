@@ -24,6 +24,10 @@ Workloads (problem statement in Section 3.1; objectives below):
   {2,4,8,16,32,64}, N log-uniform in [256, 16384], K log-uniform integer in
   [4, 128], sigma uniform in [0.3, 1], means uniform in [-10, 10]^d, equal
   weights.
+* ``benchmark(name, d, n)`` -- the Appendix D benchmark functions (Rastrigin,
+  Ackley, Schwefel, Styblinski-Tang, Michalewicz, Trid, Bukin N.6) on their
+  App. D domains, population uniform in the domain; ``rastrigin_d64`` etc.
+  name the d = 64, N = 65536 cases.
 
 The Gaussian-mixture family follows the mixture definition of Appendix D
 (log of a weighted sum of Gaussian densities); the noise model of Section 5.6
@@ -40,6 +44,9 @@ import numpy as np
 OBJ_MIXTURE_DIAG = 1
 OBJ_MIXTURE_FULL = 2
 OBJ_QUADRATIC = 3
+# Appendix D benchmark functions (no parameters beyond d)
+BENCHMARK_KINDS = {"rastrigin": 10, "ackley": 11, "schwefel": 12, "styblinski_tang": 13, "michalewicz": 14,
+                   "trid": 15, "bukin6": 16}
 
 
 @dataclasses.dataclass
@@ -195,10 +202,37 @@ def small_full_mixture(d: int, K: int, n: int, seed: int, box: float = 8.0) -> P
     return Problem(d, n, lo, hi, obj, _uniform_box(rng, n, lo, hi), eps_grad=1e-2, sigma_mode=0.3)
 
 
+def benchmark_box(name: str, d: int):
+    """The domain Theta each benchmark function is stated on in Appendix D."""
+    half = {"rastrigin": 5.12, "ackley": 32.768, "schwefel": 500.0, "styblinski_tang": 5.0,
+            "trid": float(d * d)}
+    if name in half:
+        return np.full(d, -half[name]), np.full(d, half[name])
+    if name == "michalewicz":
+        return np.zeros(d), np.full(d, np.pi)
+    if name == "bukin6":
+        if d != 2:
+            raise ValueError("Bukin N.6 is two-dimensional")
+        return np.array([-15.0, -3.0]), np.array([-5.0, 3.0])
+    raise KeyError(name)
+
+
+def benchmark(name: str, d: int = 64, n: int = 65536, seed: int = 0, eps_grad: float = 1e-3) -> Problem:
+    """An Appendix D benchmark function on its domain, population uniform in it."""
+    rng = np.random.default_rng(9000 + seed)
+    lo, hi = benchmark_box(name, d)
+    obj = Objective(BENCHMARK_KINDS[name], d, {})
+    return Problem(d, n, lo, hi, obj, _uniform_box(rng, n, lo, hi), eps_grad=eps_grad, sigma_mode=1.0)
+
+
 WORKLOADS = {
     "mixture4_d2": mixture4_d2,
     "mixture32_d16": mixture32_d16,
     "quadratic_d64": quadratic_d64,
     "mixture256_d64": mixture256_d64,
 }
+for _name in BENCHMARK_KINDS:
+    if _name != "bukin6":
+        WORKLOADS[_name + "_d64"] = (lambda nm: (lambda seed=0, n=65536: benchmark(nm, 64, n, seed)))(_name)
+
 
