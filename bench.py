@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNELS_PER_STEP = 18   # kernel launches in one non-final cycle of one problem
+KERNELS_PER_STEP = 22   # kernel launches in one non-final cycle of one problem
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the population size (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=2, help="cycles of the full-covariance tensor-core leg")
     ap.add_argument("--batched-steps", type=int, default=3, help="cycles of the 512-problem leg")
+    ap.add_argument("--bench-fn-steps", type=int, default=3, help="cycles of each benchmark-function leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -60,9 +61,9 @@ def launches_per_step(params, tc, d):
         return KERNELS_PER_STEP
     n_conv = params.n_conv or max(10, int(np.ceil(3 * np.log2(d))))
     # cycle begin + first evaluation, per L-BFGS iteration one direction kernel and T_ls
-    # (evaluation, acceptance) pairs, freeze/dedup/reseed (9), HLC and anti with their scale
-    # passes, cycle end
-    return (2 + n_conv * (1 + 2 * params.T_ls) + 9 + (3 + 3 * params.n_cloud)
+    # (evaluation, acceptance) pairs, freeze (3) / dedup (6) / reseed (4), HLC and anti with
+    # their scale passes, cycle end
+    return (2 + n_conv * (1 + 2 * params.T_ls) + 13 + (3 + 3 * params.n_cloud)
             + (2 + 2 * params.n_anti) + 1)
 
 
@@ -296,6 +297,23 @@ def batched_leg(CH, steps):
             "ms_per_step": 1e3 * t / steps, "steps": steps, "grad": "adjoint"}
 
 
+def benchmark_functions_leg(CH, steps, n_osc):
+    """The Appendix D benchmark functions at d = 64 (Bukin N.6: d = 2), N = 65536,
+    exact gradients: samples x cycles per second and evaluations per second."""
+    from paper_2606_26164_gb300 import inputs as I
+    res = {}
+    for name in I.BENCHMARK_KINDS:
+        d = 2 if name == "bukin6" else 64
+        prob = I.benchmark(name, d, 65536, seed=0)
+        prm = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=GRAD["adjoint"], seed=0)
+        model = CH.Chisao([prob], prm)
+        t, c0, c1 = gpu_timed(model, steps, 2)
+        res[f"{name}_d{d}"] = {"value": prob.n * steps / t, "unit": "sample-cycles/s", "ms_per_step": 1e3 * t / steps,
+                               "evals_per_s": (c1["evals"] - c0["evals"]) / t}
+        model.close()
+    return res
+
+
 def main():
     args = parse()
     if args.cpu_leg:
@@ -392,6 +410,9 @@ def main():
         # --- 512 problems of uneven size in one context (cycle graph with one branch per stream)
         if args.workload == "quadratic_d64" and args.batched_steps > 0:
             out["batched512"] = batched_leg(CH, args.batched_steps)
+        # --- the Appendix D benchmark functions
+        if args.workload == "quadratic_d64" and args.bench_fn_steps > 0:
+            out["benchmark_functions"] = benchmark_functions_leg(CH, args.bench_fn_steps, n_osc)
         # --- end to end through the C ABI: pinned host population in, modes out, every step
         xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
         xh.copy_(torch.from_numpy(prob.x0))

@@ -186,6 +186,14 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
   P.partials = b.take<float2>((size_t)MAX_PART_BLOCKS * (2 * dp + 2));
   P.max_part_blocks = MAX_PART_BLOCKS;
   P.grq = b.take<double>((size_t)d * d);
+  size_t slots = 1;
+  while (slots < 2 * n) slots <<= 1;
+  P.hkey = b.take<unsigned long long>(slots);
+  P.hhead = b.take<int>(slots);
+  P.hnext = b.take<int>(n);
+  P.hmask = (int)(slots - 1);
+  P.hspread = b.take<unsigned>(2 * (size_t)dp);
+  P.haxes = b.take<int>(4);
   size_t n0, n1, n2, n3;
   obj_elems(pr, dp, &n0, &n1, &n2, &n3);
   P.obj.f32.p0 = b.take<float>(n0);

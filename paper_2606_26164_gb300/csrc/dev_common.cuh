@@ -108,6 +108,14 @@ struct ProbDev {
   float2* partials;             // [max_part_blocks][2 dp + 2] double-single sums
   int max_part_blocks;
   double* grq;                  // Golden Rooster Q [d][d], column-major
+  // Phase 3 spatial hash: open addressing over 2^k >= 2 n slots, one list of stuck
+  // samples per cell key (head per slot, next per stuck-list position)
+  unsigned long long* hkey;
+  int* hhead;
+  int* hnext;
+  int hmask;
+  unsigned* hspread;            // [2][dp] ordered-key min and max of each coordinate over the stuck set
+  int* haxes;                   // [4] the hashed coordinates (-1 unused) and their count
   ObjDev obj;
 };
 

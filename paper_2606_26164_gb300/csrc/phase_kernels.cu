@@ -3,6 +3,8 @@
 // deduplication (Phase 3, Eq. 4), the reseeding strategies (Phase 4,
 // Sec. 3.2.4) with the Golden Rooster's FP64 Householder QR, and the scale
 // estimates' final reduction (Phases 5/6).
+#include <algorithm>
+
 #include "host.h"
 #include "dev_common.cuh"
 
@@ -136,8 +138,110 @@ __global__ void __launch_bounds__(NT_ONE) k_compact_dedup(ProbDev P) {
 
 // ------------------------------------------------------------ Phase 3
 // For every stuck x_j: removed iff some other stuck x_i ranks above it
-// (f desc, index asc) and max_k |x_ik - x_jk| < eps_dup (binary32).  The scan
-// over i stops at the first such neighbour.
+// (f desc, index asc) and max_k |x_ik - x_jk| < eps_dup (binary32).
+//
+// Candidates come from a spatial hash (App. A: the L-inf ball is a hypercube):
+// each stuck sample is filed under the cells floor((x_a - lo_a) / h) of the three
+// coordinates a along which the stuck set is most spread, h = eps_dup (1 + 1e-6).
+// Any pair the binary32 test can accept is closer than eps_dup (1 + 2^-23) in
+// every coordinate, so with h slightly above that (and the cell computed in FP64)
+// their cells differ by at most one along each hashed axis: the 27 neighbouring
+// cells hold every candidate, and the exact test on them decides as the pairwise
+// scan would.  The outcome is order-free, so the mask is the same bit for bit.
+constexpr unsigned long long HASH_EMPTY = ~0ull;
+
+__device__ __forceinline__ unsigned ordered_bits(float v) {   // monotone map float -> unsigned
+  const unsigned u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_bits(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ unsigned long long cell_key(long long c0, long long c1, long long c2) {
+  unsigned long long k = (unsigned long long)c0 * 0x9E3779B97F4A7C15ull;      // splitmix-style mixing
+  k ^= (unsigned long long)c1 * 0xC2B2AE3D27D4EB4Full + (k >> 29);
+  k ^= (unsigned long long)c2 * 0x165667B19E3779F9ull + (k >> 31);
+  k ^= k >> 33;
+  k *= 0xFF51AFD7ED558CCDull;
+  k ^= k >> 33;
+  return k == HASH_EMPTY ? 0ull : k;
+}
+__device__ __forceinline__ long long cell_of(float x, float lo, double h) {
+  return (long long)floor(((double)x - (double)lo) / h);
+}
+
+// table slots empty, coordinate spreads reset
+__global__ void __launch_bounds__(NT_LIN) k_hash_clear(ProbDev P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P.cnt->n_stuck0 == 0) return;
+  for (int s = t; s <= P.hmask; s += gridDim.x * blockDim.x) {
+    P.hkey[s] = HASH_EMPTY;
+    P.hhead[s] = -1;
+  }
+  if (t < P.dp) {
+    P.hspread[t] = 0xFFFFFFFFu;
+    P.hspread[P.dp + t] = 0u;
+  }
+}
+
+// per-coordinate min and max over the stuck set
+__global__ void __launch_bounds__(NT_LIN) k_hash_spread(ProbDev P) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Sn = P.cnt->n_stuck0;
+  if (t >= (long long)Sn * P.d) return;
+  const int jj = (int)(t / P.d), a = (int)(t % P.d);
+  const unsigned k = ordered_bits(P.x[(size_t)P.l_stuck[jj] * P.dp + a]);
+  atomicMin(&P.hspread[a], k);
+  atomicMax(&P.hspread[P.dp + a], k);
+}
+
+// the (up to) three coordinates of largest spread, largest first (ties: lower index)
+__global__ void k_hash_axes(ProbDev P) {
+  if (threadIdx.x != 0 || P.cnt->n_stuck0 == 0) return;
+  int ax[3] = {-1, -1, -1};
+  float sp[3] = {-1.f, -1.f, -1.f};
+  for (int a = 0; a < P.d; ++a) {
+    const float w = from_ordered_bits(P.hspread[P.dp + a]) - from_ordered_bits(P.hspread[a]);
+    for (int r = 0; r < 3; ++r) {
+      if (w > sp[r]) {
+        for (int q = 2; q > r; --q) {
+          sp[q] = sp[q - 1];
+          ax[q] = ax[q - 1];
+        }
+        sp[r] = w;
+        ax[r] = a;
+        break;
+      }
+    }
+  }
+  for (int r = 0; r < 3; ++r) P.haxes[r] = ax[r];
+}
+
+__device__ __forceinline__ void sample_cells(const ProbDev& P, int i, double h, long long (&c)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int a = P.haxes[r];
+    c[r] = a >= 0 ? cell_of(P.x[(size_t)i * P.dp + a], P.lo[a], h) : 0;
+  }
+}
+
+// file every stuck sample under its cell key
+__global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S) {
+  const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jj >= P.cnt->n_stuck0) return;
+  const double h = (double)S.eps_dup * (1.0 + 1e-6);
+  long long c[3];
+  sample_cells(P, P.l_stuck[jj], h, c);
+  const unsigned long long key = cell_key(c[0], c[1], c[2]);
+  unsigned slot = (unsigned)key & (unsigned)P.hmask;
+  for (int probe = 0; probe <= P.hmask; ++probe) {     // the table has at least 2 n slots: a free one exists
+    const unsigned long long prev = atomicCAS(&P.hkey[slot], HASH_EMPTY, key);
+    if (prev == HASH_EMPTY || prev == key) break;
+    slot = (slot + 1) & (unsigned)P.hmask;
+  }
+  P.hnext[jj] = atomicExch(&P.hhead[slot], jj);
+}
+
 template <int DP>
 __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
   constexpr int LPS = DP / 2;
@@ -150,18 +254,37 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
   const float2 xj = *reinterpret_cast<const float2*>(P.x + (size_t)j * DP + c0);
   const float fj = P.f[j];
   const float eps = S.eps_dup;
+  const double h = (double)eps * (1.0 + 1e-6);
+  long long cj[3];
+  sample_cells(P, j, h, cj);
+  const int na = (P.haxes[0] >= 0) + (P.haxes[1] >= 0) + (P.haxes[2] >= 0);
+  int span[3];
+  for (int r = 0; r < 3; ++r) span[r] = r < na ? 1 : 0;
   bool rem = false;
-  for (int ii = 0; ii < Sn; ++ii) {
-    const int i = P.l_stuck[ii];
-    if (i == j) continue;
-    const float fi = P.f[i];
-    if (!(fi > fj || (fi == fj && i < j))) continue;
-    const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
-    if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) {
-      rem = true;
-      break;
-    }
-  }
+  for (int d0 = -span[0]; d0 <= span[0] && !rem; ++d0)
+    for (int d1 = -span[1]; d1 <= span[1] && !rem; ++d1)
+      for (int d2 = -span[2]; d2 <= span[2] && !rem; ++d2) {
+        const unsigned long long key = cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2);
+        unsigned slot = (unsigned)key & (unsigned)P.hmask;
+        int head = -1;
+        for (int probe = 0; probe <= P.hmask; ++probe) {
+          const unsigned long long k = P.hkey[slot];
+          if (k == key) {
+            head = P.hhead[slot];
+            break;
+          }
+          if (k == HASH_EMPTY) break;
+          slot = (slot + 1) & (unsigned)P.hmask;
+        }
+        for (int ii = head; ii >= 0 && !rem; ii = P.hnext[ii]) {
+          const int i = P.l_stuck[ii];
+          if (i == j) continue;
+          const float fi = P.f[i];
+          if (!(fi > fj || (fi == fj && i < j))) continue;
+          const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
+          if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) rem = true;
+        }
+      }
   if (rem && g.l == 0) atomicOr(&P.removed[j >> 5], 1u << (j & 31));
 }
 
@@ -496,6 +619,11 @@ static void dedup_dp(const ProbDev& P, const StepParams& S, cudaStream_t st) {
 
 cudaError_t launch_dedup(const ProbDev& P, const StepParams& S, cudaStream_t st) {
   cudaMemsetAsync(P.removed, 0, sizeof(uint32_t) * P.nwords, st);
+  const long long slots = (long long)P.hmask + 1;
+  k_hash_clear<<<(unsigned)std::min<long long>(lin_blocks(slots, NT_LIN), 1024), NT_LIN, 0, st>>>(P);
+  k_hash_spread<<<lin_blocks((long long)P.n * P.d, NT_LIN), NT_LIN, 0, st>>>(P);
+  k_hash_axes<<<1, 32, 0, st>>>(P);
+  k_hash_insert<<<lin_blocks(P.n, NT_LIN), NT_LIN, 0, st>>>(P, S);
   switch (P.dp) {
     case 4: dedup_dp<4>(P, S, st); break;
     case 8: dedup_dp<8>(P, S, st); break;

@@ -305,6 +305,44 @@ def test_dedup_bit_exact(d):
     model.close()
 
 
+@pytest.mark.parametrize("case", ["one_axis", "two_axes", "flat_axes", "boundaries"])
+def test_dedup_hash_geometry(case):
+    """Candidate generation by spatial hashing on the most-spread coordinates:
+    the same mask as the pairwise definition when fewer than three coordinates
+    vary, when the stuck set is constant along most axes, and for pairs that
+    straddle cell boundaries by less than eps in every coordinate."""
+    rng = np.random.default_rng(hash(case) % 2 ** 32)
+    d = {"one_axis": 1, "two_axes": 2, "flat_axes": 6, "boundaries": 4}[case]
+    N = 2049
+    prob = I.small_mixture(d, 2, N, seed=12)
+    P = M.Params(eps_dup=1e-3)
+    model = U.open_ctx(prob, P)
+    if case == "boundaries":
+        base = rng.uniform(-2, 2, (N // 2 + 1, d))
+        # partners within eps along every coordinate (|offset| from 0.5 eps to just under eps), or just over
+        off = rng.choice([-1.0, 1.0], (N // 2 + 1, d)) * rng.uniform(0.5e-3, 0.999e-3, (N // 2 + 1, d))
+        off[::3, 0] = 1.001e-3
+        x = np.concatenate([base, base + off])[:N]
+    else:
+        x = np.tile(rng.uniform(-3, 3, (1, d)), (N, 1))
+        vary = {"one_axis": [0], "two_axes": [0, 1], "flat_axes": [4]}[case]
+        for a in vary:
+            x[:, a] = rng.uniform(-3, 3, 40)[rng.integers(0, 40, N)] + rng.uniform(-1.5e-3, 1.5e-3, N)
+    x = x.astype(np.float32)
+    f = np.round(rng.normal(0, 1, N), 1).astype(np.float32)
+    stuck = rng.random(N) < 0.8
+    st = M.new_state(x, P.m)
+    st.f = f.astype(np.float64)
+    st.stuck = stuck
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_DEDUP)
+    rem = CH.unpack_bits(model.get(0, CH.FIELD_REMOVED), N)
+    ref = M.dedup(x, f, stuck, P.eps_dup, dtype=np.float32)
+    assert ref.sum() > 0 and (stuck & ~ref).sum() > 1
+    np.testing.assert_array_equal(rem, ref)
+    model.close()
+
+
 def test_dedup_edge_cases():
     prob = I.small_mixture(3, 2, 33, seed=11)
     P = M.Params(eps_dup=1e-3)
