@@ -15,9 +15,10 @@
 //    sums, Trid's neighbour products), one kind with a runtime function id.
 //
 // Lane l of a group holds the V consecutive coordinates V l .. V l + V - 1.
-// A product with a d x d matrix walks the rows in blocks of V: the V values of
-// the block are broadcast from their owner lane with register shuffles, and
-// the matrix row is read as one V-wide vector contiguous across the group (all
+// A product with a d x d matrix walks the rows in blocks of V: in binary32 the
+// group's vector is staged once in shared memory and each block of V values is
+// one broadcast load (FP64: register shuffles from the owner lane), and the
+// matrix row is read as one V-wide vector contiguous across the group (all
 // groups of a warp read the same row, so the load is shared).
 #pragma once
 #include <type_traits>
@@ -61,24 +62,33 @@ __device__ __forceinline__ void lse_push_grad(T& m, T& s, T (&G)[V], T lc, const
 template <typename T, int V, int LPS>
 __device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&r)[V], T (&out)[V],
                                            const Grp<LPS>& g) {
-  if constexpr (std::is_same<T, float>::value && V % 2 == 0) {
+  if constexpr (std::is_same<T, float>::value && V == 4) {
+    // the group's vector r is staged once in shared memory (each lane its four values)
+    // and read back four at a time as one broadcast load, instead of a register shuffle
+    // per element
+    __shared__ float4 rstage[1024];
+    rstage[threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
+    __syncwarp(g.mask);
+    const float4* grp = rstage + (threadIdx.x - g.l);
     float2 acc[V / 2];
 #pragma unroll
     for (int w = 0; w < V / 2; ++w) acc[w] = make_float2(0.f, 0.f);
     const float* col = M + V * g.l;
     const int nb = (d + V - 1) / V;
-#pragma unroll 2
+#pragma unroll 1
     for (int jb = 0; jb < nb; ++jb) {
+      const float4 rb = grp[jb];
+      const float rv[4] = {rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const float rj = g.bcast(r[v], jb);
         float a[V];
         ldg_vec<float, V>(col + (size_t)(jb * V + v) * dp, a);
-        const float2 r2 = make_float2(rj, rj);
+        const float2 r2 = make_float2(rv[v], rv[v]);
 #pragma unroll
         for (int w = 0; w < V / 2; ++w) acc[w] = __ffma2_rn(make_float2(a[2 * w], a[2 * w + 1]), r2, acc[w]);
       }
     }
+    __syncwarp(g.mask);                           // the stage is reused by the next product
 #pragma unroll
     for (int w = 0; w < V / 2; ++w) {
       out[2 * w] = acc[w].x;
