@@ -155,6 +155,11 @@ typedef struct {
   int32_t use_graph;       /* 1: capture each cycle in a CUDA graph           */
   int32_t n_refine;        /* CHISAO_GRAD_ADJOINT_TC: FP32 L-BFGS steps on the
                               survivors after the last cycle (exact objective) */
+  int32_t hlc_value_only;  /* 0: Phase 5 averages gradients at x + sigma z_k (Eq. 5);
+                              1: the value-only estimator (1/M) sum_k
+                              (f(x + sigma z_k) - f(x)) z_k / sigma (the Gaussian-
+                              smoothing estimator Sec. 3.2.5 cites; a variant, not
+                              Eq. 5), M + 1 evaluations per step in every grad_mode */
 } chisao_params;
 
 /* Per-problem counters accumulated on the device since create. */

@@ -65,6 +65,7 @@ class Params:
     seed: int = 0
     rm_min_unfrozen: int = 5   # Repulse Monkey needs >= 5 unfrozen samples
     gr_patience: int = 2       # Golden Rooster disables after 2 generations without new peaks
+    hlc_value_only: int = 0    # 1: Phase 5 with the value-only smoothing estimator (a variant)
 
     def n_conv_for(self, d: int) -> int:
         if self.n_conv > 0:
@@ -463,7 +464,10 @@ def hlc(prob, st: State, P: Params, cycle: int, prob_index: int = 0):
     """n_cloud ascent steps x <- clip(x + alpha_h * (1/M) sum_k grad f(x + sigma z_k))
     on unfrozen samples, z_k from the TAG_HLC stream (c0 = sample index,
     step = cloud step, k = perturbation).  The step alpha_h follows the same
-    auto rule as the anti-convergence step, evaluated at the phase start."""
+    auto rule as the anti-convergence step, evaluated at the phase start.
+    With P.hlc_value_only the gradients are replaced by the value-only
+    Gaussian-smoothing estimator (f(x + sigma z_k) - f(x)) z_k / sigma (a
+    variant of Eq. 5 built from M + 1 evaluations)."""
     unfrozen = ~st.stuck
     if not unfrozen.any() or P.n_cloud == 0:
         return None
@@ -472,9 +476,14 @@ def hlc(prob, st: State, P: Params, cycle: int, prob_index: int = 0):
     d = prob.d
     for t in range(P.n_cloud):
         acc = np.zeros_like(X)
+        f0 = evaluate(prob, X, st, P.seed, prob_index) if P.hlc_value_only else None
         for k in range(P.M):
             z = PX.normal_rows(P.seed, idx, d, PX.TAG_HLC, cycle, t, prob_index, k)
-            acc += gradient(prob, X + sigma * z, P, st)
+            if P.hlc_value_only:
+                # Gaussian-smoothing estimator from values only: (f(x + sigma z) - f(x)) z / sigma
+                acc += ((evaluate(prob, X + sigma * z, st, P.seed, prob_index) - f0) / sigma)[:, None] * z
+            else:
+                acc += gradient(prob, X + sigma * z, P, st)
         X = np.clip(X + alpha * (acc / P.M), prob.lo, prob.hi)
     st.x[idx] = X
     st.hlen[idx] = 0

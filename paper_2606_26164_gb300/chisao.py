@@ -38,7 +38,8 @@ class CParams(C.Structure):
                 ("alpha", C.c_double), ("sigma", C.c_double), ("c_sigma", C.c_double),
                 ("alpha_scale", C.c_double), ("h", C.c_double), ("h_rel", C.c_double), ("c1", C.c_double),
                 ("curv_eps", C.c_double), ("seed", C.c_uint64), ("rm_min_unfrozen", C.c_int32),
-                ("gr_patience", C.c_int32), ("use_graph", C.c_int32), ("n_refine", C.c_int32)]
+                ("gr_patience", C.c_int32), ("use_graph", C.c_int32), ("n_refine", C.c_int32),
+                ("hlc_value_only", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)

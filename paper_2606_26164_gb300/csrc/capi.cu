@@ -103,6 +103,11 @@ chisao_status validate_params(const chisao_params* p, std::string& why) {
   if (p->n_cloud > 255) { why = "n_cloud must be <= 255"; return CHISAO_ERR_ARG; }
   if (p->grad_mode < 0 || p->grad_mode > 3) { why = "unknown grad_mode"; return CHISAO_ERR_ARG; }
   if (p->n_refine < 0) { why = "n_refine must be >= 0"; return CHISAO_ERR_ARG; }
+  if (p->hlc_value_only != 0 && p->hlc_value_only != 1) { why = "hlc_value_only must be 0 or 1"; return CHISAO_ERR_ARG; }
+  if (p->hlc_value_only && p->grad_mode == CHISAO_GRAD_ADJOINT_TC) {
+    why = "the value-only smoothing estimator is not available with the tensor-core mode";
+    return CHISAO_ERR_ARG;
+  }
   if (!(p->eps_grad > 0) || !(p->eps_dup > 0)) { why = "eps_grad and eps_dup must be > 0"; return CHISAO_ERR_ARG; }
   if (!(p->delta > 0 && p->delta < 1)) { why = "delta must be in (0, 1)"; return CHISAO_ERR_ARG; }
   if (!(p->h > 0) || !(p->h_rel > 0) || !(p->c1 > 0 && p->c1 < 1)) { why = "h, h_rel > 0 and c1 in (0,1) required"; return CHISAO_ERR_ARG; }
@@ -289,6 +294,7 @@ StepParams make_step_params(const chisao_params& p, int d) {
   StepParams s{};
   s.n_conv = p.n_conv > 0 ? p.n_conv : (d > 1 ? std::max(10, (int)std::ceil(3.0 * std::log2((double)d))) : 10);
   s.n_anti = p.n_anti;
+  s.hlc_value_only = p.hlc_value_only;
   s.n_cloud = p.n_cloud;
   s.M = p.M;
   s.m = p.m;

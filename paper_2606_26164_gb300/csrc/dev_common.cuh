@@ -120,7 +120,7 @@ struct ProbDev {
 };
 
 struct StepParams {
-  int n_conv, n_anti, n_cloud, M, m, T_ls, grad_mode, rm_min, gr_patience, n_refine;
+  int n_conv, n_anti, n_cloud, M, m, T_ls, grad_mode, rm_min, gr_patience, n_refine, hlc_value_only;
   float eps_grad, eps_dup, log_delta, mu, alpha_fixed, sigma_fixed, c_sigma, alpha_scale;
   double h, h_rel, c1, curv_eps;
   unsigned seed_lo, seed_hi;

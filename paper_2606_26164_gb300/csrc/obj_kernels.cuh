@@ -353,19 +353,29 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
     ld_vec<V>(P.lo + j0, lo);
     ld_vec<V>(P.hi + j0, hi);
     const float invM = 1.0f / (float)S.M;
+    using TE = EvalT<GM>;
     for (int t = 0; t < S.n_cloud; ++t) {
       float acc[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
+      // value-only variant: f at the centre once per step
+      const TE f0 = S.hlc_value_only ? value_at<KIND, GM, V, LPS>(P.obj, S, x, g, ec) : TE(0);
       for (int k = 0; k < S.M; ++k) {
         float z[V], xp[V], a[V];
         normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index,
                         (unsigned)k, z);
 #pragma unroll
         for (int v = 0; v < V; ++v) xp[v] = (j0 + v < P.d) ? fmaf(sigma, z[v], x[v]) : x[v];
-        gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xp, a, g, ec);
+        if (S.hlc_value_only) {
+          // (f(x + sigma z) - f(x)) z / sigma, the difference formed in the evaluation precision
+          const float w = (float)((value_at<KIND, GM, V, LPS>(P.obj, S, xp, g, ec) - f0) / (TE)sigma);
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += a[v];
+          for (int v = 0; v < V; ++v) acc[v] = fmaf(w, (j0 + v < P.d) ? z[v] : 0.f, acc[v]);
+        } else {
+          gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xp, a, g, ec);
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] += a[v];
+        }
       }
 #pragma unroll
       for (int v = 0; v < V; ++v) x[v] = clampf(fmaf(alpha, acc[v] * invM, x[v]), lo[v], hi[v]);

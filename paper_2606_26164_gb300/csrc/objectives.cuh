@@ -456,6 +456,18 @@ struct EvalCount {
   unsigned long long evals = 0, grads = 0;
 };
 
+// f (+ noise) at a binary32 point, in the evaluation precision of the gradient mode.
+template <int KIND, int GM, int V, int LPS>
+__device__ __forceinline__ EvalT<GM> value_at(const ObjDev& O, const StepParams& S, const float (&xf)[V],
+                                              const Grp<LPS>& g, EvalCount& ec) {
+  using TE = EvalT<GM>;
+  TE x[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) x[v] = (TE)xf[v];
+  ec.evals += 1;
+  return value_noisy<KIND, TE, V, LPS>(O, params_of<GM>(O), S, x, g);
+}
+
 // Central differences on the coordinates j < d: g_j = (f(x + h_j e_j) - f(x - h_j e_j)) / (x+_j - x-_j),
 // the stencil points regenerated one at a time in registers.
 template <int KIND, int GM, int V, int LPS>

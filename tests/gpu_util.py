@@ -22,7 +22,8 @@ def lib_params(P: M.Params, **over) -> CH.CParams:
                           T_ls=P.T_ls, grad_mode=P.grad_mode, eps_grad=P.eps_grad, eps_dup=P.eps_dup,
                           delta=P.delta, mu=P.mu, alpha=P.alpha, sigma=P.sigma, c_sigma=P.c_sigma,
                           alpha_scale=P.alpha_scale, h=P.h, h_rel=P.h_rel, c1=P.c1, curv_eps=P.curv_eps,
-                          seed=P.seed, rm_min_unfrozen=P.rm_min_unfrozen, gr_patience=P.gr_patience)
+                          seed=P.seed, rm_min_unfrozen=P.rm_min_unfrozen, gr_patience=P.gr_patience,
+                          hlc_value_only=P.hlc_value_only)
     for k, v in over.items():
         setattr(p, k, v)
     return p

@@ -125,6 +125,50 @@ def test_hands_like_clouds(mode, d, n_cloud):
     model.close()
 
 
+@pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64])
+@pytest.mark.parametrize("d", [3, 16])
+def test_hands_like_clouds_value_only(mode, d):
+    """The value-only smoothing variant, one step: the same Philox perturbations,
+    the estimator (f(x + sigma z) - f(x)) z / sigma from binary32 (FD64 mode: FP64)
+    values.  Besides 1e-5 of the move, the device's rounding of f (a few u of the
+    magnitude of the values) enters through the division by sigma."""
+    rng = np.random.default_rng(d + 7)
+    N = 777
+    prob = I.small_mixture(d, 4, N, seed=13)
+    P = M.Params(n_cloud=1, M=8, grad_mode=mode, seed=3, hlc_value_only=1)
+    st = M.new_state(prob.x0, P.m)
+    st.stuck = rng.random(N) < 0.3
+    st = U.rounded(st)
+    model = U.open_ctx(prob, P)
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_HLC, 2)
+    got = U.read_state(model, prob, P.m)
+    ref = _copy(st)
+    sigma, alpha = M.hlc(prob, ref, P, cycle=2)
+    c = model.counters(0)
+    assert c["sigma"] == pytest.approx(sigma, rel=1e-6)
+    unf = np.flatnonzero(~st.stuck)
+    X = st.x[unf]
+    fabs = np.abs(OB.value(prob.objective, X))
+    zsum = np.zeros_like(X)
+    for k in range(8):
+        z = PX.normal_rows(3, unf, d, PX.TAG_HLC, 2, 0, 0, k)
+        fabs = np.maximum(fabs, np.abs(OB.value(prob.objective, X + sigma * z)))
+        zsum += np.abs(z)
+    # binary32 values: each f carries ~ (d + 4) u |f| (the log-sum-exp and its terms),
+    # and the perturbed point is rounded before the evaluation (|grad f| u |x|)
+    u = 2.0 ** -24 if mode == M.GRAD_ADJOINT else 2.0 ** -50
+    gscale = np.abs(OB.grad(prob.objective, X)).max(axis=1) * np.abs(X).max(axis=1) + 1.0
+    ferr = 32 * (d + 4) * u * (fabs + 1.0) + 4 * 2.0 ** -24 * gscale
+    bound = alpha * (2 * ferr / sigma)[:, None] * zsum / 8
+    move = np.abs(ref.x[unf] - X).max(axis=1)
+    err = np.abs(got.x[unf] - ref.x[unf])
+    tol = 1e-5 * move[:, None] + bound + 2e-6 * np.abs(X)
+    assert np.all(err <= tol), (err / tol).max()
+    np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
+    model.close()
+
+
 @pytest.mark.parametrize("n_anti", [1, 5])
 @pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64])
 @pytest.mark.parametrize("d", [2, 16])

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import method as M
+from oracle import objectives as OB
 from oracle import philox as PX
 from paper_2606_26164_gb300 import inputs as I
 
@@ -219,6 +220,33 @@ def test_hlc_step_algebra_and_unbiasedness():
     chi2 = float((8.0 * zbar * zbar).sum())
     dof = zbar.size
     assert abs(chi2 - dof) < 5 * np.sqrt(2 * dof)
+
+
+def test_hlc_value_only_estimator_algebra_and_unbiasedness():
+    """The value-only smoothing variant on a quadratic f = -r^T A r (r = x - c):
+    f(x + sigma z) - f(x) = -2 sigma z^T A r - sigma^2 z^T A z, so one step adds
+    alpha (1/M) sum_k (-2 z_k^T A r - sigma z_k^T A z_k) z_k; and the estimator
+    (f(x + sigma z) - f(x)) z / sigma has the gradient as its mean over z."""
+    p, st = _quad_state(N=400, d=3)
+    P = M.Params(n_cloud=1, M=8, grad_mode=M.GRAD_ADJOINT, seed=4, hlc_value_only=1)
+    x0 = st.x.copy()
+    sigma, alpha = M.hlc(p, st, P, cycle=1)
+    A = p.objective.arrays["Q"].T @ np.diag(p.objective.arrays["lam"]) @ p.objective.arrays["Q"]
+    r = x0 - p.objective.arrays["center"]
+    acc = np.zeros_like(x0)
+    for k in range(8):
+        z = PX.normal_rows(4, np.arange(400), 3, PX.TAG_HLC, 1, 0, 0, k)
+        w = -2.0 * np.einsum("ni,ij,nj->n", z, A, r) - sigma * np.einsum("ni,ij,nj->n", z, A, z)
+        acc += w[:, None] * z
+    np.testing.assert_allclose(st.x, np.clip(x0 + alpha * acc / 8, p.lo, p.hi), rtol=1e-9, atol=1e-9)
+    # mean of the estimator at one point over many independent draws = grad f
+    rng = np.random.default_rng(9)
+    x = x0[:1]
+    Z = rng.normal(size=(200000, 3))
+    est = ((OB.value(p.objective, x + 0.3 * Z) - OB.value(p.objective, x)) / 0.3)[:, None] * Z
+    g = OB.grad(p.objective, x)[0]
+    se = est.std(axis=0) / np.sqrt(len(Z))
+    assert np.all(np.abs(est.mean(axis=0) - g) < 5 * se)
 
 
 def test_anti_convergence_momentum_algebra():
