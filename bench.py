@@ -403,6 +403,15 @@ def main():
                        "evals_per_s": (f1["evals"] - f0["evals"]) / tf, "ms_per_step": 1e3 * tf / args.fd_steps,
                        "steps": args.fd_steps}
         mfd.close()
+        # --- the same FD cycle with the value-only smoothing estimator in Phase 5 (a variant:
+        #     M + 1 evaluations per smoothing step instead of M central-difference gradients)
+        fd.hlc_value_only = 1
+        mfv = CH.Chisao([prob], fd)
+        tv, v0, v1 = gpu_timed(mfv, args.fd_steps, 1)
+        out["fd64_value_only_hlc"] = {"value": N * args.fd_steps / tv, "unit": "sample-cycles/s",
+                                      "evals_per_s": (v1["evals"] - v0["evals"]) / tv,
+                                      "ms_per_step": 1e3 * tv / args.fd_steps, "steps": args.fd_steps}
+        mfv.close()
         # --- the d=64, K=256 full-covariance mixture at N=65536: BF16 tensor-core cycle vs FP32 cycle,
         #     and the tensor-core objective kernel against the measured BF16 peak
         if args.workload == "quadratic_d64" and args.tc_steps > 0:
