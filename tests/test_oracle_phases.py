@@ -272,3 +272,38 @@ def test_anti_convergence_zeroes_velocity_on_clamped_coordinates():
     # step 1: g = (-1.8, -0.2), v = (1.8, 0.2), x = (2.7 -> 1.0 clamped, 0.3), v_x := 0
     # step 2: g = (-2, -0.6), v = (0 + 2, 0.1 + 0.6), x = (1.0 clamped, 1.0)
     np.testing.assert_allclose(st.x, [[1.0, 1.0]], atol=1e-12)
+
+
+def test_carry_tiger_rays():
+    """Carry Tiger (reading of Sec. 5.1): every sample on the segment from the box
+    centre to a face centre, an edge midpoint or a vertex, classes cycling with the
+    index; face centres round-robin; positions along the ray uniform in (0, 1)."""
+    from oracle import seeding as SD
+    d, n = 5, 6000
+    lo, hi = np.full(d, -3.0), np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    X = SD.carry_tiger(lo, hi, n, seed=11)
+    E, t = SD.carry_tiger_directions(d, n, seed=11)
+    c, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    assert np.all((X >= lo) & (X <= hi))
+    R = (X - c) / half                                  # = t e on every coordinate
+    nz = (E != 0).sum(axis=1)
+    cls = np.arange(n) % 3
+    assert np.all(nz[cls == 0] == 1) and np.all(nz[cls == 1] == d - 1) and np.all(nz[cls == 2] == d)
+    np.testing.assert_allclose(np.abs(R).max(axis=1), t, rtol=1e-12)
+    np.testing.assert_allclose(R, t[:, None] * E, atol=1e-12)
+    faces = [tuple(e) for e in E[cls == 0][:2 * d]]
+    assert len(set(faces)) == 2 * d                      # the first 2d face samples cover every face
+    from scipy import stats
+    assert stats.kstest(t, "uniform").pvalue > 1e-4
+    # vertex signs: each coordinate +-1 about equally often
+    assert abs(E[cls == 2].mean()) < 4 / np.sqrt(E[cls == 2].size)
+
+
+def test_uniform_seed_in_box():
+    from oracle import seeding as SD
+    lo, hi = np.array([-1.0, 0.0, 5.0]), np.array([1.0, 10.0, 6.0])
+    X = SD.uniform(lo, hi, 4000, seed=3)
+    assert np.all((X > lo) & (X < hi))
+    from scipy import stats
+    for a in range(3):
+        assert stats.kstest((X[:, a] - lo[a]) / (hi[a] - lo[a]), "uniform").pvalue > 1e-4
