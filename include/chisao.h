@@ -215,6 +215,17 @@ chisao_status chisao_step(chisao_ctx *c);
  * such as chisao_modes, or a stream synchronize). */
 chisao_status chisao_load_population(chisao_ctx *c, int32_t prob, const float *x_host);
 
+/* Initial population generated on the device.  method 0: uniform in the box Theta
+ * (counter-based Philox, keyed by the context seed, the problem and the sample);
+ * method 1: Carry Tiger (Sec. 5.1: "structured ray-based initialization from domain
+ * vertices, edges, and faces"; reading) - sample i lies on the ray from the box
+ * centre to a face centre, an edge midpoint or a vertex (the class cycles with i,
+ * face centres round-robin, edge free axis round-robin, signs random), at a
+ * uniform position along it.  Resets the per-sample state and the cycle count as
+ * chisao_load_population does.  Asynchronous on the context's stream. */
+typedef enum { CHISAO_SEED_UNIFORM = 0, CHISAO_SEED_CARRY_TIGER = 1 } chisao_seed_method;
+chisao_status chisao_seed(chisao_ctx *c, int32_t prob, int32_t method);
+
 /* The estimated mode set {x_i : stuck_i} of problem `prob` after the last
  * deduplication (Algorithm 1's return value), in sample-index order:
  * x_out host [cap][d], f_out host [cap] (may be NULL).  *count receives the

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libchisao.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE = 0, 1, 2, 3, 4, 5
 GRAD_FD64, GRAD_FD32, GRAD_ADJOINT, GRAD_ADJOINT_TC = 0, 1, 2, 3
+SEED_UNIFORM, SEED_CARRY_TIGER = 0, 1
 FIELD_X, FIELD_G, FIELD_F, FIELD_HS, FIELD_HY, FIELD_HRHO, FIELD_HLEN, FIELD_STUCK, FIELD_REMOVED = range(9)
 (PHASE_LBFGS, PHASE_FREEZE, PHASE_DEDUP, PHASE_RESEED, PHASE_HLC, PHASE_ANTI, PHASE_DIRECTION, PHASE_LISTS,
  PHASE_REFINE) = range(1, 10)
@@ -28,7 +29,7 @@ MMAX = 10
 EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chisao_step",
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
-           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc"]
+           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed"]
 
 
 class CParams(C.Structure):
@@ -81,6 +82,7 @@ def library() -> C.CDLL:
                                       C.POINTER(vp)]
         lib.chisao_step.argtypes = [vp]
         lib.chisao_load_population.argtypes = [vp, C.c_int32, C.POINTER(C.c_float)]
+        lib.chisao_seed.argtypes = [vp, C.c_int32, C.c_int32]
         lib.chisao_modes.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
                                      C.POINTER(C.c_int64)]
         lib.chisao_get_counters.argtypes = [vp, C.c_int32, C.POINTER(CCounters)]
@@ -184,6 +186,10 @@ class Chisao:
         self._check(library().chisao_load_population(self.ctx, prob, x.ctypes.data_as(C.POINTER(C.c_float))),
                     "chisao_load_population")
         self.synchronize()
+
+    def seed(self, prob: int, method: int = SEED_CARRY_TIGER):
+        """Initial population generated on the device (uniform or Carry Tiger)."""
+        self._check(library().chisao_seed(self.ctx, prob, method), "chisao_seed")
 
     def modes(self, prob: int = 0, cap: Optional[int] = None):
         pr = self.problems[prob]

@@ -697,6 +697,26 @@ chisao_status chisao_load_population(chisao_ctx* c, int32_t prob, const float* x
   return CHISAO_OK;
 }
 
+chisao_status chisao_seed(chisao_ctx* c, int32_t prob, int32_t method) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (method != CHISAO_SEED_UNIFORM && method != CHISAO_SEED_CARRY_TIGER)
+    return fail(c, CHISAO_ERR_ARG, "unknown seeding method");
+  ProbHost& ph = c->probs[prob];
+  ProbDev& P = ph.dev;
+  const size_t n = (size_t)ph.n;
+  CK(launch_seed(P, ph.sp, method, c->stream));
+  CK(cudaMemsetAsync(P.g, 0, n * ph.dp * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(P.f, 0, n * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(P.hlen, 0, n * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(P.stuck, 0, P.nwords * sizeof(uint32_t), c->stream));
+  CK(cudaMemsetAsync(P.removed, 0, P.nwords * sizeof(uint32_t), c->stream));
+  k_reset_problem<<<1, 32, 0, c->stream>>>(P);
+  CK(cudaGetLastError());
+  c->cycles_done = 0;
+  return CHISAO_OK;
+}
+
 chisao_status chisao_step(chisao_ctx* c) {
   if (!c) return CHISAO_ERR_ARG;
   if (c->cycles_done >= c->params.n_osc) return fail(c, CHISAO_ERR_STATE, "all n_osc cycles have run");

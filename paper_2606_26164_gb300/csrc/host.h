@@ -36,6 +36,7 @@ cudaError_t launch_set_cycle(const ProbDev& P, int completed, cudaStream_t st);
 cudaError_t launch_freeze(const ProbDev& P, const StepParams& S, cudaStream_t st);
 cudaError_t launch_compact_stuck(const ProbDev& P, cudaStream_t st);
 cudaError_t launch_lists(const ProbDev& P, cudaStream_t st);
+cudaError_t launch_seed(const ProbDev& P, const StepParams& S, int method, cudaStream_t st);
 cudaError_t launch_dedup(const ProbDev& P, const StepParams& S, cudaStream_t st);
 cudaError_t launch_reseed(const ProbDev& P, const StepParams& S, cudaStream_t st);
 cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int which, cudaStream_t st);

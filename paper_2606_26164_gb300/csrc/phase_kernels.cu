@@ -288,6 +288,49 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
   if (rem && g.l == 0) atomicOr(&P.removed[j >> 5], 1u << (j & 31));
 }
 
+// ------------------------------------------------------------ initial populations
+// Uniform: x_a = lo_a + u (hi_a - lo_a), u from the TAG_SEED stream (c0 = sample,
+// c1 = coordinate block of four, step 1).  Carry Tiger (reading of Sec. 5.1): the
+// ray from the box centre c to an anchor, x = c + t (e * half): class i % 3 = face
+// centre (axis q / 2, side q % 2, q = (i / 3) mod 2d), edge midpoint (free axis
+// (i / 3) mod d, other coordinates +-1 from the sign bits), vertex (all +-1); t is
+// word 0 of the stream with c1 = 0, the signs the bits of the words with c1 = 1.
+constexpr unsigned TAG_SEED = 8;
+
+__global__ void __launch_bounds__(NT_LIN) k_seed(ProbDev P, StepParams S, int method) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  const int d = P.d, dp = P.dp;
+  const unsigned pq = (unsigned)P.obj.prob_index;
+  float* xr = P.x + (size_t)i * dp;
+  if (method == 0) {
+    for (int blk = 0; blk < (d + 3) / 4; ++blk) {
+      const uint4 w = rng_words(S, (unsigned)i, (unsigned)blk, TAG_SEED, 0u, 1u, pq, 0u);
+      const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+      for (int v = 0; v < 4; ++v) {
+        const int a = 4 * blk + v;
+        if (a < d) xr[a] = fmaf(u01f(ws[v]), P.hi[a] - P.lo[a], P.lo[a]);
+      }
+    }
+  } else {
+    const float t = u01f(rng_words(S, (unsigned)i, 0u, TAG_SEED, 0u, 0u, pq, 0u).x);
+    const uint4 w = rng_words(S, (unsigned)i, 1u, TAG_SEED, 0u, 0u, pq, 0u);
+    const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+    const int cls = i % 3, j = i / 3;
+    const int q = j % (2 * d), free_ax = j % d;
+    for (int a = 0; a < d; ++a) {
+      const float sgn = ((ws[a >> 5] >> (a & 31)) & 1u) ? 1.f : -1.f;
+      float e;
+      if (cls == 0) e = (a == q / 2) ? ((q & 1) ? 1.f : -1.f) : 0.f;
+      else if (cls == 1) e = (a == free_ax) ? 0.f : sgn;
+      else e = sgn;
+      const float c = 0.5f * (P.lo[a] + P.hi[a]), half = 0.5f * (P.hi[a] - P.lo[a]);
+      xr[a] = fmaf(t, e * half, c);
+    }
+  }
+  for (int a = d; a < dp; ++a) xr[a] = 0.f;
+}
+
 // ------------------------------------------------------------ Phase 4
 // Strategy choice and Golden Rooster bookkeeping (single thread):
 //   K_lost = 0 -> none; >= rm_min unfrozen -> Repulse Monkey; else Golden
@@ -615,6 +658,11 @@ template <int DP>
 static void dedup_dp(const ProbDev& P, const StepParams& S, cudaStream_t st) {
   const long long th = (long long)P.n * (DP / 2);
   k_dedup_impl<DP><<<lin_blocks(th, 128), 128, 0, st>>>(P, S);
+}
+
+cudaError_t launch_seed(const ProbDev& P, const StepParams& S, int method, cudaStream_t st) {
+  k_seed<<<lin_blocks(P.n, NT_LIN), NT_LIN, 0, st>>>(P, S, method);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dedup(const ProbDev& P, const StepParams& S, cudaStream_t st) {

@@ -268,3 +268,29 @@ def test_tc_hlc_and_anti_single_steps():
         assert np.all(err <= tol), (phase, (err / tol).max())
         np.testing.assert_array_equal(got.x[st.stuck], st.x[st.stuck])
         model.close()
+
+
+@pytest.mark.parametrize("method", [CH.SEED_UNIFORM, CH.SEED_CARRY_TIGER])
+@pytest.mark.parametrize("d", [2, 7, 64])
+def test_seeding(method, d):
+    """Device populations against the oracle's: the same Philox words, so the same
+    anchors and ray positions; binary32 coordinates within a few ulp of the box."""
+    from oracle import seeding as SD
+    prob = I.small_mixture(d, 2, 3001, seed=5)
+    prob.lo = prob.lo - np.arange(d) * 0.5                 # an asymmetric box
+    P = M.Params(seed=17)
+    model = U.open_ctx(prob, P)
+    model.seed(0, method)
+    x = model.get(0, CH.FIELD_X)[:, :d].astype(np.float64)
+    lo32, hi32 = prob.lo.astype(np.float32).astype(np.float64), prob.hi.astype(np.float32).astype(np.float64)
+    f = SD.uniform if method == CH.SEED_UNIFORM else SD.carry_tiger
+    ref = f(lo32, hi32, prob.n, seed=17)
+    scale = np.abs(lo32) + np.abs(hi32)
+    np.testing.assert_allclose(x, ref, rtol=0, atol=4 * 2.0 ** -24 * scale.max())
+    assert np.all((x >= lo32) & (x <= hi32))
+    if method == CH.SEED_CARRY_TIGER:
+        E, _ = SD.carry_tiger_directions(d, prob.n, seed=17)
+        c = (0.5 * (lo32 + hi32)).astype(np.float32).astype(np.float64)
+        np.testing.assert_array_equal(x[E == 0], np.broadcast_to(c, x.shape)[E == 0])   # off-ray axes at the centre
+    assert model.counters(0)["cycles"] == 0
+    model.close()
