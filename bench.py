@@ -155,25 +155,35 @@ def profiled_traffic(kernel):
 
 
 def dist_setup():
+    """Ranks from the torchrun environment; NCCL when there is a GPU, gloo otherwise."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
 
 
 def allmax(v, world):
+    """The largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(n_per_rank, steps, world, t_max):
+    """Whole-job throughput of independent replicas (weak scaling): every rank's
+    samples x cycles over the slowest rank's time."""
+    return n_per_rank * steps * world / t_max
 
 
 def barrier(world):
@@ -349,7 +359,7 @@ def main():
     t, c0, c1 = gpu_timed(model, args.steps, args.warmup)
     clocks = clk.stop()
     t_max = allmax(t, world)
-    value = N * args.steps * world / t_max
+    value = job_value(N, args.steps, world, t_max)
     evals = (c1["evals"] - c0["evals"]) * world / t_max
     grads = (c1["grads"] - c0["grads"]) * world / t_max
 
