@@ -56,6 +56,47 @@ __device__ __forceinline__ void two_loop(const float (&s)[MMAX][V], const float 
   for (int v = 0; v < V; ++v) p[v] = -q[v];
 }
 
+// The same recursion over a history held in shared memory as a ring: logical slot
+// k (0 newest) of this lane is row (head + k) mod MMAX of hs / hy (one float4 per
+// lane and slot); rho stays in registers in logical order.
+template <int LPS>
+__device__ __forceinline__ void two_loop_ring(const float4 (*hs)[NT_OBJ], const float4 (*hy)[NT_OBJ], int head,
+                                              const float (&rho)[MMAX], int len, float gam, const float (&G)[4],
+                                              float (&p)[4], const Grp<LPS>& g) {
+  const int t = threadIdx.x;
+  float q[4], al[MMAX];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] = G[v];
+#pragma unroll
+  for (int k = 0; k < MMAX; ++k) {
+    al[k] = 0.f;
+    if (k < len) {
+      const int r = head + k < MMAX ? head + k : head + k - MMAX;
+      const float4 s4 = hs[r][t], y4 = hy[r][t];
+      const float sv[4] = {s4.x, s4.y, s4.z, s4.w}, yv[4] = {y4.x, y4.y, y4.z, y4.w};
+      al[k] = rho[k] * g.sum(dotv<4>(sv, q));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[v] = fmaf(-al[k], yv[v], q[v]);
+    }
+  }
+  const float gm = len > 0 ? gam : 1.f;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] *= gm;
+#pragma unroll
+  for (int k = MMAX - 1; k >= 0; --k) {
+    if (k < len) {
+      const int r = head + k < MMAX ? head + k : head + k - MMAX;
+      const float4 s4 = hs[r][t], y4 = hy[r][t];
+      const float sv[4] = {s4.x, s4.y, s4.z, s4.w}, yv[4] = {y4.x, y4.y, y4.z, y4.w};
+      const float be = rho[k] * g.sum(dotv<4>(yv, q));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[v] = fmaf(sv[v], al[k] - be, q[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) p[v] = -q[v];
+}
+
 // History of sample i into registers; gam = s^T y / y^T y of the newest pair
 // (s^T y = 1 / rho).
 template <int DP, int V, int LPS>
@@ -89,11 +130,22 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 //   exact products in double-single.  A failed search clears the history.
 // With a row list (rows, *nrows on the device) only those samples iterate:
 // the final FP32 refinement of the survivors.
+// Resident blocks per SM the fused Phase 1 asks the compiler for: with the history in
+// shared memory (45 KB per block) the binary32 adjoint kernels of the cheaper
+// objectives fit five blocks in 96 registers without spilling; the FP64 stencil
+// and full-covariance variants keep the compiler's register choice.
+template <int KIND, int GM>
+constexpr int phase1_min_blocks() {
+  return (GM == GRAD_ADJOINT && KIND != OBJ_MIXTURE_FULL) ? 5 : 1;
+}
+
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
+__global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
                                                    const int* __restrict__ rows, const int* __restrict__ nrows) {
   constexpr int V = VL, LPS = DP / V;
+  static_assert(V == 4, "one float4 of history per lane and slot");
   using TE = EvalT<GM>;
+  __shared__ float4 hist_s[MMAX][NT_OBJ], hist_y[MMAX][NT_OBJ];
   const Grp<LPS> g;
   const int gi = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   const bool act = rows ? gi < *nrows : gi < P.n;
@@ -107,9 +159,27 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
     ld_vec<V>(P.lo + j0, lo);
     ld_vec<V>(P.hi + j0, hi);
     int len = P.hlen[i];
-    float s[MMAX][V], y[MMAX][V], rho[MMAX], gam;
+    float rho[MMAX], gam = 1.f;
     const float curv_eps = (float)S.curv_eps;
-    load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
+    // the (s, y) history lives in shared memory (a ring per lane, logical slot k at row
+    // head + k mod MMAX): registers hold only rho, which keeps more samples resident
+    int head = 0;
+#pragma unroll
+    for (int k = 0; k < MMAX; ++k) {
+      if (k < len) {
+        const size_t o = ((size_t)i * MMAX + k) * DP + j0;
+        hist_s[k][threadIdx.x] = *reinterpret_cast<const float4*>(P.hs + o);
+        hist_y[k][threadIdx.x] = *reinterpret_cast<const float4*>(P.hy + o);
+        rho[k] = P.hrho[(size_t)i * MMAX + k];
+      } else {
+        rho[k] = 0.f;
+      }
+    }
+    if (len > 0) {                                 // gam = s^T y / y^T y of the newest pair
+      const float4 y4 = hist_y[0][threadIdx.x];
+      const float y0[V] = {y4.x, y4.y, y4.z, y4.w};
+      gam = (1.0f / rho[0]) / g.sum(dotv<V>(y0, y0));
+    }
     TE F;
     float G[V];
     if (fresh) {
@@ -130,7 +200,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
       const float gn = g.maxf(gl);
       if (!(gn > 0.f)) break;                      // exactly stationary (or invalid): stays put
       float p[V];
-      two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
+      two_loop_ring<LPS>(hist_s, hist_y, head, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       const float gp = g.sum(dotv<V>(G, p));
       if (!(gp < 0.f)) {                           // not a descent direction: restart
@@ -205,19 +275,10 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
       yy = g.sum(yy);
       if (sy > curv_eps * sqrtf(ss) * sqrtf(yy)) {
 #pragma unroll
-        for (int k = MMAX - 1; k > 0; --k) {
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            s[k][v] = s[k - 1][v];
-            y[k][v] = y[k - 1][v];
-          }
-          rho[k] = rho[k - 1];
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          s[0][v] = sv[v];
-          y[0][v] = yv[v];
-        }
+        for (int k = MMAX - 1; k > 0; --k) rho[k] = rho[k - 1];
+        head = head == 0 ? MMAX - 1 : head - 1;      // the oldest row takes the newest pair
+        hist_s[head][threadIdx.x] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        hist_y[head][threadIdx.x] = make_float4(yv[0], yv[1], yv[2], yv[3]);
         rho[0] = 1.0f / sy;
         len = min(len + 1, S.m);
         gam = sy / yy;
@@ -238,8 +299,9 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1(ProbDev P, StepParams S, int 
     for (int k = 0; k < MMAX; ++k) {
       if (k < len) {
         const size_t o = ((size_t)i * MMAX + k) * DP + j0;
-        st_vec<V>(P.hs + o, s[k]);
-        st_vec<V>(P.hy + o, y[k]);
+        const int r = head + k < MMAX ? head + k : head + k - MMAX;
+        *reinterpret_cast<float4*>(P.hs + o) = hist_s[r][threadIdx.x];
+        *reinterpret_cast<float4*>(P.hy + o) = hist_y[r][threadIdx.x];
         if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = rho[k];
       }
     }

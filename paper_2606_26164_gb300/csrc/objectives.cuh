@@ -66,7 +66,7 @@ __device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&
     // the group's vector r is staged once in shared memory (each lane its four values)
     // and read back four at a time as one broadcast load, instead of a register shuffle
     // per element
-    __shared__ float4 rstage[1024];
+    __shared__ float4 rstage[256];                // the largest block of the objective kernels
     rstage[threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
     __syncwarp(g.mask);
     const float4* grp = rstage + (threadIdx.x - g.l);
