@@ -433,6 +433,24 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
           const float w = (float)((value_at<KIND, GM, V, LPS>(P.obj, S, xp, g, ec) - f0) / (TE)sigma);
 #pragma unroll
           for (int v = 0; v < V; ++v) acc[v] = fmaf(w, (j0 + v < P.d) ? z[v] : 0.f, acc[v]);
+        } else if (GM == GRAD_ADJOINT && HasPair<KIND>::value && k + 1 < S.M) {
+          // two perturbations at once, sharing the objective's parameter loads; the sum
+          // keeps the order of the one-at-a-time loop
+          float z2[V], xp2[V], a2[V], fa, fb;
+          normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index,
+                          (unsigned)(k + 1), z2);
+#pragma unroll
+          for (int v = 0; v < V; ++v) xp2[v] = (j0 + v < P.d) ? fmaf(sigma, z2[v], x[v]) : x[v];
+          if constexpr (HasPair<KIND>::value)
+            Obj<KIND>::template value_grad_pair<V, LPS>(P.obj.f32, xp, xp2, a, a2, fa, fb, g);
+          ec.evals += 2;
+          ec.grads += 2;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            acc[v] += a[v];
+            acc[v] += a2[v];
+          }
+          ++k;
         } else {
           gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xp, a, g, ec);
 #pragma unroll

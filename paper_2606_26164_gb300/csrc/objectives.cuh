@@ -113,8 +113,56 @@ __device__ __forceinline__ void rows_times(const T* M, int dp, int d, const T (&
   }
 }
 
+// Two products with the same matrix at once (two evaluation points of one lane
+// group): each row block is read once for both; each output keeps the FMA order of
+// rows_times, so the results are the same bit for bit.
+template <int LPS>
+__device__ __forceinline__ void rows_times2(const float* M, int dp, int d, const float (&r1)[4],
+                                            const float (&r2)[4], float (&out1)[4], float (&out2)[4],
+                                            const Grp<LPS>& g) {
+  __shared__ float4 rpair[2][256];                // the largest block of the objective kernels
+  rpair[0][threadIdx.x] = make_float4(r1[0], r1[1], r1[2], r1[3]);
+  rpair[1][threadIdx.x] = make_float4(r2[0], r2[1], r2[2], r2[3]);
+  __syncwarp(g.mask);
+  const float4* grp1 = rpair[0] + (threadIdx.x - g.l);
+  const float4* grp2 = rpair[1] + (threadIdx.x - g.l);
+  float2 a1[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, a2[2] = {a1[0], a1[1]};
+  const float* col = M + 4 * g.l;
+  const int nb = (d + 3) / 4;
+#pragma unroll 1
+  for (int jb = 0; jb < nb; ++jb) {
+    const float4 b1 = grp1[jb], b2 = grp2[jb];
+    const float v1[4] = {b1.x, b1.y, b1.z, b1.w}, v2[4] = {b2.x, b2.y, b2.z, b2.w};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float a[4];
+      ldg_vec<float, 4>(col + (size_t)(jb * 4 + v) * dp, a);
+      const float2 s1 = make_float2(v1[v], v1[v]), s2 = make_float2(v2[v], v2[v]);
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const float2 aw = make_float2(a[2 * w], a[2 * w + 1]);
+        a1[w] = __ffma2_rn(aw, s1, a1[w]);
+        a2[w] = __ffma2_rn(aw, s2, a2[w]);
+      }
+    }
+  }
+  __syncwarp(g.mask);
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    out1[2 * w] = a1[w].x;
+    out1[2 * w + 1] = a1[w].y;
+    out2[2 * w] = a2[w].x;
+    out2[2 * w + 1] = a2[w].y;
+  }
+}
+
 template <int KIND>
 struct Obj;
+
+// Objectives that evaluate two points of one lane group sharing their parameter loads
+// (binary32 value and gradient; each point's arithmetic exactly that of value_grad).
+template <int KIND>
+struct HasPair : std::false_type {};
 
 // ------------------------------------------------------------ diagonal mixture
 template <>
@@ -161,7 +209,43 @@ struct Obj<OBJ_MIXTURE_DIAG> {
     for (int v = 0; v < V; ++v) gr[v] = G[v] / s;
     return m + log(s);
   }
+  template <int V, int LPS>
+  static __device__ __forceinline__ void value_grad_pair(const ObjParams<float>& o, const float (&x1)[V],
+                                                         const float (&x2)[V], float (&g1)[V], float (&g2)[V],
+                                                         float& f1, float& f2, const Grp<LPS>& g) {
+    float m1 = -CUDART_INF_F, s1 = 0.f, G1[V], m2 = -CUDART_INF_F, s2 = 0.f, G2[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) G1[v] = G2[v] = 0.f;
+    for (int k = 0; k < o.K; ++k) {
+      float mk[V], ak[V], sc1[V], sc2[V];
+      ldg_vec<float, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
+      ldg_vec<float, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
+      float q1 = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float r1 = x1[v] - mk[v], r2 = x2[v] - mk[v];
+        q1 = fmaf(ak[v] * r1, r1, q1);
+        q2 = fmaf(ak[v] * r2, r2, q2);
+        sc1[v] = -ak[v] * r1;
+        sc2[v] = -ak[v] * r2;
+      }
+      q1 = g.sum(q1);
+      q2 = g.sum(q2);
+      const float ck = __ldg(o.p2 + k);
+      lse_push_grad<float, V>(m1, s1, G1, ck - 0.5f * q1, sc1);
+      lse_push_grad<float, V>(m2, s2, G2, ck - 0.5f * q2, sc2);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      g1[v] = G1[v] / s1;
+      g2[v] = G2[v] / s2;
+    }
+    f1 = m1 + logf(s1);
+    f2 = m2 + logf(s2);
+  }
 };
+template <>
+struct HasPair<OBJ_MIXTURE_DIAG> : std::true_type {};
 
 // ------------------------------------------------------------ full-covariance mixture
 template <>
@@ -241,7 +325,32 @@ struct Obj<OBJ_QUADRATIC> {
     for (int v = 0; v < V; ++v) gr[v] = T(-2) * u[v];
     return f;
   }
+  template <int V, int LPS>
+  static __device__ __forceinline__ void value_grad_pair(const ObjParams<float>& o, const float (&x1)[V],
+                                                         const float (&x2)[V], float (&g1)[V], float (&g2)[V],
+                                                         float& f1, float& f2, const Grp<LPS>& g) {
+    float c[V], r1[V], r2[V], u1[V], u2[V];
+    ldg_vec<float, V>(o.p0 + V * g.l, c);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      r1[v] = x1[v] - c[v];
+      r2[v] = x2[v] - c[v];
+    }
+    rows_times2<LPS>(o.p1, o.dp, o.d, r1, r2, u1, u2, g);
+    float acc1 = 0.f, acc2 = 0.f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      acc1 = fmaf(r1[v], u1[v], acc1);
+      acc2 = fmaf(r2[v], u2[v], acc2);
+      g1[v] = -2.f * u1[v];
+      g2[v] = -2.f * u2[v];
+    }
+    f1 = -g.sum(acc1);
+    f2 = -g.sum(acc2);
+  }
 };
+template <>
+struct HasPair<OBJ_QUADRATIC> : std::true_type {};
 
 // ------------------------------------------------------------ Appendix D benchmark functions
 // Negated (maximisation) forms, coordinate i = j + 1 for the lane's coordinate j;
