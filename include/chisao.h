@@ -8,7 +8,7 @@
  * (Phase 2, Eq. 3), L-infinity deduplication (Phase 3, Eq. 4), Repulse Monkey /
  * Golden Rooster reseeding (Phase 4, Sec. 3.2.4), Hands Like Clouds smoothed
  * ascent (Phase 5, Eq. 5) and momentum anti-convergence (Phase 6, Eq. 6).
- * Phases 4-6 are skipped on the last cycle.
+ * The last cycle runs Phases 1-3 only.
  *
  * One context owns the device state of one or more independent problems.
  * Every phase runs in hand-written CUDA kernels on the context's stream;
@@ -75,8 +75,8 @@ typedef enum {
   CHISAO_OBJ_BUKIN6 = 16
 } chisao_objective_kind;
 
-/* How gradients are obtained (Section 3.1: "by finite differences, or
- * supplied analytically"). */
+/* How gradients are obtained (Section 3.1: central differences of the values,
+ * or an exact gradient where one is available). */
 typedef enum {
   /* central differences at absolute step h; stencil coordinates and every
    * stencil evaluation in FP64, quotient in FP64, result stored FP32       */
@@ -217,8 +217,8 @@ chisao_status chisao_load_population(chisao_ctx *c, int32_t prob, const float *x
 
 /* Initial population generated on the device.  method 0: uniform in the box Theta
  * (counter-based Philox, keyed by the context seed, the problem and the sample);
- * method 1: Carry Tiger (Sec. 5.1: "structured ray-based initialization from domain
- * vertices, edges, and faces"; reading) - sample i lies on the ray from the box
+ * method 1: Carry Tiger (Sec. 5.1 describes it only as rays toward the box's corners,
+ * edges and faces, so this is a reading) - sample i lies on the ray from the box
  * centre to a face centre, an edge midpoint or a vertex (the class cycles with i,
  * face centres round-robin, edge free axis round-robin, signs random), at a
  * uniform position along it.  Resets the per-sample state and the cycle count as

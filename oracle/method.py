@@ -105,7 +105,7 @@ def new_state(x0, m: int) -> State:
 
 
 # ----------------------------------------------------------------------------------------------
-# objective access (Sec. 3.1: gradients by finite differences or supplied analytically)
+# objective access (Sec. 3.1: gradients from differences of values, or exact where available)
 # ----------------------------------------------------------------------------------------------
 
 def _pidx(prob) -> int:

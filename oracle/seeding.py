@@ -2,9 +2,9 @@
 
 * Uniform: x_a = lo_a + u (hi_a - lo_a), u from the TAG_SEED stream (c0 = sample,
   c1 = coordinate block, word a % 4).
-* Carry Tiger (Sec. 5.1 names it "structured ray-based initialization from domain
-  vertices, edges, and faces"; the sentence is all the paper gives, so the
-  construction below is a reading): sample i lies on the ray from the box centre c
+* Carry Tiger (Sec. 5.1 describes it only as placing the initial samples along rays
+  toward the box's corners, edge midpoints and face centres; that one description is
+  all the paper gives, so the construction below is a reading): sample i lies on the ray from the box centre c
   to a boundary anchor, x = c + t (e * half), half = (hi - lo) / 2, t uniform in
   (0, 1).  The anchor class cycles with i: i % 3 = 0 face centres (round-robin over
   the 2d faces: axis q // 2, side q % 2 with q = (i // 3) mod 2d), 1 edge midpoints

@@ -28,8 +28,8 @@ def test_delta_gate_drops_low_modes():
 
 
 def test_single_mode_cycle_collapses():
-    """Remark 1: with one mode the first Phase 1 finds the peak, every sample
-    sticks and deduplication leaves a single survivor."""
+    """Remark 1: a unimodal objective is solved by the first Phase 1 alone: all
+    samples reach the maximum, all are stuck, and one survives deduplication."""
     p = I.small_quadratic(3, 64, seed=11, cond=4.0)
     P = M.Params(n_osc=1, n_conv=40, m=5, eps_grad=1e-8, grad_mode=M.GRAD_ADJOINT)
     st = M.new_state(p.x0, P.m)
