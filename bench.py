@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--tc-steps", type=int, default=2, help="cycles of the full-covariance tensor-core leg")
     ap.add_argument("--batched-steps", type=int, default=3, help="cycles of the 512-problem leg")
     ap.add_argument("--bench-fn-steps", type=int, default=3, help="cycles of each benchmark-function leg")
+    ap.add_argument("--noise-trials", type=int, default=10, help="trials per level of the noise-table leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -324,6 +325,52 @@ def benchmark_functions_leg(CH, steps, n_osc):
     return res
 
 
+def noise_table_leg(CH, trials):
+    """The Sec. 5.6 noise workload (d = 6, unit components at +-2 e_1, N = 2048) at
+    each noise level of its table, exact gradients, 3 cycles per trial: how often both
+    peaks are returned, the mean L2 error of the returned peaks, spurious returns and
+    the device time of a whole run (its three cycles, the first one's graph capture
+    included; context creation excluded).  The true peaks are
+    +-x* e_1 with x* = 2 tanh(2 x*) (the stationarity condition along e_1)."""
+    import torch
+    from paper_2606_26164_gb300 import inputs as I
+    xs = 2.0
+    for _ in range(50):                                    # Newton on x - 2 tanh(2x) = 0
+        t = np.tanh(2 * xs)
+        xs -= (xs - 2 * t) / (1 - 4 * (1 - t * t))
+    peaks_true = np.zeros((2, 6))
+    peaks_true[0, 0], peaks_true[1, 0] = xs, -xs
+    rows = []
+    for noise in I.NOISE_LEVELS:
+        both = spurious = 0
+        errs, ms = [], []
+        for seed in range(trials):
+            prob = I.mixture2_d6(n=2048, seed=seed, noise_sigma=noise)
+            prm = CH.default_params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=GRAD["adjoint"], seed=seed)
+            model = CH.Chisao([prob], prm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(model._stream)
+            for _ in range(3):
+                model.step()
+            e1.record(model._stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            fx, _ = model.modes(0)
+            model.close()
+            dist = np.abs(fx[:, None, :].astype(np.float64) - peaks_true[None]).max(axis=2)   # L-inf
+            hit = dist.min(axis=0) <= 1e-3
+            both += int(hit.all())
+            matched = dist.min(axis=1) <= 1e-3
+            spurious += int((~matched).sum())
+            for k in range(2):
+                if hit[k]:
+                    errs.append(float(np.linalg.norm(fx[dist[:, k].argmin()] - peaks_true[k])))
+        rows.append({"sigma_noise": noise, "both_found": f"{both}/{trials}", "spurious": spurious,
+                     "mean_peak_error_l2": float(np.mean(errs)) if errs else None,
+                     "ms_per_run": float(np.median(ms))})
+    return {"d": 6, "N": 2048, "cycles": 3, "grad": "adjoint", "trials": trials, "levels": rows}
+
+
 def main():
     args = parse()
     if args.cpu_leg:
@@ -432,6 +479,9 @@ def main():
         # --- the Appendix D benchmark functions
         if args.workload == "quadratic_d64" and args.bench_fn_steps > 0:
             out["benchmark_functions"] = benchmark_functions_leg(CH, args.bench_fn_steps, n_osc)
+        # --- the Sec. 5.6 noise table workload
+        if args.workload == "quadratic_d64" and args.noise_trials > 0:
+            out["noise_d6"] = noise_table_leg(CH, args.noise_trials)
         # --- end to end through the C ABI: pinned host population in, modes out, every step
         xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
         xh.copy_(torch.from_numpy(prob.x0))

@@ -234,6 +234,22 @@ chisao_status chisao_seed(chisao_ctx *c, int32_t prob, int32_t method);
 chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
                            float *f_out, int64_t cap, int64_t *count);
 
+/* Laplace widths of the modes chisao_modes returns (same order).  Phase 3
+ * (Sec. 3.2.3) keeps each surviving sample's inverse-Hessian estimate for width
+ * estimation; the paper gives no formula, and the reading here is the Laplace
+ * approximation at the mode: the covariance is H, the L-BFGS inverse-Hessian
+ * estimate of F = -f that the two-loop recursion applies (H_0 = gamma I, gamma =
+ * s^T y / y^T y of the newest pair; H = I with no stored pairs), computed column
+ * by column as H e_j in binary32.
+ *   w_out    [cap][d]: w[r][j] = sqrt(max(H_jj, 0)) of mode r;
+ *   cov_out  [cap][d][d] or NULL: row j of mode r holds H e_j.
+ * Outputs may be host or device memory (copied with cudaMemcpyDefault); cov_out
+ * needs a temporary device buffer of count*d*d floats (CHISAO_ERR_OOM without
+ * it).  *count receives the number of modes; CHISAO_ERR_CAPACITY (nothing
+ * written) when cap < count.  Synchronizes the stream. */
+chisao_status chisao_widths(chisao_ctx *c, int32_t prob, float *w_out, float *cov_out,
+                            int64_t cap, int64_t *count);
+
 /* Counters of problem `prob` (synchronizes the stream). */
 chisao_status chisao_get_counters(chisao_ctx *c, int32_t prob, chisao_counters *out);
 

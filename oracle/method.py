@@ -225,10 +225,12 @@ def line_search(prob, X, F, G, Pd, alpha0, P: Params, st: Optional[State] = None
 
 
 def push_pair(st: State, idx, s, y, P: Params):
-    """Store (s, y) as the newest pair when it has curvature s^T y > curv_eps |s| |y|."""
+    """Store (s, y) as the newest pair when it has curvature s^T y > curv_eps |s| |y|
+    and rho = 1 / s^T y is finite in the state precision (a subnormal s^T y, reached
+    when the coordinates converge to 0, would store an infinite rho)."""
     sy = np.einsum("nd,nd->n", s, y)
     nrm = np.sqrt(np.einsum("nd,nd->n", s, s) * np.einsum("nd,nd->n", y, y))
-    ok = sy > P.curv_eps * nrm
+    ok = (sy > P.curv_eps * nrm) & (sy >= 1.0 / np.finfo(np.float64).max)
     j = idx[ok]
     if j.size:
         st.S[j] = np.roll(st.S[j], 1, axis=1)
@@ -546,3 +548,24 @@ def run(prob, P: Params, prob_index: int = 0):
 def modes_of(st: State):
     idx = np.flatnonzero(st.stuck)
     return st.x[idx].copy(), st.f[idx].copy()
+
+
+def laplace_widths(st: State, idx):
+    """Laplace widths of the samples idx (normally the survivors) from their kept
+    L-BFGS history.  Sec. 3.2.3 keeps a surviving sample's inverse-Hessian estimate
+    so that its width can be estimated; the paper gives no formula, so this is a
+    reading: the estimate is the matrix H that the two-loop recursion applies
+    (H_0 = gamma I with gamma of the newest pair), and under the Laplace
+    approximation of f = log p at the mode the covariance is H, the inverse of the
+    Hessian of F = -f.  Column j of H is H e_j = -lbfgs_direction(e_j); the width
+    along coordinate j is sqrt(H_jj).  Returns (H (k, d, d), widths (k, d)).
+    """
+    idx = np.asarray(idx, dtype=np.int64)
+    k, d = idx.size, st.x.shape[1]
+    H = np.empty((k, d, d))
+    for j in range(d):
+        E = np.zeros((k, d))
+        E[:, j] = 1.0
+        H[:, :, j] = -lbfgs_direction(E, st.S[idx], st.Y[idx], st.rho[idx], st.hlen[idx])
+    w = np.sqrt(np.maximum(np.diagonal(H, axis1=1, axis2=2), 0.0))
+    return H, w

@@ -29,7 +29,8 @@ MMAX = 10
 EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chisao_step",
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
-           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed"]
+           "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
+           "chisao_widths"]
 
 
 class CParams(C.Structure):
@@ -202,6 +203,21 @@ class Chisao:
                     "chisao_modes")
         k = cnt.value
         return xo[:k].copy(), fo[:k].copy()
+
+    def widths(self, prob: int = 0, cov: bool = False):
+        """Laplace widths of the modes (order of `modes`): (w [k, d], H [k, d, d] or None)."""
+        d = self.problems[prob].d
+        cnt = C.c_int64(0)
+        fp = C.POINTER(C.c_float)
+        library().chisao_widths(self.ctx, prob, None, None, 0, C.byref(cnt))    # the count only
+        k = cnt.value
+        wo = np.empty((max(k, 1), d), np.float32)
+        co = np.empty((max(k, 1), d, d), np.float32) if cov else None
+        if k > 0:
+            self._check(library().chisao_widths(self.ctx, prob, wo.ctypes.data_as(fp),
+                                                co.ctypes.data_as(fp) if cov else None, k, C.byref(cnt)),
+                        "chisao_widths")
+        return wo[:k].copy(), (co[:k].copy() if cov else None)
 
     def counters(self, prob: int = 0) -> dict:
         c = CCounters()

@@ -767,6 +767,33 @@ chisao_status chisao_modes(chisao_ctx* c, int32_t prob, float* x_out, float* f_o
   return CHISAO_OK;
 }
 
+chisao_status chisao_widths(chisao_ctx* c, int32_t prob, float* w_out, float* cov_out, int64_t cap,
+                            int64_t* count) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (!count || cap < 0 || (cap > 0 && !w_out)) return fail(c, CHISAO_ERR_ARG, "bad output arguments");
+  ProbHost& ph = c->probs[prob];
+  Counters cnt;
+  CK(cudaMemcpyAsync(&cnt, ph.dev.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *count = cnt.n_surv;
+  if (cnt.n_surv > cap) return fail(c, CHISAO_ERR_CAPACITY, "output capacity below the number of modes");
+  if (cnt.n_surv == 0) return CHISAO_OK;
+  const size_t S = (size_t)cnt.n_surv, d = (size_t)ph.d;
+  float* cov = nullptr;
+  if (cov_out && cudaMalloc(&cov, sizeof(float) * S * d * d) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CHISAO_ERR_OOM, "no device memory for the covariance rows");
+  }
+  cudaError_t e = launch_widths(ph.dev, cnt.n_surv, ph.gather_x, cov, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w_out, ph.gather_x, sizeof(float) * S * d, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess && cov) e = cudaMemcpyAsync(cov_out, cov, sizeof(float) * S * d * d, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (cov) cudaFree(cov);
+  CK(e);
+  return CHISAO_OK;
+}
+
 chisao_status chisao_get_counters(chisao_ctx* c, int32_t prob, chisao_counters* out) {
   chisao_status s = check_prob(c, prob);
   if (s != CHISAO_OK) return s;

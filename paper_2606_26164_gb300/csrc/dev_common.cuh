@@ -17,6 +17,7 @@
 // every lane of the group ends with the bitwise-identical result and all
 // control decisions stay group-uniform.
 #pragma once
+#include <cfloat>
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>

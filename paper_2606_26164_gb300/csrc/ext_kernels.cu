@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
       const float sy = syh + syl;
       ss = g.sum(ss);
       yy = g.sum(yy);
-      if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy)) {
+      if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && 1.0f / sy <= FLT_MAX) {
         const int len = P.hlen[i];
         for (int k = min(len, S.m - 1); k > 0; --k) {      // shift the pairs one slot back
           const size_t o = ((size_t)i * MMAX + k) * DP + j0;
@@ -259,6 +259,57 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_anti_step(ProbDev P, StepParams 
   }
   block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
   block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
+}
+
+// ------------------------------------------------------------------ Laplace widths
+// Sec. 3.2.3 keeps a surviving sample's inverse-Hessian estimate for width
+// estimation.  The estimate is the matrix H the two-loop recursion applies; its
+// column j is H e_j (the recursion on the unit vector e_j), and the Laplace
+// approximation at the mode gives the width sqrt(H_jj) along coordinate j.  One
+// lane group per survivor, d recursions from the history in registers.
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_widths(ProbDev P, int rows, float* __restrict__ w,
+                                                   float* __restrict__ cov) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int r = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  if (r >= rows || r >= P.cnt->n_surv) return;
+  const int i = P.l_surv[r];
+  const int j0 = V * g.l, d = P.d;
+  const int len = P.hlen[i];
+  float s[MMAX][V], y[MMAX][V], rho[MMAX], gam;
+  load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
+  for (int j = 0; j < d; ++j) {
+    float e[V], p[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = (j0 + v == j) ? 1.f : 0.f;
+    two_loop<V, LPS>(s, y, rho, len, gam, e, p, g);          // p = -H e_j
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (cov && j0 + v < d) cov[((size_t)r * d + j) * d + j0 + v] = -p[v];
+      if (j0 + v == j) w[(size_t)r * d + j] = sqrtf(fmaxf(-p[v], 0.f));
+    }
+  }
+}
+
+template <int DP>
+static cudaError_t widths_dp(const ProbDev& P, int rows, float* w, float* cov, cudaStream_t st) {
+  constexpr int LPS = DP / VL;
+  const unsigned blocks = (unsigned)(((long long)rows * LPS + NT_OBJ - 1) / NT_OBJ);
+  k_widths<DP><<<blocks, NT_OBJ, 0, st>>>(P, rows, w, cov);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widths(const ProbDev& P, int rows, float* w, float* cov, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  switch (P.dp) {
+    case 4: return widths_dp<4>(P, rows, w, cov, st);
+    case 8: return widths_dp<8>(P, rows, w, cov, st);
+    case 16: return widths_dp<16>(P, rows, w, cov, st);
+    case 32: return widths_dp<32>(P, rows, w, cov, st);
+    case 64: return widths_dp<64>(P, rows, w, cov, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ launchers

@@ -44,6 +44,10 @@ cudaError_t launch_gather_modes(const ProbDev& P, float* xo, float* fo, cudaStre
 cudaError_t prepare_kernel_attributes();
 
 // Phases 1, 5 and 6 around a batched evaluator (ext_kernels.cu)
+// Laplace widths of the first n_surv survivors (l_surv order): w[r][j] = sqrt(H_jj),
+// cov[r][j][:] = H e_j when cov is not null (H the sample's L-BFGS inverse-Hessian
+// estimate); rows is the host's count of survivors (the grid size).
+cudaError_t launch_widths(const ProbDev& P, int rows, float* w, float* cov, cudaStream_t st);
 cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const ExtBuf& E, int arg,
                        cudaStream_t st);
 

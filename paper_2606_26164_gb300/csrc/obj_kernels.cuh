@@ -126,7 +126,8 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 //   direction; backtracking Armijo over alpha0 2^-t on the box projection
 //   x_t = clip(x + alpha p), F(x_t) <= F(x) + c1 grad F^T (x_t - x), first pass
 //   wins (alpha0 = 1, or min(1, 1/|grad F|_inf) on an empty history); new
-//   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y|, s^T y summed from
+//   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y| and 1/s^T y is finite
+//   (a subnormal s^T y near a mode at the origin would give rho = inf), s^T y summed from
 //   exact products in double-single.  A failed search clears the history.
 // With a row list (rows, *nrows on the device) only those samples iterate:
 // the final FP32 refinement of the survivors.
@@ -273,13 +274,14 @@ __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase
       const float sy = syh + syl;
       ss = g.sum(ss);                                // sums of squares: no cancellation
       yy = g.sum(yy);
-      if (sy > curv_eps * sqrtf(ss) * sqrtf(yy)) {
+      const float rsy = 1.0f / sy;
+      if (sy > curv_eps * sqrtf(ss) * sqrtf(yy) && rsy <= FLT_MAX) {   // rho = 1/s^T y finite
 #pragma unroll
         for (int k = MMAX - 1; k > 0; --k) rho[k] = rho[k - 1];
         head = head == 0 ? MMAX - 1 : head - 1;      // the oldest row takes the newest pair
         hist_s[head][threadIdx.x] = make_float4(sv[0], sv[1], sv[2], sv[3]);
         hist_y[head][threadIdx.x] = make_float4(yv[0], yv[1], yv[2], yv[3]);
-        rho[0] = 1.0f / sy;
+        rho[0] = rsy;
         len = min(len + 1, S.m);
         gam = sy / yy;
       }

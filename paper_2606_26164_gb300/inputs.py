@@ -91,6 +91,25 @@ def mixture4_d2(n: int = 1024, seed: int = 0) -> Problem:
     return Problem(d, n, lo, hi, obj, _uniform_box(rng, n, lo, hi), eps_grad=1e-3, sigma_mode=0.5)
 
 
+def mixture2_d6(n: int = 2048, seed: int = 0, noise_sigma: float = 0.0) -> Problem:
+    """The noise-robustness workload of Sec. 5.6: two equally weighted unit-variance
+    isotropic components at +2 e_1 and -2 e_1 in d = 6 (peaks four sigma apart).
+    The box [-6, 6]^6 and the population size are this workload's choices (the paper
+    states neither)."""
+    d = 6
+    means = np.zeros((2, d))
+    means[0, 0], means[1, 0] = 2.0, -2.0
+    obj = Objective(OBJ_MIXTURE_DIAG, d, {"weights": np.full(2, 0.5), "means": means, "sigmas": np.ones((2, d))},
+                    noise_sigma)
+    lo, hi = np.full(d, -6.0), np.full(d, 6.0)
+    rng = np.random.default_rng(6000 + seed)
+    return Problem(d, n, lo, hi, obj, _uniform_box(rng, n, lo, hi), eps_grad=1e-3, sigma_mode=1.0)
+
+
+# the noise levels of the Sec. 5.6 table
+NOISE_LEVELS = (1e-3, 1e-2, 0.05, 0.1, 0.2, 0.5, 1.0)
+
+
 def _separated_means(rng, K, d, box, sig_max, sep):
     means = np.empty((K, d))
     for k in range(K):
@@ -230,6 +249,7 @@ WORKLOADS = {
     "mixture32_d16": mixture32_d16,
     "quadratic_d64": quadratic_d64,
     "mixture256_d64": mixture256_d64,
+    "mixture2_d6": mixture2_d6,
 }
 for _name in BENCHMARK_KINDS:
     if _name != "bukin6":

@@ -258,3 +258,19 @@ def test_carry_tiger_seeding_on_ackley(d):
             assert np.all(_local_mode_errors(prob, fx) <= 1e-3)
         model.close()
     assert best[CH.SEED_CARRY_TIGER] > best[CH.SEED_UNIFORM] + 5.0
+
+
+@pytest.mark.parametrize("noise", I.NOISE_LEVELS)
+def test_two_mode_d6_noise_levels(noise):
+    """The Sec. 5.6 noise workload (d = 6, unit components at +-2 e_1) at each noise
+    level of its table, exact gradients: both peaks within 1e-3 sigma, no spurious
+    mode, over three seeds."""
+    for seed in range(3):
+        prob = I.mixture2_d6(n=2048, seed=seed, noise_sigma=noise)
+        P = M.Params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=seed)
+        model = U.open_ctx(prob, P)
+        fx, ff = _run(model, P.n_osc)
+        mx, mf, negH = MD.significant_modes(prob)
+        frac, worst, _ = MD.recovery(fx, mx, negH)
+        assert frac == 1.0 and fx.shape[0] == 2, (seed, frac, fx.shape)
+        model.close()

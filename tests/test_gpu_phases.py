@@ -294,3 +294,73 @@ def test_seeding(method, d):
         np.testing.assert_array_equal(x[E == 0], np.broadcast_to(c, x.shape)[E == 0])   # off-ray axes at the centre
     assert model.counters(0)["cycles"] == 0
     model.close()
+
+
+def _history(rng, N, d, m, hlen):
+    S = np.zeros((N, m, d))
+    Y = np.zeros((N, m, d))
+    for n in range(N):
+        B = rng.standard_normal((d, d)) / np.sqrt(d)
+        A = B @ B.T + 0.5 * np.eye(d)
+        for k in range(hlen[n]):
+            s = rng.standard_normal(d)
+            S[n, k], Y[n, k] = s, A @ s
+    return S, Y
+
+
+@pytest.mark.parametrize("d,m,p_stuck", [(2, 5, 0.5), (5, 10, 0.3), (16, 10, 0.7), (64, 10, 0.2), (7, 4, 0.0)])
+def test_laplace_widths(d, m, p_stuck):
+    """Widths and inverse-Hessian rows of the survivors from their stored history
+    (empty histories included: H = I) against the oracle on the same binary32
+    pairs; survivors in sample-index order, none at all when nothing is stuck."""
+    rng = np.random.default_rng(100 + d)
+    N = 333
+    prob = I.small_quadratic(d, N, seed=d)
+    P = M.Params(m=m, grad_mode=M.GRAD_ADJOINT)
+    model = U.open_ctx(prob, P)
+    st = M.new_state(prob.x0, m)
+    st.hlen = rng.integers(0, m + 1, size=N)
+    st.S, st.Y = _history(rng, N, d, m, st.hlen)
+    st = U.rounded(st)
+    st.stuck = rng.random(N) < p_stuck
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_LISTS)
+    w, H = model.widths(0, cov=True)
+    idx = np.flatnonzero(st.stuck)
+    assert w.shape == (idx.size, d) and H.shape == (idx.size, d, d)
+    if idx.size == 0:
+        model.close()
+        return
+    H_ref, w_ref = M.laplace_widths(st, idx)
+    # H e_j in binary32: each row within 1e-5 of its norm (the direction test's bound)
+    rows = H.reshape(-1, d).astype(np.float64)
+    rows_ref = H_ref.reshape(-1, d)
+    err = U.rel_err_rows(rows, rows_ref)
+    assert err.max() <= 1e-5, err.max()
+    # w^2 = H_jj within the same bound relative to |H e_j|
+    scale = np.abs(H_ref).max(axis=2)
+    assert np.all(np.abs(w.astype(np.float64) ** 2 - w_ref ** 2) <= 1e-5 * scale)
+    empty = st.hlen[idx] == 0
+    np.testing.assert_array_equal(w[empty], np.ones((empty.sum(), d), np.float32))
+    w_only, none = model.widths(0)
+    assert none is None
+    np.testing.assert_array_equal(w_only, w)
+    model.close()
+
+
+def test_laplace_widths_after_cycles_match_the_mode_curvature():
+    """d = 2, four isotropic components (sigma = 0.5): after the cycles every
+    mode's width from its kept history is the Laplace width sqrt(diag(-Hess f)^-1)
+    at the returned point to 1 %."""
+    prob = I.mixture4_d2(n=1024)
+    P = M.Params(n_osc=3, m=5, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=0)
+    model = U.open_ctx(prob, P)
+    for _ in range(P.n_osc):
+        model.step()
+    fx, _ = model.modes(0)
+    w, _ = model.widths(0)
+    assert fx.shape[0] == 4 and w.shape == (4, 2)
+    for x, wr in zip(fx.astype(np.float64), w.astype(np.float64)):
+        lap = np.sqrt(np.diag(np.linalg.inv(-OB.hessian(prob.objective, x))))
+        np.testing.assert_allclose(wr, lap, rtol=1e-2)
+    model.close()

@@ -1,5 +1,6 @@
 """Whole-cycle pins for the oracle (Algorithm 1, Propositions 1-2, Remark 1)."""
 import numpy as np
+import pytest
 
 from oracle import method as M
 from oracle import modes as MD
@@ -74,3 +75,17 @@ def test_mahalanobis_recovery_metric():
     found = np.array([[4e-4, 0.0], [0.0, 2e-3]])
     frac, worst, best = MD.recovery(found, mx, negH)
     assert frac == 1.0 and abs(best[0] - 8e-4) < 1e-15
+
+
+@pytest.mark.parametrize("noise", [0.0, 1.0])
+def test_two_mode_d6_noise_workload_both_peaks(noise):
+    """The Sec. 5.6 workload (d = 6, unit components at +-2 e_1): with exact
+    gradients the evaluation noise enters only through the Armijo test and the
+    quality gate, and both peaks are returned with nothing else."""
+    prob = I.mixture2_d6(n=256, seed=0, noise_sigma=noise)
+    P = M.Params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=0)
+    (ox, of), _ = M.run(prob, P)
+    mx, mf, negH = MD.significant_modes(prob)
+    assert len(mx) == 2 and abs(abs(mx[0][0]) - 2.0) < 2e-3     # x = 2 tanh(2 x): 1.99865
+    frac, worst, _ = MD.recovery(ox, mx, negH)
+    assert frac == 1.0 and ox.shape[0] == 2

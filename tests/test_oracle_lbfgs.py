@@ -81,6 +81,17 @@ def test_curvature_pair_rejected_when_not_positive():
     assert list(st.hlen) == [1, 0] and st.rho[0, 0] == 1.0
 
 
+def test_curvature_pair_rejected_when_rho_would_overflow():
+    """s^T y = 1e-310 (subnormal) passes the angle test but 1 / s^T y is not a
+    finite double: the pair is not stored, so no infinite rho enters the history."""
+    st = M.new_state(np.zeros((2, 2)), 3)
+    s = np.array([[1e-155, 0.0], [1e-150, 0.0]])
+    y = np.array([[1e-155, 0.0], [1e-150, 0.0]])
+    ok = M.push_pair(st, np.arange(2), s, y, M.Params())
+    assert list(ok) == [False, True]
+    assert list(st.hlen) == [0, 1] and np.all(np.isfinite(st.rho))
+
+
 def test_phase1_converges_to_quadratic_center():
     """Proposition 1: on a strictly log-concave target every sample converges to theta*."""
     p = I.small_quadratic(4, 16, seed=5, cond=10.0)
@@ -101,3 +112,77 @@ def test_phase1_fd_and_adjoint_agree_on_mixture():
         M.lbfgs_iterations(p, st, P, 30)
         out.append(st.x.copy())
     np.testing.assert_allclose(out[0], out[1], atol=1e-5)
+
+
+def _state_with_pairs(pairs_per_sample, d, m):
+    N = len(pairs_per_sample)
+    st = M.new_state(np.zeros((N, d)), m)
+    for n, pairs in enumerate(pairs_per_sample):
+        st.hlen[n] = len(pairs)
+        for i, (s, y) in enumerate(pairs):                 # slot 0 = newest
+            st.S[n, i], st.Y[n, i], st.rho[n, i] = s, y, 1.0 / (s @ y)
+    return st
+
+
+def test_laplace_widths_eigenvector_pairs_closed_form():
+    """Pairs along eigenvectors v_i of an SPD B (y = B s): the inverse update of
+    each pair leaves the others alone, so H = sum_i v_i v_i^T / lam_i over the
+    stored pairs plus gamma times the projector onto the rest, gamma = 1 / lam of
+    the newest pair.  A wrong gamma (oldest pair, or 1) or a dropped rho s s^T term
+    changes H."""
+    d, m = 6, 4
+    rng = np.random.default_rng(3)
+    Qm, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    lam = np.array([0.5, 2.0, 3.0, 7.0, 11.0, 13.0])
+    used = [3, 0, 4]                                       # newest first
+    pairs = [(2.5 * Qm[:, i], 2.5 * lam[i] * Qm[:, i]) for i in used]
+    st = _state_with_pairs([pairs], d, m)
+    H, w = M.laplace_widths(st, [0])
+    Vu = Qm[:, used]
+    P_rest = np.eye(d) - Vu @ Vu.T
+    H_ref = Vu @ np.diag(1.0 / lam[used]) @ Vu.T + P_rest / lam[used[0]]
+    np.testing.assert_allclose(H[0], H_ref, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(w[0], np.sqrt(np.diag(H_ref)), rtol=1e-12)
+
+
+def test_laplace_widths_conjugate_pairs_give_the_inverse_hessian():
+    """d pairs along B-conjugate directions (s_i^T B s_j = 0), y = B s: the L-BFGS
+    matrix is B^-1 exactly, whatever gamma (the finite-termination property of
+    BFGS on a quadratic), so the widths are sqrt(diag B^-1)."""
+    d = 5
+    rng = np.random.default_rng(8)
+    C = rng.standard_normal((d, d))
+    B = C @ C.T + 0.3 * np.eye(d)
+    S = []
+    for v in rng.standard_normal((d, d)):                 # B-orthogonalise (Gram-Schmidt)
+        for s in S:
+            v = v - (s @ B @ v) / (s @ B @ s) * s
+        S.append(v)
+    pairs = [(s, B @ s) for s in S[::-1]]
+    st = _state_with_pairs([pairs], d, d)
+    H, w = M.laplace_widths(st, [0])
+    Binv = np.linalg.inv(B)
+    np.testing.assert_allclose(H[0], Binv, rtol=1e-9, atol=1e-12 * np.abs(Binv).max())
+    np.testing.assert_allclose(w[0], np.sqrt(np.diag(Binv)), rtol=1e-9)
+
+
+def test_laplace_widths_secant_symmetry_and_empty_history():
+    """Any history: H is symmetric positive definite and satisfies the secant
+    equation H y = s of the newest pair; no pairs: H = I, widths 1."""
+    d, m = 7, 5
+    rng = np.random.default_rng(21)
+    samples = []
+    for n in range(4):
+        Cm = rng.standard_normal((d, d))
+        A = Cm @ Cm.T + 0.5 * np.eye(d)
+        samples.append([(s, A @ s) for s in rng.standard_normal((n + 1, d))])
+    samples.append([])
+    st = _state_with_pairs(samples, d, m)
+    H, w = M.laplace_widths(st, np.arange(5))
+    for n in range(4):
+        s0, y0 = samples[n][0]
+        np.testing.assert_allclose(H[n] @ y0, s0, rtol=1e-9, atol=1e-12 * np.abs(s0).max())
+        np.testing.assert_allclose(H[n], H[n].T, rtol=1e-9, atol=1e-12 * np.abs(H[n]).max())
+        assert np.linalg.eigvalsh(H[n]).min() > 0
+    np.testing.assert_array_equal(H[4], np.eye(d))
+    np.testing.assert_array_equal(w[4], np.ones(d))
