@@ -346,7 +346,7 @@ def noise_table_leg(CH, trials):
         errs, ms = [], []
         for seed in range(trials):
             prob = I.mixture2_d6(n=2048, seed=seed, noise_sigma=noise)
-            prm = CH.default_params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=GRAD["adjoint"], seed=seed)
+            prm = CH.default_params(n_osc=3, m=10, eps_grad=prob.eps_grad, grad_mode=GRAD["adjoint"], seed=seed)
             model = CH.Chisao([prob], prm)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(model._stream)

@@ -72,8 +72,31 @@ typedef enum {
   CHISAO_OBJ_TRID = 15,
   /* -100 sqrt|x_2 - x_1^2 / 100| - |x_1 + 10| / 100, d = 2,
    * domain [-15, -5] x [-3, 3]                                              */
-  CHISAO_OBJ_BUKIN6 = 16
+  CHISAO_OBJ_BUKIN6 = 16,
+  /* A caller-supplied batched evaluator (chisao_objective.eval below): the
+   * cycle runs Phases 1, 5 and 6 as per-sample kernels around batched calls
+   * to it, as in the tensor-core mode.  Needs grad_mode CHISAO_GRAD_ADJOINT
+   * (the evaluator returns exact gradients), noise_sigma 0, hlc_value_only 0. */
+  CHISAO_OBJ_EXTERNAL = 20
 } chisao_objective_kind;
+
+/* Batched evaluator of a CHISAO_OBJ_EXTERNAL objective (Sec. 3.1: f is a
+ * black box and its gradient is supplied).  Every pointer is device memory.
+ * The points are rows of x (row r starts at x + r * ldx, its first d floats
+ * are the coordinates).  The rows to evaluate are 0 .. rows-1 when idx is NULL,
+ * else idx[k] for k < *count (idx and count on the device, *count <= rows,
+ * every idx[k] < rows).  For each such row write f[r] (when f is not NULL) and
+ * the exact gradient of f, g[r * ldg + j] for j < d (when g is not NULL);
+ * writing other rows is allowed and ignored.  All work must go onto `stream`
+ * (a cudaStream_t) and may finish after the call returns.  With use_graph = 1
+ * the call happens while the stream is being captured into a CUDA graph, so
+ * it must be capture-safe (no synchronization, no reading *count on the
+ * host); the graph then replays the captured work every cycle.  Return 0 on
+ * success; any other value aborts the step with CHISAO_ERR_CUDA and a message
+ * naming that value. */
+typedef int32_t (*chisao_batch_eval_fn)(void *user, const float *x, int32_t ldx, int64_t rows,
+                                        const int32_t *idx, const int32_t *count, float *f,
+                                        float *g, int32_t ldg, void *stream);
 
 /* How gradients are obtained (Section 3.1: central differences of the values,
  * or an exact gradient where one is available). */
@@ -113,6 +136,10 @@ typedef struct {
    * by the point's binary32 coordinates and the Philox seed.  Exact (adjoint)
    * gradients are those of the noise-free f. */
   double noise_sigma;
+  /* CHISAO_OBJ_EXTERNAL: the evaluator and its opaque argument (the caller
+   * keeps both valid until chisao_destroy). */
+  chisao_batch_eval_fn eval;
+  void *user;
 } chisao_objective;
 
 /* One problem: dimension, population size, the box Theta and the initial

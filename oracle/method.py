@@ -262,7 +262,9 @@ def lbfgs_iterations(prob, st: State, P: Params, n_iter: int, fresh_gradient: bo
         Pd = lbfgs_direction(G, st.S, st.Y, st.rho, st.hlen)
         alpha0 = np.where(st.hlen > 0, 1.0, np.minimum(1.0, inv_g))
         gp = np.einsum("nd,nd->n", G, Pd)
-        bad = moving & ~(gp < 0.0)                       # not a descent direction: restart
+        # restart when p is an ascent direction or not finite; g^T p = 0 (a product that
+        # underflows next to a stationary point) keeps the history, the mode's curvature
+        bad = moving & ~(gp <= 0.0)
         if bad.any():
             st.hlen[bad] = 0
             Pd[bad] = -G[bad]

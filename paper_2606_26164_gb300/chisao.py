@@ -47,10 +47,79 @@ class CParams(C.Structure):
 _DP = C.POINTER(C.c_double)
 
 
+# int32 (*)(user, x, ldx, rows, idx, count, f, g, ldg, stream)
+BATCH_EVAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p)
+
+
 class CObjective(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_comp", C.c_int32), ("weights", _DP), ("means", _DP),
                 ("sigmas", _DP), ("chol", _DP), ("center", _DP), ("Q", _DP), ("lam", _DP),
-                ("noise_sigma", C.c_double)]
+                ("noise_sigma", C.c_double), ("eval", BATCH_EVAL_FN), ("user", C.c_void_p)]
+
+
+class _DevArray:
+    """A device buffer seen by torch.as_tensor (CUDA array interface, no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+def _external_evaluator(fn, d: int, errors: list):
+    """The C evaluator of an OBJ_EXTERNAL objective: runs fn on the listed rows on
+    the stream the library passes (reading the row count synchronizes that stream,
+    so contexts with such objectives run without CUDA graphs)."""
+    import torch
+
+    def call(user, x, ldx, rows, idx, count, f, g, ldg, stream):
+        try:
+            if rows <= 0:
+                return 0
+            with torch.cuda.stream(torch.cuda.ExternalStream(stream)):
+                X = torch.as_tensor(_DevArray(x, (rows, ldx), "<f4"), device="cuda")
+                if idx:
+                    k = int(torch.as_tensor(_DevArray(count, (1,), "<i4"), device="cuda").item())
+                    if k <= 0:
+                        return 0
+                    sel = torch.as_tensor(_DevArray(idx, (k,), "<i4"), device="cuda").long()
+                else:
+                    sel = None
+                pts = (X[sel] if sel is not None else X)[:, :d].contiguous()
+                fv, gv = fn(pts)
+                if f:
+                    Fo = torch.as_tensor(_DevArray(f, (rows,), "<f4"), device="cuda")
+                    if sel is None:
+                        Fo.copy_(fv.reshape(-1))
+                    else:
+                        Fo.index_copy_(0, sel, fv.reshape(-1).to(torch.float32))
+                if g:
+                    Go = torch.as_tensor(_DevArray(g, (rows, ldg), "<f4"), device="cuda")
+                    gv = gv.reshape(-1, d).to(torch.float32)
+                    if sel is None:
+                        Go[:, :d].copy_(gv)
+                    else:
+                        Go[sel, :d] = gv
+            return 0
+        except Exception as e:                 # reported by the next call into the binding
+            errors.append(e)
+            return ERR_ARG
+
+    return BATCH_EVAL_FN(call)
+
+
+def autograd_objective(fval):
+    """fn for an OBJ_EXTERNAL objective from a value-only torch function
+    fval(x [k, d]) -> f [k]: the gradient comes from torch.autograd."""
+    import torch
+
+    def fn(x):
+        with torch.enable_grad():
+            xr = x.detach().requires_grad_(True)
+            fv = fval(xr)
+            (gv,) = torch.autograd.grad(fv.sum(), xr)
+        return fv.detach(), gv
+    return fn
 
 
 class CProblem(C.Structure):
@@ -105,6 +174,12 @@ def library() -> C.CDLL:
     return _lib
 
 
+def copy_params(p: CParams) -> CParams:
+    q = CParams()
+    C.memmove(C.byref(q), C.byref(p), C.sizeof(CParams))
+    return q
+
+
 def default_params(**over) -> CParams:
     p = CParams()
     library().chisao_default_params(C.byref(p))
@@ -130,6 +205,8 @@ class Chisao:
                  stream=None):
         lib = library()
         self._keep = []
+        self._callbacks = []                   # live as long as the context
+        self._cb_errors = []
         cprobs = (CProblem * len(problems))()
         for q, pr in enumerate(problems):
             ob = pr.objective
@@ -142,6 +219,13 @@ class Chisao:
                             means=_dptr(A.get("means")), sigmas=_dptr(A.get("sigmas")), chol=_dptr(A.get("chol")),
                             center=_dptr(A.get("center")), Q=_dptr(A.get("Q")), lam=_dptr(A.get("lam")),
                             noise_sigma=float(getattr(ob, "noise_sigma", 0.0)))
+            if ob.kind == I.OBJ_EXTERNAL:
+                cb = _external_evaluator(ob.fn, pr.d, self._cb_errors)
+                self._callbacks.append(cb)
+                co.eval = cb
+                if params.use_graph:
+                    params = copy_params(params)
+                    params.use_graph = 0           # the evaluator reads the row count on the host
             cprobs[q] = CProblem(d=pr.d, n=pr.n, lo=_dptr(lo), hi=_dptr(hi),
                                  x0=x0.ctypes.data_as(C.POINTER(C.c_float)), objective=co)
         self.problems = list(problems)
@@ -175,6 +259,10 @@ class Chisao:
 
     # ------------------------------------------------------------------ core API
     def _check(self, st, what):
+        if self._cb_errors:
+            e = self._cb_errors[0]
+            self._cb_errors.clear()
+            raise ChisaoError(f"{what}: the external objective raised {e!r}") from e
         if st != OK:
             msg = library().chisao_last_error(self.ctx).decode()
             raise ChisaoError(f"{what} failed ({st}): {msg}")

@@ -31,8 +31,11 @@ struct ProbHost {
   float* gather_x = nullptr;
   float* gather_f = nullptr;
   uint8_t* tc_weights = nullptr;     // tensor-core operand tiles (full-covariance mixtures)
-  bool tc = false;                   // the cycle runs on the tensor-core objective
+  bool tc = false;                   // the cycle runs around a batched evaluator (tensor cores or external)
   ExtBuf ext{};                      // its buffers
+  chisao_batch_eval_fn ext_eval = nullptr;   // CHISAO_OBJ_EXTERNAL: the caller's evaluator
+  void* ext_user = nullptr;
+  mutable int32_t ext_status = 0;    // its last non-zero return value, for the error message
 };
 
 // Bump allocator over the arena; with a null base it only measures.
@@ -84,6 +87,13 @@ chisao_status fail(chisao_ctx* c, chisao_status s, const std::string& msg) {
 }
 
 chisao_status cuda_fail(chisao_ctx* c, cudaError_t e, const char* what) {
+  for (const ProbHost& ph : c->probs)
+    if (ph.ext_status != 0) {
+      const int32_t r = ph.ext_status;
+      ph.ext_status = 0;
+      return fail(c, CHISAO_ERR_CUDA, std::string(what) + ": the external objective's evaluator returned " +
+                                          std::to_string(r));
+    }
   return fail(c, CHISAO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -148,8 +158,25 @@ chisao_status validate_problem(const chisao_problem* pr, std::string& why) {
     if (!o.center || !o.Q || !o.lam) { why = "quadratic needs center, Q and lam"; return CHISAO_ERR_ARG; }
   } else if (is_bench_kind(o.kind)) {
     if (o.kind == CHISAO_OBJ_BUKIN6 && pr->d != 2) { why = "Bukin N.6 needs d = 2"; return CHISAO_ERR_ARG; }
+  } else if (o.kind == CHISAO_OBJ_EXTERNAL) {
+    if (!o.eval) { why = "an external objective needs its evaluator"; return CHISAO_ERR_ARG; }
+    if (o.noise_sigma != 0) { why = "an external objective adds its own noise (noise_sigma must be 0)"; return CHISAO_ERR_ARG; }
   } else {
     why = "unknown objective kind";
+    return CHISAO_ERR_ARG;
+  }
+  return CHISAO_OK;
+}
+
+// Objective kind against the gradient mode and the Phase 5 variant.
+chisao_status validate_mode(const chisao_problem* pr, const chisao_params* p, std::string& why) {
+  const int kind = pr->objective.kind;
+  if (p->grad_mode == CHISAO_GRAD_ADJOINT_TC && kind != CHISAO_OBJ_MIXTURE_FULL) {
+    why = "the tensor-core mode needs full-covariance mixtures";
+    return CHISAO_ERR_ARG;
+  }
+  if (kind == CHISAO_OBJ_EXTERNAL && (p->grad_mode != CHISAO_GRAD_ADJOINT || p->hlc_value_only)) {
+    why = "an external objective supplies exact gradients: grad_mode ADJOINT, hlc_value_only 0";
     return CHISAO_ERR_ARG;
   }
   return CHISAO_OK;
@@ -212,7 +239,7 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
   ph.gather_x = b.take<float>(n * d);
   ph.gather_f = b.take<float>(n);
   if (pr.objective.kind == CHISAO_OBJ_MIXTURE_FULL) ph.tc_weights = b.take<uint8_t>(tc_weight_bytes(pr.objective.n_comp));
-  ph.tc = prm.grad_mode == CHISAO_GRAD_ADJOINT_TC;
+  ph.tc = prm.grad_mode == CHISAO_GRAD_ADJOINT_TC || pr.objective.kind == CHISAO_OBJ_EXTERNAL;
   if (ph.tc) {
     ExtBuf& E = ph.ext;
     E.p = b.take<float>(n * dp);
@@ -325,6 +352,7 @@ cudaError_t launch_objective(int which, const ProbHost& ph, int gm, int arg, con
     case CHISAO_OBJ_MIXTURE_DIAG: return launch_obj_mixdiag(which, gm, ph.dev, ph.sp, arg, ea, st);
     case CHISAO_OBJ_QUADRATIC: return launch_obj_quad(which, gm, ph.dev, ph.sp, arg, ea, st);
     case CHISAO_OBJ_MIXTURE_FULL: return launch_obj_mixfull(which, gm, ph.dev, ph.sp, arg, ea, st);
+    case CHISAO_OBJ_EXTERNAL: return cudaErrorNotSupported;      // no per-sample device objective
     default: return launch_obj_bench(which, gm, ph.dev, ph.sp, arg, ea, st);
   }
 }
@@ -349,9 +377,17 @@ cudaError_t enqueue_explore(const ProbHost& ph, cudaStream_t st) {
   return launch_objective(OKID_ANTI, ph, ph.sp.grad_mode, 0, nullptr, st);
 }
 
-// ---- the tensor-core objective: batched evaluations around per-sample kernels
+// ---- batched objectives (the tensor-core mixture, or the caller's evaluator) around per-sample kernels
 cudaError_t tc_eval_rows(const ProbHost& ph, const float* x, float* f, float* g, int rows, const int* idx,
                          const int* count, cudaStream_t st) {
+  if (ph.kind == CHISAO_OBJ_EXTERNAL) {
+    const int32_t r = ph.ext_eval(ph.ext_user, x, ph.dp, rows, idx, count, f, g, ph.dp, st);
+    if (r != 0) {
+      ph.ext_status = r;
+      return cudaErrorUnknown;
+    }
+    return cudaSuccess;
+  }
   return tc_launch_mixfull(x, ph.dp, rows, ph.d, ph.K, ph.tc_weights, f, g, ph.dp, &ph.dev.cnt->err, st, idx,
                            count);
 }
@@ -420,8 +456,8 @@ cudaError_t enqueue_cycle_tc(const ProbHost& ph, bool last, cudaStream_t st) {
     if ((e = launch_reseed(ph.dev, ph.sp, st)) != cudaSuccess) return e;
     if ((e = enqueue_hlc_tc(ph, st)) != cudaSuccess) return e;
     if ((e = enqueue_anti_tc(ph, st)) != cudaSuccess) return e;
-  } else if ((e = enqueue_refine(ph, ph.sp.n_refine, st)) != cudaSuccess) {
-    return e;
+  } else if (ph.kind == CHISAO_OBJ_MIXTURE_FULL && (e = enqueue_refine(ph, ph.sp.n_refine, st)) != cudaSuccess) {
+    return e;                        // the FP32 polish of tensor-core modes (an external objective is exact)
   }
   return launch_cycle_end(ph.dev, st);
 }
@@ -538,8 +574,7 @@ chisao_status chisao_arena_bytes(const chisao_problem* probs, int32_t n_probs, c
   for (int q = 0; q < n_probs; ++q) {
     if (validate_problem(&probs[q], why) != CHISAO_OK) return CHISAO_ERR_ARG;
     ProbHost ph;
-    if (params->grad_mode == CHISAO_GRAD_ADJOINT_TC && probs[q].objective.kind != CHISAO_OBJ_MIXTURE_FULL)
-      return CHISAO_ERR_ARG;                     // the tensor-core mode needs full-covariance mixtures
+    if (validate_mode(&probs[q], params, why) != CHISAO_OK) return CHISAO_ERR_ARG;
     layout_problem(b, probs[q], *params, ph);
   }
   *bytes = (b.off + ALIGN - 1) / ALIGN * ALIGN;
@@ -557,7 +592,7 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     return CHISAO_ERR_ARG;
   }
   for (int q = 0; q < n_probs; ++q)
-    if (validate_problem(&probs[q], why) != CHISAO_OK) {
+    if (validate_problem(&probs[q], why) != CHISAO_OK || validate_mode(&probs[q], params, why) != CHISAO_OK) {
       fprintf(stderr, "chisao_create: problem %d: %s\n", q, why.c_str());
       return CHISAO_ERR_ARG;
     }
@@ -613,6 +648,8 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     ph.n = pr.n;
     ph.kind = pr.objective.kind;
     ph.K = pr.objective.n_comp;
+    ph.ext_eval = pr.objective.eval;
+    ph.ext_user = pr.objective.user;
     layout_problem(b, pr, *params, ph);
     ProbDev& P = ph.dev;
     P.d = ph.d;
@@ -827,6 +864,12 @@ chisao_status chisao_eval(chisao_ctx* c, int32_t prob, const float* x_dev, int64
   if (grad_mode < 0 || grad_mode > 3) return fail(c, CHISAO_ERR_ARG, "unknown grad_mode");
   if (n == 0 || (!f_dev && !g_dev)) return CHISAO_OK;
   const ProbHost& ph = c->probs[prob];
+  if (ph.kind == CHISAO_OBJ_EXTERNAL) {
+    if (grad_mode != CHISAO_GRAD_ADJOINT) return fail(c, CHISAO_ERR_ARG, "an external objective supplies exact gradients only");
+    const int32_t r = ph.ext_eval(ph.ext_user, x_dev, ph.d, n, nullptr, nullptr, f_dev, g_dev, ph.d, c->stream);
+    if (r != 0) return fail(c, CHISAO_ERR_CUDA, "the external objective's evaluator returned " + std::to_string(r));
+    return CHISAO_OK;
+  }
   if (grad_mode == CHISAO_GRAD_ADJOINT_TC) {
     if (ph.kind != CHISAO_OBJ_MIXTURE_FULL) return fail(c, CHISAO_ERR_ARG, "tensor-core mode needs a full-covariance mixture");
     CK(tc_launch_mixfull(x_dev, ph.d, (int)n, ph.d, ph.K, ph.tc_weights, f_dev, g_dev, ph.d, &ph.dev.cnt->err,

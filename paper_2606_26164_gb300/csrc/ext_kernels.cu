@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
       load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
       two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
-      if (!(g.sum(dotv<V>(G, p)) < 0.f)) {           // not a descent direction: restart
+      if (!(g.sum(dotv<V>(G, p)) <= 0.f)) {          // ascent or not finite: restart
         len = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) p[v] = -G[v];

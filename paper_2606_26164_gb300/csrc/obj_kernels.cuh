@@ -122,8 +122,8 @@ __device__ __forceinline__ void load_history(const ProbDev& P, int i, int j0, in
 
 // ------------------------------------------------------------------ Phase 1
 // n_iter iterations of L-BFGS per sample, all in registers:
-//   p = -H grad F (two-loop); restart with -grad F when p is not a descent
-//   direction; backtracking Armijo over alpha0 2^-t on the box projection
+//   p = -H grad F (two-loop); restart with -grad F when p is an ascent direction
+//   or not finite; backtracking Armijo over alpha0 2^-t on the box projection
 //   x_t = clip(x + alpha p), F(x_t) <= F(x) + c1 grad F^T (x_t - x), first pass
 //   wins (alpha0 = 1, or min(1, 1/|grad F|_inf) on an empty history); new
 //   gradient; pair (s, y) kept iff s^T y > curv_eps |s||y| and 1/s^T y is finite
@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase
       two_loop_ring<LPS>(hist_s, hist_y, head, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       const float gp = g.sum(dotv<V>(G, p));
-      if (!(gp < 0.f)) {                           // not a descent direction: restart
+      // restart when p is an ascent direction or not finite; g^T p = 0 (the product
+      // underflows next to a stationary point) keeps the history, the mode's curvature
+      if (!(gp <= 0.f)) {
         len = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) p[v] = -G[v];

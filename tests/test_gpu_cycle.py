@@ -267,7 +267,7 @@ def test_two_mode_d6_noise_levels(noise):
     mode, over three seeds."""
     for seed in range(3):
         prob = I.mixture2_d6(n=2048, seed=seed, noise_sigma=noise)
-        P = M.Params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=seed)
+        P = M.Params(n_osc=3, m=10, eps_grad=prob.eps_grad, grad_mode=M.GRAD_ADJOINT, seed=seed)
         model = U.open_ctx(prob, P)
         fx, ff = _run(model, P.n_osc)
         mx, mf, negH = MD.significant_modes(prob)

@@ -83,7 +83,7 @@ def test_two_mode_d6_noise_workload_both_peaks(noise):
     gradients the evaluation noise enters only through the Armijo test and the
     quality gate, and both peaks are returned with nothing else."""
     prob = I.mixture2_d6(n=256, seed=0, noise_sigma=noise)
-    P = M.Params(n_osc=3, m=10, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=0)
+    P = M.Params(n_osc=3, m=10, eps_grad=prob.eps_grad, grad_mode=M.GRAD_ADJOINT, seed=0)
     (ox, of), _ = M.run(prob, P)
     mx, mf, negH = MD.significant_modes(prob)
     assert len(mx) == 2 and abs(abs(mx[0][0]) - 2.0) < 2e-3     # x = 2 tanh(2 x): 1.99865

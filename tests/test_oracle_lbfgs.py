@@ -186,3 +186,36 @@ def test_laplace_widths_secant_symmetry_and_empty_history():
         assert np.linalg.eigvalsh(H[n]).min() > 0
     np.testing.assert_array_equal(H[4], np.eye(d))
     np.testing.assert_array_equal(w[4], np.ones(d))
+
+
+def test_underflowing_descent_product_keeps_the_history():
+    """Next to a stationary point g^T p can underflow to 0 (here |g| = 1e-170): that
+    is not an ascent direction, so the history (the mode's curvature estimate) is
+    kept; an ascent direction (g^T p > 0) still clears it."""
+    d, m = 3, 4
+    prob = I.small_quadratic(d, 2, seed=3)
+    P = M.Params(m=m, grad_mode=M.GRAD_ADJOINT)
+    st = M.new_state(np.zeros((2, d)), m)
+    A = np.diag([1.0, 2.0, 3.0])
+    for n in range(2):
+        for k, s in enumerate(np.eye(d)[:2]):
+            st.S[n, k], st.Y[n, k], st.rho[n, k] = s, A @ s, 1.0 / (s @ A @ s)
+        st.hlen[n] = 2
+    st.x = np.asarray(prob.objective.arrays["center"], np.float64)[None].repeat(2, axis=0)
+    G = np.array([1e-170, 0.0, 0.0])
+    Pd = M.lbfgs_direction(G[None], st.S[:1], st.Y[:1], st.rho[:1], st.hlen[:1])
+    assert np.einsum("nd,nd->n", G[None], Pd)[0] == 0.0          # the product underflows
+    st.f = np.zeros(2)
+    st.g = -np.stack([G, G])                                     # grad f = -grad F
+    M.lbfgs_iterations(prob, st, P, 1, fresh_gradient=False)
+    assert list(st.hlen) == [2, 2]
+    # a pair with negative curvature makes p an ascent direction: the history is cleared
+    # (the restart along -grad F then fails its search here, which leaves it empty)
+    st2 = M.new_state(np.zeros((1, d)), m)
+    s, y = np.array([1.0, 0.0, 0.0]), np.array([-1.0, 0.0, 0.0])
+    st2.S[0, 0], st2.Y[0, 0], st2.rho[0, 0], st2.hlen[0] = s, y, 1.0 / (s @ y), 1
+    st2.x = st.x[:1].copy()
+    st2.g = np.array([[1.0, 0.0, 0.0]])
+    st2.f = M.evaluate(prob, st2.x)
+    M.lbfgs_iterations(prob, st2, P, 1, fresh_gradient=False)
+    assert st2.hlen[0] == 0
