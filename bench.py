@@ -202,7 +202,7 @@ def cpu_leg(spec):
     from oracle import method as M
     prob = make_problem(a["workload"], a["seed"])
     from paper_2606_26164_gb300 import inputs as I
-    rows = np.arange(a["sample_n"])
+    rows = np.arange(a.get("offset", 0), a.get("offset", 0) + a["sample_n"]) % prob.n
     sub = I.Problem(prob.d, rows.size, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad,
                     prob.sigma_mode)
     P = M.Params(n_osc=10 ** 6, m=10, eps_grad=prob.eps_grad, grad_mode=GRAD[a["grad"]], seed=a["seed"])
@@ -231,6 +231,30 @@ def run_cpu_leg(workload, grad, seed, sample_n, budget_s, max_cycles=10 ** 6):
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_cpu_legs_all_cores(workload, grad, sample_n, budget_s):
+    """The oracle on every host core at once: one single-threaded process per core,
+    each on its own slice of the same workload; aggregate samples x cycles / the
+    longest process's time."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = []
+    for k in range(n):
+        spec = json.dumps({"workload": workload, "grad": grad, "seed": 0, "sample_n": sample_n,
+                           "offset": k * sample_n, "budget_s": budget_s})
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-leg", spec], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    res = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    t = max(r["seconds"] for r in res)
+    work = sum(sample_n * r["cycles"] for r in res)
+    return {"value": work / t, "cores": n, "cycles_per_process": [r["cycles"] for r in res], "seconds": t,
+            "evals_per_s": sum(r["evals"] for r in res) / t}
 
 
 # --------------------------------------------------------------------------- GPU legs
@@ -510,6 +534,15 @@ def main():
                                    "evals_per_s": cpu["evals_per_s"]}
         except Exception as e:  # report, do not hide
             out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+        try:
+            cpa = run_cpu_legs_all_cores(args.workload, args.grad, sample_n=512, budget_s=12.0)
+            out["cpu_baseline_all_cores"] = {
+                "value": cpa["value"], "unit": "sample-cycles/s", "cores": cpa["cores"], "kind": "oracle",
+                "sample": f"{cpa['cores']} processes x 512 samples (disjoint slices of the {N}), non-final cycles "
+                          f"for {cpa['seconds']:.1f} s, {args.grad} gradients, FP64 NumPy, one BLAS thread each",
+                "evals_per_s": cpa["evals_per_s"]}
+        except Exception as e:
+            out["cpu_baseline_all_cores"] = {"value": None, "error": str(e)[:200]}
     model.close()
     if rank == 0:
         print(json.dumps(out))
