@@ -51,6 +51,16 @@ struct Bump {
   }
 };
 
+// Problems of one objective kind and padded dimension whose Phases 1, 5 and 6 run as
+// one grouped launch each (exact gradients, several problems in the context).
+struct Group {
+  int kind = 0, dp = 0;
+  std::vector<int> members;          // problem indices
+  unsigned blocks = 0;               // blocks of one per-sample launch over all members
+  GroupTab tab{};                    // device tables (one allocation, `mem`)
+  void* mem = nullptr;
+};
+
 int pad_dim(int d) {
   int dp = 4;
   while (dp < d) dp <<= 1;
@@ -76,6 +86,7 @@ struct chisao_ctx {
   std::vector<cudaEvent_t> joined;
   cudaEvent_t forked = nullptr;
   std::vector<int> branch_of;              // problem -> branch
+  std::vector<Group> groups;               // grouped Phase 1 / 5 / 6 launches (empty: per problem)
   std::string err;
 };
 
@@ -475,9 +486,86 @@ cudaError_t enqueue_problem_cycle(const ProbHost& ph, bool last, cudaStream_t st
   return launch_cycle_end(ph.dev, st);
 }
 
+cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st) {
+  switch (gr.kind) {
+    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, gr.tab, gr.blocks, st);
+    case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, gr.tab, gr.blocks, st);
+    case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, gr.tab, gr.blocks, st);
+    default: return launch_grp_bench(which, gr.dp, gr.tab, gr.blocks, st);
+  }
+}
+
+// Fork the branch streams from the context stream, run f(branch index) on each, join back.
+template <class F>
+cudaError_t forked(chisao_ctx* c, F&& f) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(c->forked, c->stream)) != cudaSuccess) return e;
+  for (cudaStream_t s : c->branch)
+    if ((e = cudaStreamWaitEvent(s, c->forked, 0)) != cudaSuccess) return e;
+  if ((e = f()) != cudaSuccess) return e;
+  for (size_t b = 0; b < c->branch.size(); ++b) {
+    if ((e = cudaEventRecord(c->joined[b], c->branch[b])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->stream, c->joined[b], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One cycle with grouped launches: the per-problem steps (release, freeze, dedup,
+// reseed, the scale passes, cycle end) run on the problems' branch streams, and each of
+// Phase 1, HLC and anti-convergence runs as one launch per group (the groups on
+// separate branches), with joins in between, since every phase needs the previous one
+// of the same problem.
+cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
+  auto per_problem = [&](auto&& body) {
+    return forked(c, [&]() -> cudaError_t {
+      for (size_t q = 0; q < c->probs.size(); ++q) {
+        const cudaError_t e = body(c->probs[q], c->branch[c->branch_of[q]]);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+  };
+  auto per_group = [&](int which) {
+    return forked(c, [&]() -> cudaError_t {
+      for (size_t k = 0; k < c->groups.size(); ++k) {
+        const cudaError_t e = launch_grouped(which, c->groups[k], c->branch[k % c->branch.size()]);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+  };
+  cudaError_t e;
+  if ((e = per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_begin(ph.dev, s); })) !=
+      cudaSuccess)
+    return e;
+  if ((e = per_group(OKID_PHASE1)) != cudaSuccess) return e;                              // Phase 1
+  if ((e = per_problem([last](const ProbHost& ph, cudaStream_t s) {                        // Phases 2-4, scales
+         cudaError_t r;
+         if ((r = launch_freeze(ph.dev, ph.sp, s)) != cudaSuccess) return r;
+         if ((r = launch_dedup(ph.dev, ph.sp, s)) != cudaSuccess) return r;
+         if (last) return cudaSuccess;
+         if ((r = launch_reseed(ph.dev, ph.sp, s)) != cudaSuccess) return r;
+         if ((r = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, s)) != cudaSuccess) return r;
+         return launch_finalize_scales(ph.dev, ph.sp, 0, s);
+       })) != cudaSuccess)
+    return e;
+  if (!last) {
+    if ((e = per_group(OKID_HLC)) != cudaSuccess) return e;                                 // Phase 5
+    if ((e = per_problem([](const ProbHost& ph, cudaStream_t s) {
+           cudaError_t r;
+           if ((r = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, s)) != cudaSuccess) return r;
+           return launch_finalize_scales(ph.dev, ph.sp, 1, s);
+         })) != cudaSuccess)
+      return e;
+    if ((e = per_group(OKID_ANTI)) != cudaSuccess) return e;                                // Phase 6
+  }
+  return per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_end(ph.dev, s); });
+}
+
 // One oscillation cycle of every problem: independent problems on the branch streams.
 cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
   cudaError_t e;
+  if (!c->groups.empty()) return enqueue_cycle_grouped(c, last);
   if (c->branch.empty()) {
     for (const ProbHost& ph : c->probs)
       if ((e = enqueue_problem_cycle(ph, last, c->stream)) != cudaSuccess) return e;
@@ -521,6 +609,59 @@ cudaError_t make_branches(chisao_ctx* c) {
     const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     c->branch_of[q] = b;
     load[b] += work(q);
+  }
+  return cudaSuccess;
+}
+
+// Grouped launches when the context holds several problems with exact gradients (none
+// on the batched-evaluator path): problems of one (kind, dp) form a group whose Phase 1,
+// HLC and anti-convergence each run as one launch covering all its samples.
+cudaError_t make_groups(chisao_ctx* c) {
+  const int nq = (int)c->probs.size();
+  if (nq < 2 || c->params.grad_mode != CHISAO_GRAD_ADJOINT) return cudaSuccess;
+  for (const ProbHost& ph : c->probs)
+    if (ph.tc) return cudaSuccess;
+  for (int q = 0; q < nq; ++q) {
+    const ProbHost& ph = c->probs[q];
+    Group* gr = nullptr;
+    for (Group& x : c->groups)
+      if (x.kind == ph.kind && x.dp == ph.dp) gr = &x;
+    if (!gr) {
+      c->groups.emplace_back();
+      gr = &c->groups.back();
+      gr->kind = ph.kind;
+      gr->dp = ph.dp;
+    }
+    gr->members.push_back(q);
+  }
+  for (Group& gr : c->groups) {
+    const size_t k = gr.members.size();
+    std::vector<int> first(k), owner;
+    std::vector<ProbDev> pd(k);
+    std::vector<StepParams> sp(k);
+    for (size_t j = 0; j < k; ++j) {
+      const ProbHost& ph = c->probs[gr.members[j]];
+      pd[j] = ph.dev;
+      sp[j] = ph.sp;
+      first[j] = (int)owner.size();
+      owner.insert(owner.end(), obj_blocks(ph.n, ph.dp), (int)j);
+    }
+    gr.blocks = (unsigned)owner.size();
+    auto up = [](size_t off) { return (off + ALIGN - 1) / ALIGN * ALIGN; };
+    const size_t o_sp = up(k * sizeof(ProbDev)), o_first = up(o_sp + k * sizeof(StepParams)),
+                 o_owner = up(o_first + k * sizeof(int)), total = up(o_owner + owner.size() * sizeof(int));
+    cudaError_t e;
+    if ((e = cudaMalloc(&gr.mem, total)) != cudaSuccess) return e;
+    char* base = static_cast<char*>(gr.mem);
+    if ((e = cudaMemcpy(base, pd.data(), k * sizeof(ProbDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(base + o_sp, sp.data(), k * sizeof(StepParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(base + o_first, first.data(), k * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(base + o_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+    gr.tab.probs = reinterpret_cast<const ProbDev*>(base);
+    gr.tab.sps = reinterpret_cast<const StepParams*>(base + o_sp);
+    gr.tab.blk_first = reinterpret_cast<const int*>(base + o_first);
+    gr.tab.blk_prob = reinterpret_cast<const int*>(base + o_owner);
   }
   return cudaSuccess;
 }
@@ -694,6 +835,7 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
     up(P.hi, box.data(), box.size() * 4);
   }
   if (st == CHISAO_OK && make_branches(c) != cudaSuccess) st = cuda_fail(c, cudaGetLastError(), "branch streams");
+  if (st == CHISAO_OK && make_groups(c) != cudaSuccess) st = cuda_fail(c, cudaGetLastError(), "grouped launch tables");
   if (st != CHISAO_OK) {
     chisao_destroy(c);
     return st;
@@ -894,6 +1036,8 @@ void chisao_destroy(chisao_ctx* c) {
   }
   for (cudaEvent_t ev : c->joined) cudaEventDestroy(ev);
   if (c->forked) cudaEventDestroy(c->forked);
+  for (Group& gr : c->groups)
+    if (gr.mem) cudaFree(gr.mem);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -127,6 +127,15 @@ struct StepParams {
   unsigned seed_lo, seed_hi;
 };
 
+// A grouped launch over several problems: block b belongs to problem q = blk_prob[b]
+// and is block b - blk_first[q] of that problem (its blocks are consecutive).
+struct GroupTab {
+  const ProbDev* probs;
+  const StepParams* sps;
+  const int* blk_prob;
+  const int* blk_first;
+};
+
 enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5,
                    OKID_REFINE = 6 };
 

@@ -300,6 +300,10 @@ static cudaError_t widths_dp(const ProbDev& P, int rows, float* w, float* cov, c
   return cudaGetLastError();
 }
 
+unsigned obj_blocks(long long n, int dp) {
+  return (unsigned)((n * (dp / VL) + NT_OBJ - 1) / NT_OBJ);
+}
+
 cudaError_t launch_widths(const ProbDev& P, int rows, float* w, float* cov, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   switch (P.dp) {

@@ -140,15 +140,18 @@ constexpr int phase1_min_blocks() {
   return (GM == GRAD_ADJOINT && KIND != OBJ_MIXTURE_FULL) ? 5 : 1;
 }
 
+// The body takes the problem, its parameters and the block's index within the
+// problem, so one problem's launch and a grouped launch over many problems share it.
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
-                                                   const int* __restrict__ rows, const int* __restrict__ nrows) {
+__device__ __forceinline__ void phase1_body(const ProbDev& P, const StepParams& S, int n_iter, int fresh,
+                                            const int* __restrict__ rows, const int* __restrict__ nrows,
+                                            unsigned blk) {
   constexpr int V = VL, LPS = DP / V;
   static_assert(V == 4, "one float4 of history per lane and slot");
   using TE = EvalT<GM>;
   __shared__ float4 hist_s[MMAX][NT_OBJ], hist_y[MMAX][NT_OBJ];
   const Grp<LPS> g;
-  const int gi = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int gi = (int)(((size_t)blk * NT_OBJ + threadIdx.x) / LPS);
   const bool act = rows ? gi < *nrows : gi < P.n;
   const int i = rows ? (act ? rows[gi] : 0) : gi;
   EvalCount ec;
@@ -323,6 +326,20 @@ __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase
   block_add_u64<NT_OBJ>(fails, &P.cnt->ls_fail);
 }
 
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
+                                                   const int* __restrict__ rows, const int* __restrict__ nrows) {
+  phase1_body<KIND, DP, GM>(P, S, n_iter, fresh, rows, nrows, blockIdx.x);
+}
+
+// Phase 1 of every problem of a group in one launch (n_conv iterations each, fresh gradient).
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1_grp(GroupTab T) {
+  const int q = T.blk_prob[blockIdx.x];
+  const StepParams& S = T.sps[q];
+  phase1_body<KIND, DP, GM>(T.probs[q], S, S.n_conv, 1, nullptr, nullptr, blockIdx.x - (unsigned)T.blk_first[q]);
+}
+
 // Direction only (test hook): p = -H grad F written into g.
 template <int DP>
 __global__ void __launch_bounds__(NT_OBJ) k_direction(ProbDev P) {
@@ -405,10 +422,10 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
 // unfrozen samples; z_k from the HLC Philox stream (row = sample, step = cloud
 // step, k = perturbation).  History is cleared (the sample moved).
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
+__device__ __forceinline__ void hlc_body(const ProbDev& P, const StepParams& S, unsigned blk) {
   constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
-  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int i = (int)(((size_t)blk * NT_OBJ + threadIdx.x) / LPS);
   EvalCount ec;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
     const int j0 = V * g.l;
@@ -472,15 +489,26 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
   block_add_u64<NT_OBJ>(ec.grads, &P.cnt->grads);
 }
 
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_hlc(ProbDev P, StepParams S) {
+  hlc_body<KIND, DP, GM>(P, S, blockIdx.x);
+}
+
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_hlc_grp(GroupTab T) {
+  const int q = T.blk_prob[blockIdx.x];
+  hlc_body<KIND, DP, GM>(T.probs[q], T.sps[q], blockIdx.x - (unsigned)T.blk_first[q]);
+}
+
 // ------------------------------------------------------------------ Phase 6
 // n_anti momentum steps v <- mu v - alpha grad f(x), x <- clip(x + v), v = 0
 // on coordinates the projection moved; v_0 = 0; the first gradient is the one
 // the scale pass stored.  History is cleared.
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_OBJ) k_anti(ProbDev P, StepParams S) {
+__device__ __forceinline__ void anti_body(const ProbDev& P, const StepParams& S, unsigned blk) {
   constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
-  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int i = (int)(((size_t)blk * NT_OBJ + threadIdx.x) / LPS);
   EvalCount ec;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
     const int j0 = V * g.l;
@@ -509,6 +537,17 @@ __global__ void __launch_bounds__(NT_OBJ) k_anti(ProbDev P, StepParams S) {
   }
   block_add_u64<NT_OBJ>(ec.evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(ec.grads, &P.cnt->grads);
+}
+
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_anti(ProbDev P, StepParams S) {
+  anti_body<KIND, DP, GM>(P, S, blockIdx.x);
+}
+
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_anti_grp(GroupTab T) {
+  const int q = T.blk_prob[blockIdx.x];
+  anti_body<KIND, DP, GM>(T.probs[q], T.sps[q], blockIdx.x - (unsigned)T.blk_first[q]);
 }
 
 // ------------------------------------------------------------------ plain evaluation
@@ -599,6 +638,32 @@ cudaError_t launch_obj(int which, int gm, const ProbDev& P, const StepParams& S,
     case 16: return launch_obj_dp<KIND, 16>(which, gm, P, S, arg, ea, st);
     case 32: return launch_obj_dp<KIND, 32>(which, gm, P, S, arg, ea, st);
     case 64: return launch_obj_dp<KIND, 64>(which, gm, P, S, arg, ea, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Grouped launches (exact gradients): one launch runs Phase 1, 5 or 6 of every problem
+// of a group that shares the objective kind and padded dimension.
+template <int KIND, int DP>
+cudaError_t launch_grp_dp(int which, const GroupTab& T, unsigned blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  switch (which) {
+    case OKID_PHASE1: k_phase1_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
+    case OKID_HLC: k_hlc_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
+    case OKID_ANTI: k_anti_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_grp(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st) {
+  switch (dp) {
+    case 4: return launch_grp_dp<KIND, 4>(which, T, blocks, st);
+    case 8: return launch_grp_dp<KIND, 8>(which, T, blocks, st);
+    case 16: return launch_grp_dp<KIND, 16>(which, T, blocks, st);
+    case 32: return launch_grp_dp<KIND, 32>(which, T, blocks, st);
+    case 64: return launch_grp_dp<KIND, 64>(which, T, blocks, st);
   }
   return cudaErrorInvalidValue;
 }

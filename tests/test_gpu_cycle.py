@@ -128,12 +128,21 @@ def test_batched_problems_in_one_context():
     model.close()
 
 
-def test_batched_problems_match_separate_contexts():
-    """Problems of one context are independent (the cycle forks them onto branch
-    streams): problem q's state after two cycles is bit-identical in a context of
-    six problems and in one of the first q + 1 (same problem index, hence the same
-    Philox streams; different branch assignment), with and without graph capture."""
-    probs = I.batched512(n_problems=6, n_scale=0.1, seed=3)
+def _mixed_kinds():
+    return [I.small_quadratic(7, 900, seed=1), I.small_mixture(5, 4, 700, seed=2),
+            I.benchmark("rastrigin", 4, 600, seed=3), I.small_full_mixture(3, 3, 500, seed=4),
+            I.small_mixture(6, 3, 300, seed=5), I.small_quadratic(8, 200, seed=6)]
+
+
+@pytest.mark.parametrize("case", ["batched", "mixed_kinds"])
+def test_batched_problems_match_separate_contexts(case):
+    """Problems of one context are independent: with exact gradients the context runs
+    Phases 1, 5 and 6 as one grouped launch per (objective kind, padded dimension) and
+    the rest per problem on branch streams.  Problem q's state after two cycles is
+    bit-identical in a context of six problems and in one of the first q + 1 (same
+    problem index, hence the same Philox streams; a single problem runs ungrouped),
+    with and without graph capture."""
+    probs = I.batched512(n_problems=6, n_scale=0.1, seed=3) if case == "batched" else _mixed_kinds()
     P = M.Params(n_osc=4, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=2)
     U.ensure_built()
     fields = (CH.FIELD_X, CH.FIELD_F, CH.FIELD_STUCK)
