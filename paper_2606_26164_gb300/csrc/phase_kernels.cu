@@ -607,9 +607,10 @@ __global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParam
 
 // ------------------------------------------------------------ modes gather
 __global__ void __launch_bounds__(NT_LIN) k_gather_modes(ProbDev P, float* xo, float* fo) {
-  const int Sv = P.cnt->n_surv;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Sv * P.d; t += gridDim.x * blockDim.x) {
-    const int r = t / P.d, j = t % P.d;
+  const long long total = (long long)P.cnt->n_surv * P.d;     // up to 2^27 x 64: 64-bit
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / P.d), j = (int)(t % P.d);
     const int i = P.l_surv[r];
     xo[t] = P.x[(size_t)i * P.dp + j];
     if (j == 0) fo[r] = P.f[i];

@@ -283,3 +283,62 @@ def test_two_mode_d6_noise_levels(noise):
         frac, worst, _ = MD.recovery(fx, mx, negH)
         assert frac == 1.0 and fx.shape[0] == 2, (seed, frac, fx.shape)
         model.close()
+
+
+def test_large_population_quadratic():
+    """N = 2^22 samples at d = 64 (the history holds 2.7e9 floats, past 32-bit
+    indexing): one Phase-1 iteration on sampled rows, the first and the last
+    included, matches the oracle's on the same rows, and a whole cycle runs."""
+    n = 1 << 22
+    prob = I.quadratic_d64(n=n, seed=1)
+    P = M.Params(n_osc=1000, m=10, eps_grad=0.05, grad_mode=M.GRAD_ADJOINT, seed=3)
+    model = U.open_ctx(prob, P)
+    model.run_phase(0, CH.PHASE_LBFGS, 1)
+    x1 = model.get(0, CH.FIELD_X)[:, :64]
+    rows = np.concatenate([[0, 1, n // 2], np.random.default_rng(1).choice(n, 40, replace=False), [n - 2, n - 1]])
+    sub = I.Problem(64, rows.size, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad, prob.sigma_mode)
+    ref = M.new_state(prob.x0[rows].astype(np.float64), P.m)
+    M.lbfgs_iterations(sub, ref, P, 1)
+    x0 = prob.x0[rows].astype(np.float64)
+    move = np.abs(ref.x - x0).max(axis=1)
+    err = np.abs(x1[rows].astype(np.float64) - ref.x).max(axis=1)
+    ok = err <= 1e-4 * move + 1e-6 * np.abs(x0).max(axis=1)
+    # a binary32-vs-FP64 tie of the Armijo test takes the neighbouring trial (a power-of-two step)
+    assert (~ok).sum() <= 2, (err / move)[~ok]
+    for i in np.flatnonzero(~ok):
+        dg, dr = x1[rows[i]] - x0[i], ref.x[i] - x0[i]
+        j = np.argmax(np.abs(dr))
+        ratio = abs(dg[j] / dr[j])
+        assert abs(np.log2(ratio) - round(np.log2(ratio))) < 1e-3
+    hlen = model.get(0, CH.FIELD_HLEN)
+    np.testing.assert_array_equal(hlen[rows][ok], ref.hlen[ok])
+    model.step()
+    c = model.counters(0)
+    assert c["cycles"] == 1 and c["evals"] > 2 * n
+    model.close()
+
+
+@pytest.mark.parametrize("d,n", [(1, 1), (1, 37), (3, 1), (64, 1), (2, 2)])
+def test_degenerate_sizes(d, n):
+    """One coordinate, one sample, two samples: one Phase-1 iteration matches the
+    oracle, whole cycles run, and the returned modes and widths are consistent."""
+    prob = I.small_mixture(d, 2, n, seed=40 + d)
+    P = M.Params(n_osc=3, m=5, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=1)
+    model = U.open_ctx(prob, P)
+    model.run_phase(0, CH.PHASE_LBFGS, 1)
+    got = U.read_state(model, prob, P.m)
+    ref = M.new_state(prob.x0.astype(np.float64), P.m)
+    M.lbfgs_iterations(prob, ref, P, 1)
+    move = np.abs(ref.x - prob.x0).max(axis=1)
+    err = np.abs(got.x - ref.x).max(axis=1)
+    assert np.all(err <= 1e-4 * move + 1e-6 * (1.0 + np.abs(prob.x0).max(axis=1))), (err, move)
+    model.close()
+    model = U.open_ctx(prob, P)
+    for _ in range(P.n_osc):
+        model.step()
+    fx, ff = model.modes(0)
+    w, H = model.widths(0, cov=True)
+    assert fx.shape == (w.shape[0], d) and H.shape == (w.shape[0], d, d)
+    assert np.all(w > 0) and np.all(np.isfinite(H))
+    assert model.counters(0)["cycles"] == P.n_osc
+    model.close()
