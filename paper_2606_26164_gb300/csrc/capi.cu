@@ -57,7 +57,8 @@ struct Group {
   int kind = 0, dp = 0;
   std::vector<int> members;          // problem indices
   unsigned blocks = 0;               // blocks of one per-sample launch over all members
-  GroupTab tab{};                    // device tables (one allocation, `mem`)
+  unsigned blocks_sc = 0;            // blocks of the grouped scale pass
+  GroupTab tab{}, tab_sc{};          // device tables (one allocation, `mem`)
   void* mem = nullptr;
 };
 
@@ -232,6 +233,7 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
   size_t slots = 1;
   while (slots < 2 * n) slots <<= 1;
   P.hkey = b.take<unsigned long long>(slots);
+  P.hbest = b.take<unsigned long long>(slots);
   P.hhead = b.take<int>(slots);
   P.hnext = b.take<int>(n);
   P.hmask = (int)(slots - 1);
@@ -487,12 +489,26 @@ cudaError_t enqueue_problem_cycle(const ProbHost& ph, bool last, cudaStream_t st
 }
 
 cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st) {
+  const GroupTab& T = which == OKID_SCALES ? gr.tab_sc : gr.tab;
+  const unsigned blocks = which == OKID_SCALES ? gr.blocks_sc : gr.blocks;
   switch (gr.kind) {
-    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, gr.tab, gr.blocks, st);
-    case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, gr.tab, gr.blocks, st);
-    case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, gr.tab, gr.blocks, st);
-    default: return launch_grp_bench(which, gr.dp, gr.tab, gr.blocks, st);
+    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, T, blocks, st);
+    case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, T, blocks, st);
+    case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, T, blocks, st);
+    default: return launch_grp_bench(which, gr.dp, T, blocks, st);
   }
+}
+
+// Phases 5 and 6 of a group: scale pass, finalization, HLC, scale pass, finalization, anti.
+cudaError_t enqueue_explore_group(const Group& gr, cudaStream_t st) {
+  cudaError_t e;
+  const int k = (int)gr.members.size();
+  if ((e = launch_grouped(OKID_SCALES, gr, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_grp(gr.tab_sc, k, gr.dp, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_grouped(OKID_HLC, gr, st)) != cudaSuccess) return e;
+  if ((e = launch_grouped(OKID_SCALES, gr, st)) != cudaSuccess) return e;
+  if ((e = launch_finalize_grp(gr.tab_sc, k, gr.dp, 1, st)) != cudaSuccess) return e;
+  return launch_grouped(OKID_ANTI, gr, st);
 }
 
 // Fork the branch streams from the context stream, run f(branch index) on each, join back.
@@ -511,8 +527,8 @@ cudaError_t forked(chisao_ctx* c, F&& f) {
 }
 
 // One cycle with grouped launches: the per-problem steps (release, freeze, dedup,
-// reseed, the scale passes, cycle end) run on the problems' branch streams, and each of
-// Phase 1, HLC and anti-convergence runs as one launch per group (the groups on
+// reseed, cycle end) run on the problems' branch streams; Phase 1, and then the scale
+// passes with Phases 5 and 6, run as one chain of launches per group (the groups on
 // separate branches), with joins in between, since every phase needs the previous one
 // of the same problem.
 cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
@@ -525,10 +541,10 @@ cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
       return cudaSuccess;
     });
   };
-  auto per_group = [&](int which) {
+  auto per_group = [&](auto&& body) {
     return forked(c, [&]() -> cudaError_t {
       for (size_t k = 0; k < c->groups.size(); ++k) {
-        const cudaError_t e = launch_grouped(which, c->groups[k], c->branch[k % c->branch.size()]);
+        const cudaError_t e = body(c->groups[k], c->branch[k % c->branch.size()]);
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
@@ -538,27 +554,17 @@ cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
   if ((e = per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_begin(ph.dev, s); })) !=
       cudaSuccess)
     return e;
-  if ((e = per_group(OKID_PHASE1)) != cudaSuccess) return e;                              // Phase 1
-  if ((e = per_problem([last](const ProbHost& ph, cudaStream_t s) {                        // Phases 2-4, scales
+  if ((e = per_group([](const Group& gr, cudaStream_t s) { return launch_grouped(OKID_PHASE1, gr, s); })) !=
+      cudaSuccess)
+    return e;                                                                               // Phase 1
+  if ((e = per_problem([last](const ProbHost& ph, cudaStream_t s) {                        // Phases 2-4
          cudaError_t r;
          if ((r = launch_freeze(ph.dev, ph.sp, s)) != cudaSuccess) return r;
          if ((r = launch_dedup(ph.dev, ph.sp, s)) != cudaSuccess) return r;
-         if (last) return cudaSuccess;
-         if ((r = launch_reseed(ph.dev, ph.sp, s)) != cudaSuccess) return r;
-         if ((r = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, s)) != cudaSuccess) return r;
-         return launch_finalize_scales(ph.dev, ph.sp, 0, s);
+         return last ? cudaSuccess : launch_reseed(ph.dev, ph.sp, s);
        })) != cudaSuccess)
     return e;
-  if (!last) {
-    if ((e = per_group(OKID_HLC)) != cudaSuccess) return e;                                 // Phase 5
-    if ((e = per_problem([](const ProbHost& ph, cudaStream_t s) {
-           cudaError_t r;
-           if ((r = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, s)) != cudaSuccess) return r;
-           return launch_finalize_scales(ph.dev, ph.sp, 1, s);
-         })) != cudaSuccess)
-      return e;
-    if ((e = per_group(OKID_ANTI)) != cudaSuccess) return e;                                // Phase 6
-  }
+  if (!last && (e = per_group(enqueue_explore_group)) != cudaSuccess) return e;            // Phases 5-6
   return per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_end(ph.dev, s); });
 }
 
@@ -636,7 +642,9 @@ cudaError_t make_groups(chisao_ctx* c) {
   }
   for (Group& gr : c->groups) {
     const size_t k = gr.members.size();
-    std::vector<int> first(k), owner;
+    // two block maps over the same problem tables: NT_OBJ-thread blocks over the samples, and
+    // each problem's scale-pass grid
+    std::vector<int> first(k), count(k), owner, first_sc(k), count_sc(k), owner_sc;
     std::vector<ProbDev> pd(k);
     std::vector<StepParams> sp(k);
     for (size_t j = 0; j < k; ++j) {
@@ -644,24 +652,40 @@ cudaError_t make_groups(chisao_ctx* c) {
       pd[j] = ph.dev;
       sp[j] = ph.sp;
       first[j] = (int)owner.size();
-      owner.insert(owner.end(), obj_blocks(ph.n, ph.dp), (int)j);
+      count[j] = (int)obj_blocks(ph.n, ph.dp);
+      owner.insert(owner.end(), count[j], (int)j);
+      first_sc[j] = (int)owner_sc.size();
+      count_sc[j] = scale_blocks(ph.dev);
+      owner_sc.insert(owner_sc.end(), count_sc[j], (int)j);
     }
     gr.blocks = (unsigned)owner.size();
+    gr.blocks_sc = (unsigned)owner_sc.size();
     auto up = [](size_t off) { return (off + ALIGN - 1) / ALIGN * ALIGN; };
-    const size_t o_sp = up(k * sizeof(ProbDev)), o_first = up(o_sp + k * sizeof(StepParams)),
-                 o_owner = up(o_first + k * sizeof(int)), total = up(o_owner + owner.size() * sizeof(int));
+    struct Part { const void* src; size_t bytes; size_t off; };
+    std::vector<Part> parts = {{pd.data(), k * sizeof(ProbDev), 0}, {sp.data(), k * sizeof(StepParams), 0},
+                               {first.data(), k * sizeof(int), 0}, {count.data(), k * sizeof(int), 0},
+                               {owner.data(), owner.size() * sizeof(int), 0},
+                               {first_sc.data(), k * sizeof(int), 0}, {count_sc.data(), k * sizeof(int), 0},
+                               {owner_sc.data(), owner_sc.size() * sizeof(int), 0}};
+    size_t total = 0;
+    for (Part& p : parts) {
+      p.off = total;
+      total = up(total + p.bytes);
+    }
     cudaError_t e;
     if ((e = cudaMalloc(&gr.mem, total)) != cudaSuccess) return e;
     char* base = static_cast<char*>(gr.mem);
-    if ((e = cudaMemcpy(base, pd.data(), k * sizeof(ProbDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(base + o_sp, sp.data(), k * sizeof(StepParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(base + o_first, first.data(), k * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(base + o_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
-      return e;
-    gr.tab.probs = reinterpret_cast<const ProbDev*>(base);
-    gr.tab.sps = reinterpret_cast<const StepParams*>(base + o_sp);
-    gr.tab.blk_first = reinterpret_cast<const int*>(base + o_first);
-    gr.tab.blk_prob = reinterpret_cast<const int*>(base + o_owner);
+    for (const Part& p : parts)
+      if ((e = cudaMemcpy(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    auto at = [&](int t) { return reinterpret_cast<const int*>(base + parts[t].off); };
+    gr.tab.probs = gr.tab_sc.probs = reinterpret_cast<const ProbDev*>(base + parts[0].off);
+    gr.tab.sps = gr.tab_sc.sps = reinterpret_cast<const StepParams*>(base + parts[1].off);
+    gr.tab.blk_first = at(2);
+    gr.tab.blk_count = at(3);
+    gr.tab.blk_prob = at(4);
+    gr.tab_sc.blk_first = at(5);
+    gr.tab_sc.blk_count = at(6);
+    gr.tab_sc.blk_prob = at(7);
   }
   return cudaSuccess;
 }

@@ -112,6 +112,7 @@ struct ProbDev {
   // Phase 3 spatial hash: open addressing over 2^k >= 2 n slots, one list of stuck
   // samples per cell key (head per slot, next per stuck-list position)
   unsigned long long* hkey;
+  unsigned long long* hbest;    // per slot: the cell's top-ranked member, (f bits << 32) | ~index
   int* hhead;
   int* hnext;
   int hmask;
@@ -134,6 +135,7 @@ struct GroupTab {
   const StepParams* sps;
   const int* blk_prob;
   const int* blk_first;
+  const int* blk_count;         // blocks of problem q in this launch
 };
 
 enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5,

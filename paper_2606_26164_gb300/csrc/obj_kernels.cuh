@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_direction(ProbDev P) {
 // (sum x_j, sum x_j^2 per coordinate, sum |g|^2, count), accumulated in
 // double-single and reduced in a fixed order so the result is deterministic.
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
+__device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& S, unsigned blk, unsigned nblk) {
   constexpr int V = VL, LPS = DP / V;
   constexpr int GPB = NT_SCALES / LPS;             // groups per block
   constexpr int W = 2 * DP + 2;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
 #pragma unroll
   for (int v = 0; v < V; ++v) sxh[v] = sxl[v] = sqh[v] = sql[v] = 0.f;
   int cnt = 0;
-  for (int i = blockIdx.x * GPB + grp; i < P.n; i += gridDim.x * GPB) {
+  for (int i = (int)blk * GPB + grp; i < P.n; i += (int)nblk * GPB) {
     if (bit_of(P.stuck, i)) continue;
     float x[V], a[V];
     ld_vec<V>(P.x + (size_t)i * DP + j0, x);
@@ -410,11 +410,23 @@ __global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
   for (int t = threadIdx.x; t < W; t += blockDim.x) {
     float h = 0.f, l = 0.f;
     for (int q = 0; q < GPB; ++q) ff_add(h, l, buf[q][t].x, buf[q][t].y);
-    P.partials[(size_t)blockIdx.x * W + t] = make_float2(h, l);
+    P.partials[(size_t)blk * W + t] = make_float2(h, l);
   }
   if (g.l != 0) ec.evals = ec.grads = 0;
   block_add_u64<NT_SCALES>(ec.evals, &P.cnt->evals);
   block_add_u64<NT_SCALES>(ec.grads, &P.cnt->grads);
+}
+
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
+  scales_body<KIND, DP, GM>(P, S, blockIdx.x, gridDim.x);
+}
+
+// The scale pass of every problem of a group (its own partial-sum grid each).
+template <int KIND, int DP, int GM>
+__global__ void __launch_bounds__(NT_SCALES) k_scales_grp(GroupTab T) {
+  const int q = T.blk_prob[blockIdx.x];
+  scales_body<KIND, DP, GM>(T.probs[q], T.sps[q], blockIdx.x - (unsigned)T.blk_first[q], (unsigned)T.blk_count[q]);
 }
 
 // ------------------------------------------------------------------ Phase 5
@@ -642,8 +654,10 @@ cudaError_t launch_obj(int which, int gm, const ProbDev& P, const StepParams& S,
   return cudaErrorInvalidValue;
 }
 
-// Grouped launches (exact gradients): one launch runs Phase 1, 5 or 6 of every problem
-// of a group that shares the objective kind and padded dimension.
+// Grouped launches (exact gradients): one launch runs Phase 1, the scale pass, Phase 5 or
+// Phase 6 of every problem of a group that shares the objective kind and padded dimension
+// (T maps the launch's blocks to problems: NT_OBJ-thread blocks over the samples, or the
+// problems' scale-pass grids for OKID_SCALES).
 template <int KIND, int DP>
 cudaError_t launch_grp_dp(int which, const GroupTab& T, unsigned blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
@@ -651,6 +665,7 @@ cudaError_t launch_grp_dp(int which, const GroupTab& T, unsigned blocks, cudaStr
     case OKID_PHASE1: k_phase1_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
     case OKID_HLC: k_hlc_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
     case OKID_ANTI: k_anti_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
+    case OKID_SCALES: k_scales_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_SCALES, 0, st>>>(T); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

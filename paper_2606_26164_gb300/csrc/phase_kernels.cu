@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(NT_LIN) k_hash_clear(ProbDev P) {
   if (P.cnt->n_stuck0 == 0) return;
   for (int s = t; s <= P.hmask; s += gridDim.x * blockDim.x) {
     P.hkey[s] = HASH_EMPTY;
+    P.hbest[s] = 0ull;
     P.hhead[s] = -1;
   }
   if (t < P.dp) {
@@ -225,13 +226,19 @@ __device__ __forceinline__ void sample_cells(const ProbDev& P, int i, double h, 
   }
 }
 
-// file every stuck sample under its cell key
+// Rank key of sample i: larger for higher f, then for lower index (nonzero for any f).
+__device__ __forceinline__ unsigned long long rank_key(float f, int i) {
+  return ((unsigned long long)ordered_bits(f) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
+}
+
+// file every stuck sample under its cell key; each cell also keeps its top-ranked member
 __global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S) {
   const int jj = blockIdx.x * blockDim.x + threadIdx.x;
   if (jj >= P.cnt->n_stuck0) return;
   const double h = (double)S.eps_dup * (1.0 + 1e-6);
   long long c[3];
-  sample_cells(P, P.l_stuck[jj], h, c);
+  const int j = P.l_stuck[jj];
+  sample_cells(P, j, h, c);
   const unsigned long long key = cell_key(c[0], c[1], c[2]);
   unsigned slot = (unsigned)key & (unsigned)P.hmask;
   for (int probe = 0; probe <= P.hmask; ++probe) {     // the table has at least 2 n slots: a free one exists
@@ -240,6 +247,7 @@ __global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S)
     slot = (slot + 1) & (unsigned)P.hmask;
   }
   P.hnext[jj] = atomicExch(&P.hhead[slot], jj);
+  atomicMax(&P.hbest[slot], rank_key(P.f[j], j));
 }
 
 template <int DP>
@@ -267,14 +275,26 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
         const unsigned long long key = cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2);
         unsigned slot = (unsigned)key & (unsigned)P.hmask;
         int head = -1;
+        unsigned long long best = 0ull;
         for (int probe = 0; probe <= P.hmask; ++probe) {
           const unsigned long long k = P.hkey[slot];
           if (k == key) {
             head = P.hhead[slot];
+            best = P.hbest[slot];
             break;
           }
           if (k == HASH_EMPTY) break;
           slot = (slot + 1) & (unsigned)P.hmask;
+        }
+        // the cell's top-ranked member first: in a cluster of duplicates it removes every
+        // other member at once (the same exact test; the list scan below decides otherwise)
+        if (best != 0ull) {
+          const int i = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFull));
+          const float fi = P.f[i];
+          if (i != j && (fi > fj || (fi == fj && i < j))) {
+            const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
+            if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) rem = true;
+          }
         }
         for (int ii = head; ii >= 0 && !rem; ii = P.hnext[ii]) {
           const int i = P.l_stuck[ii];
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
 // then the 8 row-group sums are added in order q = 0..7 -- a fixed order, so
 // the result does not depend on timing -- and converted to FP64.
 constexpr int FIN_NT = 1024, FIN_RG = 8, FIN_COLS = FIN_NT / FIN_RG;
-__global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
+__device__ __forceinline__ void finalize_body(const ProbDev& P, const StepParams& S, int nblocks, int which) {
   const int W = 2 * P.dp + 2;
   extern __shared__ double tot[];                   // [W]
   __shared__ float2 part[FIN_RG][FIN_COLS];
@@ -603,6 +623,16 @@ __global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParam
       c->alpha_anti = (float)alpha;
     }
   }
+}
+
+__global__ void __launch_bounds__(FIN_NT) k_finalize_scales(ProbDev P, StepParams S, int nblocks, int which) {
+  finalize_body(P, S, nblocks, which);
+}
+
+// One block per problem of a group; T is the group's scale-pass table.
+__global__ void __launch_bounds__(FIN_NT) k_finalize_grp(GroupTab T, int which) {
+  const int q = blockIdx.x;
+  finalize_body(T.probs[q], T.sps[q], T.blk_count[q], which);
 }
 
 // ------------------------------------------------------------ modes gather
@@ -719,6 +749,11 @@ int scale_blocks(const ProbDev& P) {
   if (nb > P.max_part_blocks) nb = P.max_part_blocks;
   if (nb < 1) nb = 1;
   return (int)nb;
+}
+
+cudaError_t launch_finalize_grp(const GroupTab& T, int members, int dp, int which, cudaStream_t st) {
+  k_finalize_grp<<<(unsigned)members, FIN_NT, sizeof(double) * (2 * dp + 2), st>>>(T, which);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_scales(const ProbDev& P, const StepParams& S, int which, cudaStream_t st) {
