@@ -268,42 +268,45 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
   const int na = (P.haxes[0] >= 0) + (P.haxes[1] >= 0) + (P.haxes[2] >= 0);
   int span[3];
   for (int r = 0; r < 3; ++r) span[r] = r < na ? 1 : 0;
+  // the slot of a cell key, or -1 when no stuck sample is filed under it
+  auto find_slot = [&](unsigned long long key) -> int {
+    unsigned slot = (unsigned)key & (unsigned)P.hmask;
+    for (int probe = 0; probe <= P.hmask; ++probe) {
+      const unsigned long long k = P.hkey[slot];
+      if (k == key) return (int)slot;
+      if (k == HASH_EMPTY) return -1;
+      slot = (slot + 1) & (unsigned)P.hmask;
+    }
+    return -1;
+  };
+  // does sample i rank above j and lie within eps_dup of it (the binary32 test of Eq. 4)?
+  auto removes = [&](int i) -> bool {
+    if (i == j) return false;
+    const float fi = P.f[i];
+    if (!(fi > fj || (fi == fj && i < j))) return false;
+    const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
+    return g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps);
+  };
   bool rem = false;
+  // pass 1: the top-ranked member of each neighbouring cell.  In a cluster of duplicates
+  // the cluster's top is within eps_dup of most members and is the top of its own cell,
+  // so most members are decided here in 27 tests.
   for (int d0 = -span[0]; d0 <= span[0] && !rem; ++d0)
     for (int d1 = -span[1]; d1 <= span[1] && !rem; ++d1)
       for (int d2 = -span[2]; d2 <= span[2] && !rem; ++d2) {
-        const unsigned long long key = cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2);
-        unsigned slot = (unsigned)key & (unsigned)P.hmask;
-        int head = -1;
-        unsigned long long best = 0ull;
-        for (int probe = 0; probe <= P.hmask; ++probe) {
-          const unsigned long long k = P.hkey[slot];
-          if (k == key) {
-            head = P.hhead[slot];
-            best = P.hbest[slot];
-            break;
-          }
-          if (k == HASH_EMPTY) break;
-          slot = (slot + 1) & (unsigned)P.hmask;
-        }
-        // the cell's top-ranked member first: in a cluster of duplicates it removes every
-        // other member at once (the same exact test; the list scan below decides otherwise)
-        if (best != 0ull) {
-          const int i = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFull));
-          const float fi = P.f[i];
-          if (i != j && (fi > fj || (fi == fj && i < j))) {
-            const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
-            if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) rem = true;
-          }
-        }
-        for (int ii = head; ii >= 0 && !rem; ii = P.hnext[ii]) {
-          const int i = P.l_stuck[ii];
-          if (i == j) continue;
-          const float fi = P.f[i];
-          if (!(fi > fj || (fi == fj && i < j))) continue;
-          const float2 xi = *reinterpret_cast<const float2*>(P.x + (size_t)i * DP + c0);
-          if (g.all(fabsf(xi.x - xj.x) < eps && fabsf(xi.y - xj.y) < eps)) rem = true;
-        }
+        const int slot = find_slot(cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2));
+        if (slot < 0) continue;
+        const unsigned long long best = P.hbest[slot];
+        if (best != 0ull && removes((int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFull)))) rem = true;
+      }
+  // pass 2: every member of the neighbouring cells (what pass 1 did not decide)
+  for (int d0 = -span[0]; d0 <= span[0] && !rem; ++d0)
+    for (int d1 = -span[1]; d1 <= span[1] && !rem; ++d1)
+      for (int d2 = -span[2]; d2 <= span[2] && !rem; ++d2) {
+        const int slot = find_slot(cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2));
+        if (slot < 0) continue;
+        for (int ii = P.hhead[slot]; ii >= 0 && !rem; ii = P.hnext[ii])
+          if (removes(P.l_stuck[ii])) rem = true;
       }
   if (rem && g.l == 0) atomicOr(&P.removed[j >> 5], 1u << (j & 31));
 }

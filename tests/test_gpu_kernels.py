@@ -343,6 +343,32 @@ def test_dedup_hash_geometry(case):
     model.close()
 
 
+@pytest.mark.parametrize("d,N", [(2, 1 << 20), (16, 1 << 18)])
+def test_dedup_dense_cluster(d, N):
+    """Every stuck sample converged into one cluster (offsets below eps/2 in every
+    coordinate, f nearly tied): only the top-ranked sample (highest f, then lowest
+    index) survives.  The cluster's top decides each member in one test, so this
+    runs in a single short pass rather than a scan of the cluster per sample."""
+    rng = np.random.default_rng(d)
+    prob = I.small_mixture(d, 2, N, seed=13)
+    P = M.Params(eps_dup=1e-3)
+    model = U.open_ctx(prob, P)
+    x = (rng.uniform(-1, 1, (1, d)) + rng.uniform(-4.9e-4, 4.9e-4, (N, d))).astype(np.float32)
+    f = (-1.0 + np.round(rng.normal(0, 1e-6, N), 7)).astype(np.float32)      # many exact ties
+    dp, mm = model.layout(0)
+    xp = np.zeros((N, dp), np.float32)
+    xp[:, :d] = x
+    model.set(0, CH.FIELD_X, xp)
+    model.set(0, CH.FIELD_F, f)
+    model.set(0, CH.FIELD_STUCK, CH.pack_bits(np.ones(N, bool)))
+    model.set(0, CH.FIELD_REMOVED, CH.pack_bits(np.zeros(N, bool)))
+    model.run_phase(0, CH.PHASE_DEDUP)
+    rem = CH.unpack_bits(model.get(0, CH.FIELD_REMOVED), N)
+    top = np.lexsort((np.arange(N), -f.astype(np.float64)))[0]             # f desc, index asc
+    assert (~rem).sum() == 1 and not rem[top]
+    model.close()
+
+
 def test_dedup_edge_cases():
     prob = I.small_mixture(3, 2, 33, seed=11)
     P = M.Params(eps_dup=1e-3)
