@@ -226,9 +226,11 @@ __device__ __forceinline__ void sample_cells(const ProbDev& P, int i, double h, 
   }
 }
 
-// Rank key of sample i: larger for higher f, then for lower index (nonzero for any f).
+// Rank key of sample i: larger for higher f, then for lower index (nonzero for any f);
+// -0 is taken as +0 so that the key orders exactly as the (f desc, index asc) rank.
 __device__ __forceinline__ unsigned long long rank_key(float f, int i) {
-  return ((unsigned long long)ordered_bits(f) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
+  return ((unsigned long long)ordered_bits(f == 0.f ? 0.f : f) << 32) |
+         (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
 }
 
 // file every stuck sample under its cell key; each cell also keeps its top-ranked member
@@ -299,12 +301,14 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
         const unsigned long long best = P.hbest[slot];
         if (best != 0ull && removes((int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFull)))) rem = true;
       }
-  // pass 2: every member of the neighbouring cells (what pass 1 did not decide)
+  // pass 2: the members of the neighbouring cells whose top ranks above j (a cell whose top
+  // is j or ranks below it holds nobody above j), so a cluster's top scans no list at all
+  const unsigned long long kj = rank_key(fj, j);
   for (int d0 = -span[0]; d0 <= span[0] && !rem; ++d0)
     for (int d1 = -span[1]; d1 <= span[1] && !rem; ++d1)
       for (int d2 = -span[2]; d2 <= span[2] && !rem; ++d2) {
         const int slot = find_slot(cell_key(cj[0] + d0, cj[1] + d1, cj[2] + d2));
-        if (slot < 0) continue;
+        if (slot < 0 || P.hbest[slot] <= kj) continue;
         for (int ii = P.hhead[slot]; ii >= 0 && !rem; ii = P.hnext[ii])
           if (removes(P.l_stuck[ii])) rem = true;
       }
