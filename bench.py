@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3, help="cycles of the 512-problem leg")
     ap.add_argument("--bench-fn-steps", type=int, default=3, help="cycles of each benchmark-function leg")
     ap.add_argument("--noise-trials", type=int, default=10, help="trials per level of the noise-table leg")
+    ap.add_argument("--leg", default=None, choices=["batched512", "noise_d6", "benchmark_functions"],
+                    help="run only this leg (one JSON line; for profiling one workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -412,6 +414,12 @@ def main():
     barrier(world)
     from paper_2606_26164_gb300 import chisao as CH
 
+    if args.leg:
+        legs = {"batched512": lambda: batched_leg(CH, args.batched_steps),
+                "noise_d6": lambda: noise_table_leg(CH, args.noise_trials),
+                "benchmark_functions": lambda: benchmark_functions_leg(CH, args.bench_fn_steps, 2)}
+        print(json.dumps({"leg": args.leg, **legs[args.leg]()}))
+        return
     prob = make_problem(args.workload, seed=rank)
     if args.n:
         from paper_2606_26164_gb300 import inputs as I
