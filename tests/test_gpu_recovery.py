@@ -1,0 +1,135 @@
+"""Mode recovery on the five workloads at their benchmark sizes: the fraction of
+significant modes (Eq. 1; Newton's method from every component mean in FP64)
+that some returned point matches within 1e-3 of the mode's local sigma, the
+worst such error, and the returned points that match none of them, split into
+other local maxima (Eq. 3 gates on the population's own f_max, so a population
+that has not found the global maximum returns lower maxima too, and Newton from
+the means need not reach every maximum of an overlapping mixture) and points
+that are not local maxima at all (errors).
+
+Each case prints one RECOVERY line (run with -s to see them); the assertions are
+floors below the measured values, and no returned point may be a non-maximum."""
+import numpy as np
+import pytest
+
+import gpu_util as U
+from oracle import method as M
+from oracle import modes as MD
+from oracle import objectives as OB
+from paper_2606_26164_gb300 import chisao as CH
+from paper_2606_26164_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _is_local_max(prob, x):
+    xs, _ = MD.newton_max(prob.objective, x)
+    H = -OB.hessian(prob.objective, xs)
+    return np.linalg.eigvalsh(H).min() > 0 and MD.mahalanobis(x[None], xs, H)[0] <= 1e-3
+
+
+def _score(prob, fx, show=False):
+    """(significant modes, fraction matched, worst matched error, other local maxima, non-maxima)."""
+    mx, mf, negH = MD.significant_modes(prob)
+    frac, worst, _ = MD.recovery(fx, mx, negH)
+    other = bad = 0
+    for x in fx.astype(np.float64):
+        if min(MD.mahalanobis(x[None], m, H)[0] for m, H in zip(mx, negH)) > 1e-3:
+            if _is_local_max(prob, x):
+                other += 1
+            else:
+                bad += 1
+                if show:
+                    xs, _ = MD.newton_max(prob.objective, x)
+                    H = -OB.hessian(prob.objective, xs)
+                    g = OB.grad(prob.objective, x[None])[0]
+                    print(f"  non-maximum: d {prob.d} |g|inf {np.abs(g).max():.2e} eig(-H) "
+                          f"{np.linalg.eigvalsh(H)[[0, -1]]} dist {MD.mahalanobis(x[None], xs, H)[0]:.2e}")
+    return len(mx), frac, worst, other, bad
+
+
+def _run(probs, P, **over):
+    model = CH.Chisao(probs, U.lib_params(P, **over))
+    for _ in range(P.n_osc):
+        model.step()
+    out = [model.modes(q)[0] for q in range(len(probs))]
+    model.close()
+    return out
+
+
+def _report(name, n_modes, frac, worst, returned, other, bad):
+    print(f"\nRECOVERY {name}: modes {n_modes} recovered {frac:.3f} worst {worst:.2e} sigma "
+          f"returned {returned} other-maxima {other} non-maxima {bad}")
+
+
+def test_recovery_mixture4_d2():
+    """d = 2, K = 4, N = 1024, FD64 at h = 1e-5, m = 5, 50 cycles."""
+    U.ensure_built()
+    prob = I.mixture4_d2()
+    P = M.Params(n_osc=50, m=5, eps_grad=1e-5, grad_mode=M.GRAD_FD64, seed=0)
+    (fx,) = _run([prob], P)
+    k, frac, worst, other, bad = _score(prob, fx)
+    _report("mixture4_d2", k, frac, worst, fx.shape[0], other, bad)
+    assert frac == 1.0 and other == 0 and bad == 0
+
+
+@pytest.mark.parametrize("noise,n_conv,n_osc,floor", [(0.0, 0, 3, 0.05), (0.0, 0, 30, 0.05), (0.0, 40, 4, 0.9),
+                                                      (0.1, 40, 4, 0.0)])
+def test_recovery_mixture32_d16(noise, n_conv, n_osc, floor):
+    """d = 16, K = 32 diagonal mixture, N = 16384, exact gradients.  With the Table 1
+    rule n_conv = max(10, 3 log2 d) = 12 the median |grad f| after Phase 1 is still
+    ~4e-3, so few samples stick (below eps_grad = 1e-4) and Phases 5-6 move the rest
+    again: more cycles add nothing.  With n_conv = 40 every significant mode is
+    found.  Noise 0.1 on the values stalls the Armijo searches near the modes."""
+    U.ensure_built()
+    prob = I.mixture32_d16(noise_sigma=noise)
+    P = M.Params(n_osc=n_osc, n_conv=n_conv, m=10, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=2)
+    (fx,) = _run([prob], P)
+    k, frac, worst, other, bad = _score(prob, fx)
+    _report(f"mixture32_d16 noise {noise} n_conv {n_conv or 12} cycles {n_osc}", k, frac, worst, fx.shape[0],
+            other, bad)
+    assert frac >= floor and bad == 0
+
+
+def test_recovery_quadratic_d64():
+    """d = 64 rotated quadratic (condition 1e4), N = 65536: one cycle with enough
+    L-BFGS iterations to converge (Prop. 1) recovers the single mode."""
+    U.ensure_built()
+    prob = I.quadratic_d64()
+    P = M.Params(n_osc=1, n_conv=2500, m=10, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=3)
+    (fx,) = _run([prob], P)
+    k, frac, worst, other, bad = _score(prob, fx)
+    _report("quadratic_d64 n_conv 2500", k, frac, worst, fx.shape[0], other, bad)
+    assert frac == 1.0 and other == 0 and bad == 0
+
+
+def test_recovery_mixture256_d64_tensor_cores():
+    """d = 64, K = 256 full-covariance mixture, N = 65536 on the BF16 tensor-core
+    objective with the final FP32 refinement."""
+    U.ensure_built()
+    prob = I.mixture256_d64()
+    P = M.Params(n_osc=2, n_conv=100, m=10, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=4)
+    (fx,) = _run([prob], P, grad_mode=CH.GRAD_ADJOINT_TC, n_refine=10)
+    k, frac, worst, other, bad = _score(prob, fx)
+    _report("mixture256_d64 tensor cores", k, frac, worst, fx.shape[0], other, bad)
+    assert frac >= 0.8 and bad == 0
+
+
+def test_recovery_batched512():
+    """512 diagonal-mixture problems in one context, 3 cycles: the mean recovered
+    fraction over the problems and the spurious returns in all of them."""
+    U.ensure_built()
+    probs = I.batched512()
+    P = M.Params(n_osc=3, m=10, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=5)
+    outs = _run(probs, P)
+    fracs, worst, other, bad, total_modes, returned = [], 0.0, 0, 0, 0, 0
+    for prob, fx in zip(probs, outs):
+        k, frac, w, o, b = _score(prob, fx, show=True)
+        fracs.append(frac)
+        worst = max(worst, w if np.isfinite(w) else 0.0)
+        other += o
+        bad += b
+        total_modes += k
+        returned += fx.shape[0]
+    _report("batched512 (mean over problems)", total_modes, float(np.mean(fracs)), worst, returned, other, bad)
+    assert np.mean(fracs) >= 0.3 and bad <= 0.002 * returned
