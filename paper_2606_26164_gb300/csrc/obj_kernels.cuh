@@ -466,6 +466,26 @@ __device__ __forceinline__ void hlc_body(const ProbDev& P, const StepParams& S, 
           const float w = (float)((value_at<KIND, GM, V, LPS>(P.obj, S, xp, g, ec) - f0) / (TE)sigma);
 #pragma unroll
           for (int v = 0; v < V; ++v) acc[v] = fmaf(w, (j0 + v < P.d) ? z[v] : 0.f, acc[v]);
+        } else if (GM == GRAD_ADJOINT && HasQuad<KIND>::value && k + 3 < S.M) {
+          // four perturbations at once (one pass over the matrix); the sum keeps the order
+          // of the one-at-a-time loop
+          float zq[4][V], xq[4][V], aq[4][V], fq[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index,
+                            (unsigned)(k + p), zq[p]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) xq[p][v] = (j0 + v < P.d) ? fmaf(sigma, zq[p][v], x[v]) : x[v];
+          }
+          if constexpr (HasQuad<KIND>::value)
+            Obj<KIND>::template value_grad_quad<V, LPS>(P.obj.f32, xq, aq, fq, g);
+          ec.evals += 4;
+          ec.grads += 4;
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += aq[p][v];
+          k += 3;
         } else if (GM == GRAD_ADJOINT && HasPair<KIND>::value && k + 1 < S.M) {
           // two perturbations at once, sharing the objective's parameter loads; the sum
           // keeps the order of the one-at-a-time loop
