@@ -13,6 +13,9 @@ constexpr int VL = 4;              // coordinates per lane
 constexpr int NT_OBJ = 128;        // threads per block of the per-sample kernels
 constexpr int NT_SCALES = 256;     // threads per block of the scale reduction
 constexpr int SCALE_BLOCKS = 608;  // fixed grid of the scale reduction (4 x 152 SMs)
+// HLC perturbations evaluated per pass over the objective's matrix (8 measured the same
+// as 4 at d = 64 with 34 more registers)
+constexpr int HLC_NP = 4;
 
 template <int V>
 __device__ __forceinline__ float dotv(const float (&a)[V], const float (&b)[V]) {
@@ -376,6 +379,16 @@ __device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& 
 #pragma unroll
   for (int v = 0; v < V; ++v) sxh[v] = sxl[v] = sqh[v] = sql[v] = 0.f;
   int cnt = 0;
+  auto add = [&](const float (&x)[V], const float (&a)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      ff_add(sxh[v], sxl[v], x[v], 0.f);
+      const float p2 = x[v] * x[v];
+      ff_add(sqh[v], sql[v], p2, fmaf(x[v], x[v], -p2));
+    }
+    ff_add(sgh, sgl, g.sum(dotv<V>(a, a)), 0.f);    // sum of squares: no cancellation
+    ++cnt;
+  };
   for (int i = (int)blk * GPB + grp; i < P.n; i += (int)nblk * GPB) {
     if (bit_of(P.stuck, i)) continue;
     float x[V], a[V];
@@ -388,14 +401,7 @@ __device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& 
       gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
       st_vec<V>(P.g + (size_t)i * DP + j0, a);
     }
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      ff_add(sxh[v], sxl[v], x[v], 0.f);
-      const float p2 = x[v] * x[v];
-      ff_add(sqh[v], sql[v], p2, fmaf(x[v], x[v], -p2));
-    }
-    ff_add(sgh, sgl, g.sum(dotv<V>(a, a)), 0.f);    // sum of squares: no cancellation
-    ++cnt;
+    add(x, a);
   }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -466,26 +472,26 @@ __device__ __forceinline__ void hlc_body(const ProbDev& P, const StepParams& S, 
           const float w = (float)((value_at<KIND, GM, V, LPS>(P.obj, S, xp, g, ec) - f0) / (TE)sigma);
 #pragma unroll
           for (int v = 0; v < V; ++v) acc[v] = fmaf(w, (j0 + v < P.d) ? z[v] : 0.f, acc[v]);
-        } else if (GM == GRAD_ADJOINT && HasQuad<KIND>::value && k + 3 < S.M) {
-          // four perturbations at once (one pass over the matrix); the sum keeps the order
-          // of the one-at-a-time loop
-          float zq[4][V], xq[4][V], aq[4][V], fq[4];
+        } else if (GM == GRAD_ADJOINT && HasMulti<KIND>::value && k + HLC_NP - 1 < S.M) {
+          // HLC_NP perturbations at once (one pass over the matrix); the sum keeps the
+          // order of the one-at-a-time loop
+          float zq[HLC_NP][V], xq[HLC_NP][V], aq[HLC_NP][V], fq[HLC_NP];
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
+          for (int p = 0; p < HLC_NP; ++p) {
             normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index,
                             (unsigned)(k + p), zq[p]);
 #pragma unroll
             for (int v = 0; v < V; ++v) xq[p][v] = (j0 + v < P.d) ? fmaf(sigma, zq[p][v], x[v]) : x[v];
           }
-          if constexpr (HasQuad<KIND>::value)
-            Obj<KIND>::template value_grad_quad<V, LPS>(P.obj.f32, xq, aq, fq, g);
-          ec.evals += 4;
-          ec.grads += 4;
+          if constexpr (HasMulti<KIND>::value)
+            Obj<KIND>::template value_grad_multi<HLC_NP, V, LPS>(P.obj.f32, xq, aq, fq, g);
+          ec.evals += HLC_NP;
+          ec.grads += HLC_NP;
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+          for (int p = 0; p < HLC_NP; ++p)
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] += aq[p][v];
-          k += 3;
+          k += HLC_NP - 1;
         } else if (GM == GRAD_ADJOINT && HasPair<KIND>::value && k + 1 < S.M) {
           // two perturbations at once, sharing the objective's parameter loads; the sum
           // keeps the order of the one-at-a-time loop

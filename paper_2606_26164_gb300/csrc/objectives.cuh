@@ -156,34 +156,34 @@ __device__ __forceinline__ void rows_times2(const float* M, int dp, int d, const
   }
 }
 
-// Four products with the same matrix at once (four evaluation points of one lane
-// group): each row block is read once for all four; every output keeps the FMA order
-// of rows_times, so the results are the same bit for bit.
-template <int LPS>
-__device__ __forceinline__ void rows_times4(const float* M, int dp, int d, const float (&r)[4][4],
-                                            float (&out)[4][4], const Grp<LPS>& g) {
-  __shared__ float4 rquad[4][256];                // the largest block of the objective kernels
+// NP products with the same matrix at once (NP evaluation points of one lane group):
+// each row block is read once for all of them; every output keeps the FMA order of
+// rows_times, so the results are the same bit for bit.
+template <int NP, int LPS>
+__device__ __forceinline__ void rows_timesn(const float* M, int dp, int d, const float (&r)[NP][4],
+                                            float (&out)[NP][4], const Grp<LPS>& g) {
+  __shared__ float4 rmulti[NP][256];              // the largest block of the objective kernels
 #pragma unroll
-  for (int p = 0; p < 4; ++p) rquad[p][threadIdx.x] = make_float4(r[p][0], r[p][1], r[p][2], r[p][3]);
+  for (int p = 0; p < NP; ++p) rmulti[p][threadIdx.x] = make_float4(r[p][0], r[p][1], r[p][2], r[p][3]);
   __syncwarp(g.mask);
   const int base = threadIdx.x - g.l;
-  float2 acc[4][2];
+  float2 acc[NP][2];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) acc[p][0] = acc[p][1] = make_float2(0.f, 0.f);
+  for (int p = 0; p < NP; ++p) acc[p][0] = acc[p][1] = make_float2(0.f, 0.f);
   const float* col = M + 4 * g.l;
   const int nb = (d + 3) / 4;
 #pragma unroll 1
   for (int jb = 0; jb < nb; ++jb) {
-    float4 b[4];
+    float4 b[NP];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) b[p] = rquad[p][base + jb];
+    for (int p = 0; p < NP; ++p) b[p] = rmulti[p][base + jb];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       float a[4];
       ldg_vec<float, 4>(col + (size_t)(jb * 4 + v) * dp, a);
       const float2 a0 = make_float2(a[0], a[1]), a1 = make_float2(a[2], a[3]);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
+      for (int p = 0; p < NP; ++p) {
         const float s = v == 0 ? b[p].x : v == 1 ? b[p].y : v == 2 ? b[p].z : b[p].w;
         const float2 s2 = make_float2(s, s);
         acc[p][0] = __ffma2_rn(a0, s2, acc[p][0]);
@@ -193,7 +193,7 @@ __device__ __forceinline__ void rows_times4(const float* M, int dp, int d, const
   }
   __syncwarp(g.mask);
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < NP; ++p) {
     out[p][0] = acc[p][0].x;
     out[p][1] = acc[p][0].y;
     out[p][2] = acc[p][1].x;
@@ -208,9 +208,9 @@ struct Obj;
 // (binary32 value and gradient; each point's arithmetic exactly that of value_grad).
 template <int KIND>
 struct HasPair : std::false_type {};
-// ... and four points sharing one pass over the objective's parameters.
+// ... and several points (value_grad_multi<NP>) sharing one pass over them.
 template <int KIND>
-struct HasQuad : std::false_type {};
+struct HasMulti : std::false_type {};
 
 // ------------------------------------------------------------ diagonal mixture
 template <>
@@ -396,19 +396,19 @@ struct Obj<OBJ_QUADRATIC> {
     f1 = -g.sum(acc1);
     f2 = -g.sum(acc2);
   }
-  template <int V, int LPS>
-  static __device__ __forceinline__ void value_grad_quad(const ObjParams<float>& o, const float (&x)[4][V],
-                                                         float (&gr)[4][V], float (&f)[4], const Grp<LPS>& g) {
+  template <int NP, int V, int LPS>
+  static __device__ __forceinline__ void value_grad_multi(const ObjParams<float>& o, const float (&x)[NP][V],
+                                                          float (&gr)[NP][V], float (&f)[NP], const Grp<LPS>& g) {
     static_assert(V == 4, "four coordinates per lane");
-    float c[V], r[4][V], u[4][V];
+    float c[V], r[NP][V], u[NP][V];
     ldg_vec<float, V>(o.p0 + V * g.l, c);
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < NP; ++p)
 #pragma unroll
       for (int v = 0; v < V; ++v) r[p][v] = x[p][v] - c[v];
-    rows_times4<LPS>(o.p1, o.dp, o.d, r, u, g);
+    rows_timesn<NP, LPS>(o.p1, o.dp, o.d, r, u, g);
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < NP; ++p) {
       float acc = 0.f;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -422,7 +422,7 @@ struct Obj<OBJ_QUADRATIC> {
 template <>
 struct HasPair<OBJ_QUADRATIC> : std::true_type {};
 template <>
-struct HasQuad<OBJ_QUADRATIC> : std::true_type {};
+struct HasMulti<OBJ_QUADRATIC> : std::true_type {};
 
 // ------------------------------------------------------------ Appendix D benchmark functions
 // Negated (maximisation) forms, coordinate i = j + 1 for the lane's coordinate j;
