@@ -43,7 +43,10 @@ typedef enum {
   CHISAO_ERR_CUDA = 2,       /* a CUDA runtime call failed                    */
   CHISAO_ERR_OOM = 3,        /* device allocation or arena too small         */
   CHISAO_ERR_CAPACITY = 4,   /* output buffer smaller than the result        */
-  CHISAO_ERR_STATE = 5       /* call not valid in the context's state         */
+  CHISAO_ERR_STATE = 5,      /* call not valid in the context's state         */
+  CHISAO_ERR_TIMEOUT = 6     /* a device-side wait ran out of its time budget
+                                (reported once by chisao_get_counters, which
+                                clears the flag; the context stays usable)     */
 } chisao_status;
 
 /* Objective families (built-in device objectives). */
@@ -205,6 +208,7 @@ typedef struct {
   float sigma;             /* last HLC smoothing scale                           */
   float alpha_hlc;         /* last HLC step                                      */
   float alpha_anti;        /* last anti-convergence step                         */
+  int32_t device_error;    /* device error flag: 0 none, 2 a bounded wait timed out */
 } chisao_counters;
 
 typedef struct chisao_ctx chisao_ctx;
@@ -277,8 +281,16 @@ chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
 chisao_status chisao_widths(chisao_ctx *c, int32_t prob, float *w_out, float *cov_out,
                             int64_t cap, int64_t *count);
 
-/* Counters of problem `prob` (synchronizes the stream). */
+/* Counters of problem `prob` (synchronizes the stream).  When a kernel of the
+ * problem gave up a bounded wait (the tensor-core objective's barrier waits have a
+ * budget of about a second; kernels never trap), the counters are filled, the
+ * device flag is cleared and CHISAO_ERR_TIMEOUT is returned. */
 chisao_status chisao_get_counters(chisao_ctx *c, int32_t prob, chisao_counters *out);
+
+/* Test hook for that failure path: one kernel waits, with the library's bounded
+ * wait, on a shared-memory barrier nothing arrives on; after budget_ns (1 .. 10^10)
+ * it raises problem `prob`'s device error flag and returns.  Asynchronous. */
+chisao_status chisao_selftest_wait(chisao_ctx *c, int32_t prob, int64_t budget_ns);
 
 /* Evaluate problem `prob`'s objective at n device points x_dev[n][d]:
  * f_dev[n] (may be NULL) and, when g_dev[n][d] is not NULL, the gradient by

@@ -18,7 +18,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libchisao.so")
 
-OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE = 0, 1, 2, 3, 4, 5
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_STATE, ERR_TIMEOUT = 0, 1, 2, 3, 4, 5, 6
 GRAD_FD64, GRAD_FD32, GRAD_ADJOINT, GRAD_ADJOINT_TC = 0, 1, 2, 3
 SEED_UNIFORM, SEED_CARRY_TIGER = 0, 1
 FIELD_X, FIELD_G, FIELD_F, FIELD_HS, FIELD_HY, FIELD_HRHO, FIELD_HLEN, FIELD_STUCK, FIELD_REMOVED = range(9)
@@ -30,7 +30,7 @@ EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chis
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
            "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
-           "chisao_widths"]
+           "chisao_widths", "chisao_selftest_wait"]
 
 
 class CParams(C.Structure):
@@ -131,7 +131,8 @@ class CCounters(C.Structure):
     _fields_ = [("evals", C.c_uint64), ("grads", C.c_uint64), ("ls_trials", C.c_uint64), ("ls_fail", C.c_uint64),
                 ("cycles", C.c_int64), ("n_stuck", C.c_int64), ("k_lost", C.c_int64), ("n_unfrozen", C.c_int64),
                 ("last_reseed", C.c_int32), ("gr_enabled", C.c_int32), ("f_max", C.c_float),
-                ("sigma", C.c_float), ("alpha_hlc", C.c_float), ("alpha_anti", C.c_float)]
+                ("sigma", C.c_float), ("alpha_hlc", C.c_float), ("alpha_anti", C.c_float),
+                ("device_error", C.c_int32)]
 
 
 _lib = None
@@ -153,6 +154,9 @@ def library() -> C.CDLL:
         lib.chisao_step.argtypes = [vp]
         lib.chisao_load_population.argtypes = [vp, C.c_int32, C.POINTER(C.c_float)]
         lib.chisao_seed.argtypes = [vp, C.c_int32, C.c_int32]
+        lib.chisao_selftest_wait.argtypes = [vp, C.c_int32, C.c_int64]
+        lib.chisao_widths.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
+                                      C.POINTER(C.c_int64)]
         lib.chisao_modes.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
                                      C.POINTER(C.c_int64)]
         lib.chisao_get_counters.argtypes = [vp, C.c_int32, C.POINTER(CCounters)]
@@ -306,6 +310,10 @@ class Chisao:
                                                 co.ctypes.data_as(fp) if cov else None, k, C.byref(cnt)),
                         "chisao_widths")
         return wo[:k].copy(), (co[:k].copy() if cov else None)
+
+    def selftest_wait(self, prob: int = 0, budget_ns: int = 10_000_000):
+        """Test hook: a bounded device wait that runs out and raises the problem's error flag."""
+        self._check(library().chisao_selftest_wait(self.ctx, prob, budget_ns), "chisao_selftest_wait")
 
     def counters(self, prob: int = 0) -> dict:
         c = CCounters()

@@ -1019,6 +1019,21 @@ chisao_status chisao_get_counters(chisao_ctx* c, int32_t prob, chisao_counters* 
   out->sigma = cnt.sigma;
   out->alpha_hlc = cnt.alpha_hlc;
   out->alpha_anti = cnt.alpha_anti;
+  out->device_error = cnt.err;
+  if (cnt.err != 0) {
+    CK(cudaMemsetAsync(&c->probs[prob].dev.cnt->err, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return fail(c, CHISAO_ERR_TIMEOUT, "a device-side wait ran out of its time budget (flag " +
+                                           std::to_string(cnt.err) + ", now cleared)");
+  }
+  return CHISAO_OK;
+}
+
+chisao_status chisao_selftest_wait(chisao_ctx* c, int32_t prob, int64_t budget_ns) {
+  chisao_status s = check_prob(c, prob);
+  if (s != CHISAO_OK) return s;
+  if (budget_ns < 1 || budget_ns > 10000000000ll) return fail(c, CHISAO_ERR_ARG, "budget_ns out of range");
+  CK(tc_wait_selftest(budget_ns, &c->probs[prob].dev.cnt->err, c->stream));
   return CHISAO_OK;
 }
 

@@ -68,6 +68,8 @@ cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const E
 
 // tensor-core (tcgen05, BF16) full-covariance mixture objective
 cudaError_t tc_prepare_attributes();
+// A bounded wait that runs out (budget_ns of the global timer) and raises *err = 2.
+cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st);
 size_t tc_weight_bytes(int K);     // operand tiles of all component groups
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out);

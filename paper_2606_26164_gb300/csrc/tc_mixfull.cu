@@ -598,6 +598,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   }
 }
 
+// The failure path of the bounded waits, on its own: thread 0 waits on a barrier that
+// expects one arrival nobody makes, gives up after budget_ns of the global timer, raises
+// the error flag and returns (no trap), as every barrier wait of k_tc_mixfull does.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void k_wait_selftest(long long budget_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(&bar, 0)) {
+      if ((long long)(global_ns() - t0) > budget_ns) {
+        atomicExch(err, 2);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------ host side
@@ -668,6 +692,11 @@ void tc_build_weights(int K, int d, const double* linv, const double* mu, const 
       cst[kl] = (float)(logw[k] + ldet - d * half_log2pi);
     }
   }
+}
+
+cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st) {
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(budget_ns, err);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights, float* f,

@@ -342,3 +342,23 @@ def test_degenerate_sizes(d, n):
     assert np.all(w > 0) and np.all(np.isfinite(H))
     assert model.counters(0)["cycles"] == P.n_osc
     model.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
+    """A device wait that nothing completes gives up after its budget (no trap, no
+    hang), raises the problem's error flag, and chisao_get_counters reports
+    CHISAO_ERR_TIMEOUT once and clears it; the context then keeps stepping."""
+    prob = I.small_mixture(3, 2, 500, seed=1)
+    P = M.Params(n_osc=4, m=5, grad_mode=M.GRAD_ADJOINT, seed=2)
+    model = U.open_ctx(prob, P)
+    model.step()
+    model.selftest_wait(0, budget_ns=20_000_000)
+    with pytest.raises(CH.ChisaoError, match=r"\(6\)"):
+        model.counters(0)
+    c = model.counters(0)
+    assert c["device_error"] == 0 and c["cycles"] == 1
+    model.step()
+    model.step()
+    fx, _ = model.modes(0)
+    assert model.counters(0)["cycles"] == 3 and fx.shape[1] == 3
+    model.close()
