@@ -265,6 +265,27 @@ chisao_status chisao_seed(chisao_ctx *c, int32_t prob, int32_t method);
 chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
                            float *f_out, int64_t cap, int64_t *count);
 
+/* Result of chisao_autotune. */
+typedef struct {
+  int32_t n_branch;        /* branch streams chosen (contexts of several problems)  */
+  int32_t grouped;         /* 1: Phases 1, 5, 6 and the scale passes run as grouped
+                              launches per (objective kind, padded dimension)        */
+  int32_t trials;          /* configurations timed                                    */
+  float ms_per_cycle;      /* the chosen configuration's time per non-final cycle     */
+  float ms_default;        /* the configuration the context had before              */
+} chisao_tuning;
+
+/* Launch-shape autotuner for contexts of several problems: for each candidate (8, 16,
+ * 32 or 64 branch streams for the per-problem steps, times grouped or per-problem
+ * launches of the per-sample phases) it captures a non-final cycle of the context
+ * itself in a CUDA graph, runs it once untimed and then cycles_per_trial (1 .. 100)
+ * times under CUDA events, and keeps the fastest.  Every candidate computes the same
+ * results bit for bit, and the context's state is saved before and restored after
+ * each trial (one device copy of the arena, needing arena-sized free memory), so the
+ * tuning changes no result and no trajectory.  A context of one problem has nothing
+ * to tune (trials = 0).  Synchronous. */
+chisao_status chisao_autotune(chisao_ctx *c, int32_t cycles_per_trial, chisao_tuning *out);
+
 /* Laplace widths of the modes chisao_modes returns (same order).  Phase 3
  * (Sec. 3.2.3) keeps each surviving sample's inverse-Hessian estimate for width
  * estimation; the paper gives no formula, and the reading here is the Laplace

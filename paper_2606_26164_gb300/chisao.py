@@ -30,7 +30,7 @@ EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chis
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
            "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
-           "chisao_widths", "chisao_selftest_wait"]
+           "chisao_widths", "chisao_selftest_wait", "chisao_autotune"]
 
 
 class CParams(C.Structure):
@@ -127,6 +127,11 @@ class CProblem(C.Structure):
                 ("x0", C.POINTER(C.c_float)), ("objective", CObjective)]
 
 
+class CTuning(C.Structure):
+    _fields_ = [("n_branch", C.c_int32), ("grouped", C.c_int32), ("trials", C.c_int32),
+                ("ms_per_cycle", C.c_float), ("ms_default", C.c_float)]
+
+
 class CCounters(C.Structure):
     _fields_ = [("evals", C.c_uint64), ("grads", C.c_uint64), ("ls_trials", C.c_uint64), ("ls_fail", C.c_uint64),
                 ("cycles", C.c_int64), ("n_stuck", C.c_int64), ("k_lost", C.c_int64), ("n_unfrozen", C.c_int64),
@@ -155,6 +160,7 @@ def library() -> C.CDLL:
         lib.chisao_load_population.argtypes = [vp, C.c_int32, C.POINTER(C.c_float)]
         lib.chisao_seed.argtypes = [vp, C.c_int32, C.c_int32]
         lib.chisao_selftest_wait.argtypes = [vp, C.c_int32, C.c_int64]
+        lib.chisao_autotune.argtypes = [vp, C.c_int32, C.POINTER(CTuning)]
         lib.chisao_widths.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
                                       C.POINTER(C.c_int64)]
         lib.chisao_modes.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
@@ -310,6 +316,12 @@ class Chisao:
                                                 co.ctypes.data_as(fp) if cov else None, k, C.byref(cnt)),
                         "chisao_widths")
         return wo[:k].copy(), (co[:k].copy() if cov else None)
+
+    def autotune(self, cycles_per_trial: int = 2) -> dict:
+        """Pick the fastest launch shape for this context (results and state unchanged)."""
+        t = CTuning()
+        self._check(library().chisao_autotune(self.ctx, cycles_per_trial, C.byref(t)), "chisao_autotune")
+        return {name: getattr(t, name) for name, _ in CTuning._fields_}
 
     def selftest_wait(self, prob: int = 0, budget_ns: int = 10_000_000):
         """Test hook: a bounded device wait that runs out and raises the problem's error flag."""

@@ -88,6 +88,7 @@ struct chisao_ctx {
   cudaEvent_t forked = nullptr;
   std::vector<int> branch_of;              // problem -> branch
   std::vector<Group> groups;               // grouped Phase 1 / 5 / 6 launches (empty: per problem)
+  bool groups_enabled = true;              // chisao_autotune's choice
   std::string err;
 };
 
@@ -571,7 +572,7 @@ cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
 // One oscillation cycle of every problem: independent problems on the branch streams.
 cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
   cudaError_t e;
-  if (!c->groups.empty()) return enqueue_cycle_grouped(c, last);
+  if (!c->groups.empty() && c->groups_enabled) return enqueue_cycle_grouped(c, last);
   if (c->branch.empty()) {
     for (const ProbHost& ph : c->probs)
       if ((e = enqueue_problem_cycle(ph, last, c->stream)) != cudaSuccess) return e;
@@ -589,12 +590,26 @@ cudaError_t enqueue_cycle(chisao_ctx* c, bool last) {
   return cudaSuccess;
 }
 
-// Branch streams for a context of several problems; each problem goes, largest first,
-// to the branch with the least work so far (work ~ samples x padded dimension).
-cudaError_t make_branches(chisao_ctx* c) {
+void free_branches(chisao_ctx* c) {
+  for (cudaStream_t s : c->branch) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t ev : c->joined) cudaEventDestroy(ev);
+  if (c->forked) cudaEventDestroy(c->forked);
+  c->branch.clear();
+  c->joined.clear();
+  c->forked = nullptr;
+  c->branch_of.clear();
+}
+
+// Branch streams for a context of several problems (nb_req of them, at most one per
+// problem); each problem goes, largest first, to the branch with the least work so far
+// (work ~ samples x padded dimension).
+cudaError_t make_branches(chisao_ctx* c, int nb_req = 32) {
   const int nq = (int)c->probs.size();
   if (nq < 2) return cudaSuccess;
-  const int nb = std::min(nq, 32);
+  const int nb = std::max(1, std::min(nq, nb_req));
   cudaError_t e;
   if ((e = cudaEventCreateWithFlags(&c->forked, cudaEventDisableTiming)) != cudaSuccess) return e;
   for (int b = 0; b < nb; ++b) {
@@ -970,6 +985,105 @@ chisao_status chisao_modes(chisao_ctx* c, int32_t prob, float* x_out, float* f_o
   return CHISAO_OK;
 }
 
+chisao_status chisao_autotune(chisao_ctx* c, int32_t cycles_per_trial, chisao_tuning* out) {
+  if (!c) return CHISAO_ERR_ARG;
+  if (!out || cycles_per_trial < 1 || cycles_per_trial > 100) return fail(c, CHISAO_ERR_ARG, "bad arguments");
+  memset(out, 0, sizeof(*out));
+  out->n_branch = (int32_t)c->branch.size();
+  out->grouped = (!c->groups.empty() && c->groups_enabled) ? 1 : 0;
+  const int nq = (int)c->probs.size();
+  if (nq < 2) return CHISAO_OK;
+  void* backup = nullptr;
+  if (cudaMalloc(&backup, c->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CHISAO_ERR_OOM, "no device memory for the state snapshot");
+  }
+  const int saved_cycles = c->cycles_done;
+  const int def_nb = (int)c->branch.size();
+  const bool def_g = c->groups_enabled;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemcpyAsync(backup, c->arena, c->arena_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto restore = [&]() {
+    return cudaMemcpyAsync(c->arena, backup, c->arena_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  };
+  auto apply = [&](int nb, bool grouped) -> cudaError_t {
+    cudaError_t r = cudaStreamSynchronize(c->stream);
+    if (r != cudaSuccess) return r;
+    free_branches(c);
+    c->groups_enabled = grouped;
+    return make_branches(c, nb);
+  };
+  // one trial: restore, capture a non-final cycle, run it once untimed, then time it
+  auto trial = [&](float* ms) -> cudaError_t {
+    cudaError_t r;
+    if ((r = restore()) != cudaSuccess) return r;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if ((r = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return r;
+    const cudaError_t rc = enqueue_cycle(c, false);
+    r = cudaStreamEndCapture(c->stream, &graph);
+    if (rc != cudaSuccess || r != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != cudaSuccess ? rc : r;
+    }
+    r = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (r != cudaSuccess) return r;
+    if ((r = cudaGraphLaunch(ge, c->stream)) == cudaSuccess && (r = cudaEventRecord(e0, c->stream)) == cudaSuccess) {
+      for (int k = 0; k < cycles_per_trial && r == cudaSuccess; ++k) r = cudaGraphLaunch(ge, c->stream);
+      if (r == cudaSuccess) r = cudaEventRecord(e1, c->stream);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(ms, e0, e1);
+    }
+    cudaGraphExecDestroy(ge);
+    *ms /= (float)cycles_per_trial;
+    return r;
+  };
+  int best_nb = def_nb, trials = 0;
+  bool best_g = def_g;
+  float best = 3.0e38f, def_ms = 0.f;
+  const int nbs[4] = {8, 16, 32, 64};
+  for (int gi = 0; gi < (c->groups.empty() ? 1 : 2) && e == cudaSuccess; ++gi) {
+    const bool g = c->groups.empty() ? false : gi == 0;
+    int last_nb = -1;
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+      const int nb = std::min(nbs[t], nq);
+      if (nb == last_nb) continue;                   // fewer problems than the candidate
+      last_nb = nb;
+      float ms = 0.f;
+      if ((e = apply(nb, g)) != cudaSuccess || (e = trial(&ms)) != cudaSuccess) break;
+      ++trials;
+      if (nb == def_nb && g == def_g) def_ms = ms;
+      if (ms < best) {
+        best = ms;
+        best_nb = nb;
+        best_g = g;
+      }
+    }
+  }
+  // the chosen configuration, the saved state, and graphs recaptured at the next step
+  const cudaError_t ea = apply(best_nb, best_g);
+  if (e == cudaSuccess) e = ea;
+  if (e == cudaSuccess) e = restore();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (c->g_mid) cudaGraphExecDestroy(c->g_mid);
+  if (c->g_last) cudaGraphExecDestroy(c->g_last);
+  c->g_mid = c->g_last = nullptr;
+  c->cycles_done = saved_cycles;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(backup);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  out->n_branch = best_nb;
+  out->grouped = best_g ? 1 : 0;
+  out->trials = trials;
+  out->ms_per_cycle = best;
+  out->ms_default = def_ms;
+  return CHISAO_OK;
+}
+
 chisao_status chisao_widths(chisao_ctx* c, int32_t prob, float* w_out, float* cov_out, int64_t cap,
                             int64_t* count) {
   chisao_status s = check_prob(c, prob);
@@ -1069,12 +1183,7 @@ void chisao_destroy(chisao_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->g_mid) cudaGraphExecDestroy(c->g_mid);
   if (c->g_last) cudaGraphExecDestroy(c->g_last);
-  for (cudaStream_t s : c->branch) {
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  }
-  for (cudaEvent_t ev : c->joined) cudaEventDestroy(ev);
-  if (c->forked) cudaEventDestroy(c->forked);
+  free_branches(c);
   for (Group& gr : c->groups)
     if (gr.mem) cudaFree(gr.mem);
   if (c->own_arena && c->arena) cudaFree(c->arena);

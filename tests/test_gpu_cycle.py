@@ -362,3 +362,31 @@ def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
     fx, _ = model.modes(0)
     assert model.counters(0)["cycles"] == 3 and fx.shape[1] == 3
     model.close()
+
+
+def test_autotune_keeps_state_and_results():
+    """The launch-shape autotuner (branch streams x grouped or per-problem launches)
+    leaves the state as it found it, and the cycles that follow give the same bits as
+    in a context that was never tuned."""
+    probs = I.batched512(n_problems=20, n_scale=0.05, seed=8)
+    P = M.Params(n_osc=6, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=3)
+    U.ensure_built()
+    tuned = CH.Chisao(probs, U.lib_params(P))
+    plain = CH.Chisao(probs, U.lib_params(P))
+    for m in (tuned, plain):
+        m.step()
+    before = [tuned.get(q, CH.FIELD_X).copy() for q in range(len(probs))]
+    t = tuned.autotune(cycles_per_trial=1)
+    assert t["trials"] >= 4 and t["n_branch"] in (8, 16, 20) and t["grouped"] in (0, 1)
+    assert 0 < t["ms_per_cycle"] <= t["ms_default"] * 1.0001
+    for q in range(len(probs)):
+        np.testing.assert_array_equal(tuned.get(q, CH.FIELD_X), before[q])
+        assert tuned.counters(q)["cycles"] == 1
+    for m in (tuned, plain):
+        m.step()
+        m.step()
+    for q in range(len(probs)):
+        for fld in (CH.FIELD_X, CH.FIELD_F, CH.FIELD_STUCK):
+            np.testing.assert_array_equal(tuned.get(q, fld), plain.get(q, fld))
+    tuned.close()
+    plain.close()
