@@ -265,6 +265,13 @@ chisao_status chisao_seed(chisao_ctx *c, int32_t prob, int32_t method);
 chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
                            float *f_out, int64_t cap, int64_t *count);
 
+/* Measured FMA throughput of this GPU, the denominator of the ALU rooflines the
+ * benchmark reports: *flops receives FLOP/s (two per FMA) of independent FMA chains
+ * filling every SM, binary32 (precision 0; packed two-lane FMAs, as the objective
+ * kernels issue them) or binary64 (precision 1).  Runs on the given stream (NULL:
+ * the default stream) and synchronizes it; a few milliseconds. */
+chisao_status chisao_measure_fma_peak(int32_t precision, void *cuda_stream, double *flops);
+
 /* Result of chisao_autotune. */
 typedef struct {
   int32_t n_branch;        /* branch streams chosen (contexts of several problems)  */

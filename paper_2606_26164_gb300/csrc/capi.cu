@@ -985,6 +985,13 @@ chisao_status chisao_modes(chisao_ctx* c, int32_t prob, float* x_out, float* f_o
   return CHISAO_OK;
 }
 
+chisao_status chisao_measure_fma_peak(int32_t precision, void* cuda_stream, double* flops) {
+  if (!flops || (precision != 0 && precision != 1)) return CHISAO_ERR_ARG;
+  return measure_fma_peak(precision, flops, reinterpret_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+             ? CHISAO_OK
+             : CHISAO_ERR_CUDA;
+}
+
 chisao_status chisao_autotune(chisao_ctx* c, int32_t cycles_per_trial, chisao_tuning* out) {
   if (!c) return CHISAO_ERR_ARG;
   if (!out || cycles_per_trial < 1 || cycles_per_trial > 100) return fail(c, CHISAO_ERR_ARG, "bad arguments");
