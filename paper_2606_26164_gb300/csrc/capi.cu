@@ -383,7 +383,8 @@ __global__ void k_reset_problem(ProbDev P) {
 cudaError_t enqueue_explore(const ProbHost& ph, cudaStream_t st) {
   cudaError_t e;
   if ((e = launch_reseed(ph.dev, ph.sp, st)) != cudaSuccess) return e;
-  if ((e = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
+  // Phase 1 left the gradients of every unmoved sample in g: only reseeded slots need new ones
+  if ((e = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 1, nullptr, st)) != cudaSuccess) return e;
   if ((e = launch_finalize_scales(ph.dev, ph.sp, 0, st)) != cudaSuccess) return e;
   if ((e = launch_objective(OKID_HLC, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
   if ((e = launch_objective(OKID_SCALES, ph, ph.sp.grad_mode, 0, nullptr, st)) != cudaSuccess) return e;
@@ -489,14 +490,14 @@ cudaError_t enqueue_problem_cycle(const ProbHost& ph, bool last, cudaStream_t st
   return launch_cycle_end(ph.dev, st);
 }
 
-cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st) {
+cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st, int arg = 0) {
   const GroupTab& T = which == OKID_SCALES ? gr.tab_sc : gr.tab;
   const unsigned blocks = which == OKID_SCALES ? gr.blocks_sc : gr.blocks;
   switch (gr.kind) {
-    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, T, blocks, st);
-    case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, T, blocks, st);
-    case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, T, blocks, st);
-    default: return launch_grp_bench(which, gr.dp, T, blocks, st);
+    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, T, blocks, st, arg);
+    case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, T, blocks, st, arg);
+    case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, T, blocks, st, arg);
+    default: return launch_grp_bench(which, gr.dp, T, blocks, st, arg);
   }
 }
 
@@ -504,7 +505,7 @@ cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st) {
 cudaError_t enqueue_explore_group(const Group& gr, cudaStream_t st) {
   cudaError_t e;
   const int k = (int)gr.members.size();
-  if ((e = launch_grouped(OKID_SCALES, gr, st)) != cudaSuccess) return e;
+  if ((e = launch_grouped(OKID_SCALES, gr, st, 1)) != cudaSuccess) return e;      // Phase 1's gradients reused
   if ((e = launch_finalize_grp(gr.tab_sc, k, gr.dp, 0, st)) != cudaSuccess) return e;
   if ((e = launch_grouped(OKID_HLC, gr, st)) != cudaSuccess) return e;
   if ((e = launch_grouped(OKID_SCALES, gr, st)) != cudaSuccess) return e;

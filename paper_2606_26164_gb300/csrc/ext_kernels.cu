@@ -329,7 +329,7 @@ static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& 
     case EXT_HLC_STEP: k_ext_hlc_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E); break;
     case EXT_ANTI_STEP: k_ext_anti_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
     case EXT_SCALES:
-      k_scales<OBJ_MIXTURE_FULL, DP, GRAD_GIVEN><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S);
+      k_scales<OBJ_MIXTURE_FULL, DP, GRAD_GIVEN><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, 0);
       break;
     default: return cudaErrorInvalidValue;
   }

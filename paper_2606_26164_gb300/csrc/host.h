@@ -18,15 +18,15 @@ cudaError_t measure_fma_peak(int f64, double* flops, cudaStream_t st);
 unsigned obj_blocks(long long n, int dp);
 // Grouped launches of Phase 1 / 5 / 6 (OKID_PHASE1, OKID_HLC, OKID_ANTI) with exact gradients
 // over the problems of one group (same objective kind and padded dimension dp).
-cudaError_t launch_grp_mixdiag(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_mixfull(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_quad(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench_4(int which, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench_8(int which, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench_16(int which, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench_32(int which, const GroupTab& T, unsigned blocks, cudaStream_t st);
-cudaError_t launch_grp_bench_64(int which, const GroupTab& T, unsigned blocks, cudaStream_t st);
+cudaError_t launch_grp_mixdiag(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_mixfull(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_quad(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench_4(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench_8(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench_16(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench_32(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+cudaError_t launch_grp_bench_64(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
 cudaError_t launch_obj_mixdiag(int which, int gm, const ProbDev& P, const StepParams& S, int arg,
                                const EvalArgs* ea, cudaStream_t st);
 cudaError_t launch_obj_mixfull(int which, int gm, const ProbDev& P, const StepParams& S, int arg,

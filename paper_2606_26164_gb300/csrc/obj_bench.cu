@@ -15,13 +15,13 @@ cudaError_t launch_obj_bench(int which, int gm, const ProbDev& P, const StepPara
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_grp_bench(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st) {
+cudaError_t launch_grp_bench(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg) {
   switch (dp) {
-    case 4: return launch_grp_bench_4(which, T, blocks, st);
-    case 8: return launch_grp_bench_8(which, T, blocks, st);
-    case 16: return launch_grp_bench_16(which, T, blocks, st);
-    case 32: return launch_grp_bench_32(which, T, blocks, st);
-    case 64: return launch_grp_bench_64(which, T, blocks, st);
+    case 4: return launch_grp_bench_4(which, T, blocks, st, arg);
+    case 8: return launch_grp_bench_8(which, T, blocks, st, arg);
+    case 16: return launch_grp_bench_16(which, T, blocks, st, arg);
+    case 32: return launch_grp_bench_32(which, T, blocks, st, arg);
+    case 64: return launch_grp_bench_64(which, T, blocks, st, arg);
   }
   return cudaErrorInvalidValue;
 }

@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(NT_OBJ) k_direction(ProbDev P) {
 // (sum x_j, sum x_j^2 per coordinate, sum |g|^2, count), accumulated in
 // double-single and reduced in a fixed order so the result is deterministic.
 template <int KIND, int DP, int GM>
-__device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& S, unsigned blk, unsigned nblk) {
+__device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& S, unsigned blk, unsigned nblk,
+                                            int reuse) {
   constexpr int V = VL, LPS = DP / V;
   constexpr int GPB = NT_SCALES / LPS;             // groups per block
   constexpr int W = 2 * DP + 2;
@@ -397,6 +398,10 @@ __device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& 
       ld_vec<V>(P.g + (size_t)i * DP + j0, a);          // computed by the batched evaluator
       ec.evals += 1;
       ec.grads += 1;
+    } else if (reuse && !bit_of(P.removed, i)) {
+      // Phase 1 left the gradient at this point in g and nothing has moved the sample
+      // since (only the reseeded slots, the removed ones, have): the same bits
+      ld_vec<V>(P.g + (size_t)i * DP + j0, a);
     } else {
       gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
       st_vec<V>(P.g + (size_t)i * DP + j0, a);
@@ -423,16 +428,19 @@ __device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& 
   block_add_u64<NT_SCALES>(ec.grads, &P.cnt->grads);
 }
 
+// reuse = 1 at the start of Phase 5: the gradients Phase 1 stored are still those of the
+// current points except at the reseeded slots
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S) {
-  scales_body<KIND, DP, GM>(P, S, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(NT_SCALES) k_scales(ProbDev P, StepParams S, int reuse) {
+  scales_body<KIND, DP, GM>(P, S, blockIdx.x, gridDim.x, reuse);
 }
 
 // The scale pass of every problem of a group (its own partial-sum grid each).
 template <int KIND, int DP, int GM>
-__global__ void __launch_bounds__(NT_SCALES) k_scales_grp(GroupTab T) {
+__global__ void __launch_bounds__(NT_SCALES) k_scales_grp(GroupTab T, int reuse) {
   const int q = T.blk_prob[blockIdx.x];
-  scales_body<KIND, DP, GM>(T.probs[q], T.sps[q], blockIdx.x - (unsigned)T.blk_first[q], (unsigned)T.blk_count[q]);
+  scales_body<KIND, DP, GM>(T.probs[q], T.sps[q], blockIdx.x - (unsigned)T.blk_first[q], (unsigned)T.blk_count[q],
+                            reuse);
 }
 
 // ------------------------------------------------------------------ Phase 5
@@ -639,7 +647,7 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_direction<DP><<<blocks, NT_OBJ, 0, st>>>(P);
       break;
     case OKID_SCALES:
-      k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S);
+      k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, arg);
       break;
     case OKID_HLC:
       k_hlc<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
@@ -685,26 +693,26 @@ cudaError_t launch_obj(int which, int gm, const ProbDev& P, const StepParams& S,
 // (T maps the launch's blocks to problems: NT_OBJ-thread blocks over the samples, or the
 // problems' scale-pass grids for OKID_SCALES).
 template <int KIND, int DP>
-cudaError_t launch_grp_dp(int which, const GroupTab& T, unsigned blocks, cudaStream_t st) {
+cudaError_t launch_grp_dp(int which, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0) {
   if (blocks == 0) return cudaSuccess;
   switch (which) {
     case OKID_PHASE1: k_phase1_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
     case OKID_HLC: k_hlc_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
     case OKID_ANTI: k_anti_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_OBJ, 0, st>>>(T); break;
-    case OKID_SCALES: k_scales_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_SCALES, 0, st>>>(T); break;
+    case OKID_SCALES: k_scales_grp<KIND, DP, GRAD_ADJOINT><<<blocks, NT_SCALES, 0, st>>>(T, arg); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <int KIND>
-cudaError_t launch_grp(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st) {
+cudaError_t launch_grp(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0) {
   switch (dp) {
-    case 4: return launch_grp_dp<KIND, 4>(which, T, blocks, st);
-    case 8: return launch_grp_dp<KIND, 8>(which, T, blocks, st);
-    case 16: return launch_grp_dp<KIND, 16>(which, T, blocks, st);
-    case 32: return launch_grp_dp<KIND, 32>(which, T, blocks, st);
-    case 64: return launch_grp_dp<KIND, 64>(which, T, blocks, st);
+    case 4: return launch_grp_dp<KIND, 4>(which, T, blocks, st, arg);
+    case 8: return launch_grp_dp<KIND, 8>(which, T, blocks, st, arg);
+    case 16: return launch_grp_dp<KIND, 16>(which, T, blocks, st, arg);
+    case 32: return launch_grp_dp<KIND, 32>(which, T, blocks, st, arg);
+    case 64: return launch_grp_dp<KIND, 64>(which, T, blocks, st, arg);
   }
   return cudaErrorInvalidValue;
 }

@@ -10,8 +10,8 @@ cudaError_t launch_obj_mixdiag(int which, int gm, const ProbDev& P, const StepPa
   return launch_obj<OBJ_MIXTURE_DIAG>(which, gm, P, S, arg, ea, st);
 }
 
-cudaError_t launch_grp_mixdiag(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st) {
-  return launch_grp<OBJ_MIXTURE_DIAG>(which, dp, T, blocks, st);
+cudaError_t launch_grp_mixdiag(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg) {
+  return launch_grp<OBJ_MIXTURE_DIAG>(which, dp, T, blocks, st, arg);
 }
 
 }  // namespace chisao

@@ -10,8 +10,8 @@ cudaError_t launch_obj_mixfull(int which, int gm, const ProbDev& P, const StepPa
   return launch_obj<OBJ_MIXTURE_FULL>(which, gm, P, S, arg, ea, st);
 }
 
-cudaError_t launch_grp_mixfull(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st) {
-  return launch_grp<OBJ_MIXTURE_FULL>(which, dp, T, blocks, st);
+cudaError_t launch_grp_mixfull(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg) {
+  return launch_grp<OBJ_MIXTURE_FULL>(which, dp, T, blocks, st, arg);
 }
 
 }  // namespace chisao
