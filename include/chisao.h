@@ -289,8 +289,9 @@ typedef struct {
  * times under CUDA events, and keeps the fastest.  Every candidate computes the same
  * results bit for bit, and the context's state is saved before and restored after
  * each trial (one device copy of the arena, needing arena-sized free memory), so the
- * tuning changes no result and no trajectory.  A context of one problem has nothing
- * to tune (trials = 0).  Synchronous. */
+ * tuning changes no result and no trajectory.  A context of one problem, or one with
+ * an external objective (whose evaluator need not be capture-safe), is left as it is
+ * (trials = 0).  Synchronous. */
 chisao_status chisao_autotune(chisao_ctx *c, int32_t cycles_per_trial, chisao_tuning *out);
 
 /* Laplace widths of the modes chisao_modes returns (same order).  Phase 3

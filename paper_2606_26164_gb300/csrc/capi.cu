@@ -1001,6 +1001,8 @@ chisao_status chisao_autotune(chisao_ctx* c, int32_t cycles_per_trial, chisao_tu
   out->grouped = (!c->groups.empty() && c->groups_enabled) ? 1 : 0;
   const int nq = (int)c->probs.size();
   if (nq < 2) return CHISAO_OK;
+  for (const ProbHost& ph : c->probs)                 // a caller's evaluator may not be capture-safe
+    if (ph.kind == CHISAO_OBJ_EXTERNAL) return CHISAO_OK;
   void* backup = nullptr;
   if (cudaMalloc(&backup, c->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
