@@ -71,3 +71,14 @@ def test_arena_bytes_and_argument_checks(lib):
     ctx = C.c_void_p()
     assert lib.chisao_create(probs, 1, C.byref(p), None, 0, None, C.byref(ctx)) == CH.ERR_ARG
     assert lib.chisao_step(None) == CH.ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the CUDA library absent the binding raises instead of
+    computing anything another way."""
+    monkeypatch.setattr(CH, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(CH, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        CH.library()
+    with pytest.raises(RuntimeError):
+        CH.default_params()
