@@ -307,3 +307,51 @@ def test_uniform_seed_in_box():
     from scipy import stats
     for a in range(3):
         assert stats.kstest((X[:, a] - lo[a]) / (hi[a] - lo[a]), "uniform").pvalue > 1e-4
+
+
+def _exit_distance(p, u, lo, hi):
+    """Distance from p along the unit direction u to the box boundary (independent of
+    the oracle's helper): the smallest positive step that reaches a face."""
+    with np.errstate(divide="ignore"):
+        up = np.where(u > 0, (hi - p) / u, np.inf)
+        dn = np.where(u < 0, (lo - p) / u, np.inf)
+    return np.minimum(up, dn).min(axis=-1)
+
+
+@pytest.mark.parametrize("n_unfrozen,mode", [(60, "rm"), (2, "gr")])
+def test_reseed_children_uniform_along_their_rays(n_unfrozen, mode):
+    """Sec. 3.2.4 places each child uniformly along its ray inside Theta: the child's
+    distance from its parent (RM) or peak (GR) divided by the ray's exit distance is
+    uniform on [0, 1] (Kolmogorov-Smirnov over 1500 children)."""
+    from scipy import stats
+    d, N, nfree = 3, 1600, 1500
+    p = I.small_mixture(d, 3, N, seed=19)
+    st = M.new_state(p.x0, 4)
+    st.f = -np.arange(N, dtype=np.float64)
+    st.stuck[:] = True
+    st.stuck[N - n_unfrozen:] = False
+    st.removed[:] = False
+    st.removed[1:1 + nfree] = True
+    st.stuck &= ~st.removed
+    x_before = st.x.copy()
+    P = M.Params(seed=23)
+    M.reseed(p, st, P, cycle=1)
+    assert st.last_reseed == (M.RESEED_RM if mode == "rm" else M.RESEED_GR)
+    free = np.arange(1, 1 + nfree)
+    if mode == "rm":
+        unfrozen = np.flatnonzero(~st.stuck)
+        unfrozen = unfrozen[~np.isin(unfrozen, free)]
+        w = PX.words(23, np.arange(nfree), 0, PX.TAG_RM, 1, 0, 0, 0)
+        pick = ((w[:, 0].astype(np.uint64) * np.uint64(unfrozen.size)) >> np.uint64(32)).astype(int)
+        parents = x_before[unfrozen[pick]]
+    else:
+        surv = np.flatnonzero(st.stuck)
+        ranked = surv[np.lexsort((surv, -st.f[surv]))]
+        parents = x_before[ranked[np.arange(nfree) % ranked.size]]
+    delta = st.x[free] - parents
+    t = np.linalg.norm(delta, axis=1)
+    keep = t > 0
+    u = delta[keep] / t[keep, None]
+    ratio = t[keep] / _exit_distance(parents[keep], u, p.lo, p.hi)
+    assert keep.sum() > 0.99 * nfree and (ratio <= 1 + 1e-12).all()
+    assert stats.kstest(ratio, "uniform").pvalue > 1e-3
