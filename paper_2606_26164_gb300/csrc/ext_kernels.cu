@@ -74,13 +74,14 @@ template <int DP>
 __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, ExtBuf E, int t) {
   constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
-  const int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
   const int cur = t & 1;
   const int pending = E.cnt[t];
-  // the grid covers every sample; blocks past the round's list have nothing to count
+  // a grid of at most 16 blocks per SM strides over the round's list (after the first
+  // round the lists are short or empty, so most launches end at once)
   if ((int)(((size_t)blockIdx.x * blockDim.x) / LPS) >= pending) return;
+  const int stride = (int)(((size_t)gridDim.x * blockDim.x) / LPS);
   unsigned long long tr = 0, fl = 0;
-  if (jj < pending) {
+  for (int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS); jj < pending; jj += stride) {
     const int i = E.list[cur][jj];
     const int j0 = V * g.l;
     float x[V], G[V], c[V], Gt[V];
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
     }
     const float F = -P.f[i], Ft = -E.ft[i];
     const float dec = g.sum(dl);
-    if (g.l == 0) tr = 1;
+    if (g.l == 0) tr += 1;
     if (Ft <= F + (float)S.c1 * dec) {
       float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
 #pragma unroll
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
     } else {
       if (g.l == 0) {
         P.hlen[i] = 0;
-        fl = 1;
+        fl += 1;
       }
     }
   }
@@ -324,7 +325,18 @@ static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& 
   const unsigned blocks = (unsigned)(((long long)P.n * LPS + NT_OBJ - 1) / NT_OBJ);
   switch (which) {
     case EXT_DIR: k_ext_dir<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
-    case EXT_ACCEPT: k_ext_accept<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
+    case EXT_ACCEPT: {
+      static int sms = 0;                              // SM count of the device (queried once)
+      if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+          sms = 152;
+      }
+      const unsigned cap = (unsigned)(16 * sms);
+      k_ext_accept<DP><<<blocks < cap ? blocks : cap, NT_OBJ, 0, st>>>(P, S, E, arg);
+      break;
+    }
     case EXT_HLC_POINTS: k_ext_hlc_points<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
     case EXT_HLC_STEP: k_ext_hlc_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E); break;
     case EXT_ANTI_STEP: k_ext_anti_step<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
