@@ -401,7 +401,7 @@ cudaError_t tc_eval_rows(const ProbHost& ph, const float* x, float* f, float* g,
       ph.ext_status = r;
       return cudaErrorUnknown;
     }
-    return cudaSuccess;
+    return launch_zero_padding(g, rows, ph.d, ph.dp, st);   // the evaluator writes d coordinates only
   }
   return tc_launch_mixfull(x, ph.dp, rows, ph.d, ph.K, ph.tc_weights, f, g, ph.dp, &ph.dev.cnt->err, st, idx,
                            count);

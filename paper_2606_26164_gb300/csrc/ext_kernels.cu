@@ -301,6 +301,23 @@ static cudaError_t widths_dp(const ProbDev& P, int rows, float* w, float* cov, c
   return cudaGetLastError();
 }
 
+// A caller's evaluator writes the d coordinates of each gradient row; the padding
+// coordinates d .. dp-1, which the per-sample kernels read as part of their float4
+// rows, are set to zero after it.
+__global__ void k_zero_padding(float* __restrict__ g, long long rows, int d, int dp) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = dp - d;
+  if (t >= rows * w) return;
+  g[(t / w) * dp + d + t % w] = 0.f;
+}
+
+cudaError_t launch_zero_padding(float* g, long long rows, int d, int dp, cudaStream_t st) {
+  if (!g || rows <= 0 || d >= dp) return cudaSuccess;
+  const long long total = rows * (dp - d);
+  k_zero_padding<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, rows, d, dp);
+  return cudaGetLastError();
+}
+
 unsigned obj_blocks(long long n, int dp) {
   return (unsigned)((n * (dp / VL) + NT_OBJ - 1) / NT_OBJ);
 }

@@ -14,6 +14,8 @@ namespace chisao {
 cudaError_t launch_finalize_grp(const GroupTab& T, int members, int dp, int which, cudaStream_t st);
 // Measured FMA throughput (FLOP/s, 2 per FMA) in binary32 (f64 = 0) or binary64.
 cudaError_t measure_fma_peak(int f64, double* flops, cudaStream_t st);
+// Zero the padding coordinates d .. dp-1 of rows x dp gradient rows.
+cudaError_t launch_zero_padding(float* g, long long rows, int d, int dp, cudaStream_t st);
 // Blocks of a per-sample objective kernel over n samples of padded dimension dp.
 unsigned obj_blocks(long long n, int dp);
 // Grouped launches of Phase 1 / 5 / 6 (OKID_PHASE1, OKID_HLC, OKID_ANTI) with exact gradients

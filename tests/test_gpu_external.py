@@ -161,3 +161,29 @@ def test_external_objective_errors_are_reported():
     # an external objective needs exact gradients
     with pytest.raises(CH.ChisaoError):
         U.open_ctx(_external(prob), M.Params(grad_mode=M.GRAD_FD64))
+
+
+def test_external_objectives_in_one_context_match_separate_ones():
+    """Two problems with external objectives in one context (each on its own branch
+    stream, the evaluator called with that stream) give the states of two separate
+    contexts bit for bit."""
+    import torch
+    probs = [_external(PROBS["quad_d7"](300)), _external(PROBS["mix_d5"](400))]
+    P = M.Params(n_osc=3, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=4)
+    U.ensure_built()
+    # leave garbage in the allocator's cache, so the arenas below start dirty: nothing may
+    # depend on memory the library has not written (e.g. gradient padding, d < dp here)
+    junk = torch.full((64 << 20,), float("nan"), device="cuda")
+    del junk
+    together = CH.Chisao(probs, U.lib_params(P))
+    for _ in range(2):
+        together.step()
+    for q in range(2):
+        alone = CH.Chisao(probs[:q + 1], U.lib_params(P))
+        for _ in range(2):
+            alone.step()
+        for fld in (CH.FIELD_X, CH.FIELD_F, CH.FIELD_STUCK):
+            np.testing.assert_array_equal(alone.get(q, fld), together.get(q, fld))
+        alone.close()
+    assert together.autotune()["trials"] == 0             # evaluators need not be capture-safe
+    together.close()
