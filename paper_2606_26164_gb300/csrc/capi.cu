@@ -924,6 +924,7 @@ chisao_status chisao_seed(chisao_ctx* c, int32_t prob, int32_t method) {
   ProbHost& ph = c->probs[prob];
   ProbDev& P = ph.dev;
   const size_t n = (size_t)ph.n;
+  CK(cudaMemsetAsync(P.x, 0, n * ph.dp * sizeof(float), c->stream));     // the padding coordinates
   CK(launch_seed(P, ph.sp, method, c->stream));
   CK(cudaMemsetAsync(P.g, 0, n * ph.dp * sizeof(float), c->stream));
   CK(cudaMemsetAsync(P.f, 0, n * sizeof(float), c->stream));
