@@ -583,8 +583,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       if (h == 0 && live && fine) {
         float* gr = a.g + (size_t)row * a.ldg;
 #pragma unroll
-        for (int e = 0; e < 64; ++e)
-          if (e < a.d) gr[e] = gacc[e] + xch[e * TM + p];
+        for (int e = 0; e < 64; ++e)                    // the row's padding (d <= e < ldg) gets zeros
+          if (e < a.ldg) gr[e] = e < a.d ? gacc[e] + xch[e * TM + p] : 0.f;
       }
     }
   }

@@ -364,3 +364,25 @@ def test_laplace_widths_after_cycles_match_the_mode_curvature():
         lap = np.sqrt(np.diag(np.linalg.inv(-OB.hessian(prob.objective, x))))
         np.testing.assert_allclose(wr, lap, rtol=1e-2)
     model.close()
+
+
+def test_tc_cycle_independent_of_prior_memory_contents():
+    """Tensor-core mode with d < dp (d = 21, dp = 32: padding coordinates in every row):
+    whole cycles give the same bits whether the arena starts clean or holds NaNs left by
+    earlier allocations — nothing reads memory the library has not written."""
+    import torch
+    prob = I.small_full_mixture(21, 6, 1500, seed=33, box=6.0)
+    P = M.Params(n_osc=4, m=6, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=6)
+    out = []
+    for dirty in (False, True):
+        if dirty:
+            junk = torch.full((256 << 20,), float("nan"), device="cuda")
+            del junk
+        model = U.open_ctx(prob, P, grad_mode=CH.GRAD_ADJOINT_TC, use_graph=0)
+        for _ in range(2):
+            model.step()
+        out.append([model.get(0, f).copy() for f in (CH.FIELD_X, CH.FIELD_G, CH.FIELD_F)])
+        model.close()
+        torch.cuda.empty_cache() if not dirty else None
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
