@@ -142,8 +142,11 @@ def test_batched_problems_match_separate_contexts(case):
     bit-identical in a context of six problems and in one of the first q + 1 (same
     problem index, hence the same Philox streams; a single problem runs ungrouped),
     with and without graph capture."""
+    import torch
     probs = I.batched512(n_problems=6, n_scale=0.1, seed=3) if case == "batched" else _mixed_kinds()
     P = M.Params(n_osc=4, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=2)
+    junk = torch.full((64 << 20,), float("nan"), device="cuda")   # arenas below start dirty
+    del junk
     U.ensure_built()
     fields = (CH.FIELD_X, CH.FIELD_F, CH.FIELD_STUCK)
     for use_graph in (1, 0):

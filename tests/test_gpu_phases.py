@@ -383,6 +383,5 @@ def test_tc_cycle_independent_of_prior_memory_contents():
             model.step()
         out.append([model.get(0, f).copy() for f in (CH.FIELD_X, CH.FIELD_G, CH.FIELD_F)])
         model.close()
-        torch.cuda.empty_cache() if not dirty else None
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
