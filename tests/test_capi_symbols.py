@@ -82,3 +82,64 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         CH.library()
     with pytest.raises(RuntimeError):
         CH.default_params()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "chisao.h"
+
+int main(void) {
+  chisao_params p;
+  chisao_problem pr;
+  double lo[3] = {-1, -1, -1}, hi[3] = {1, 1, 1};
+  double center[3] = {0, 0, 0}, Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, lam[3] = {1, 2, 3};
+  float x0[4 * 3] = {0};
+  size_t nb = 0;
+  chisao_status status;
+  chisao_default_params(&p);
+  memset(&pr, 0, sizeof pr);
+  pr.d = 3;
+  pr.n = 4;
+  pr.lo = lo;
+  pr.hi = hi;
+  pr.x0 = x0;
+  pr.objective.kind = CHISAO_OBJ_QUADRATIC;
+  pr.objective.center = center;
+  pr.objective.Q = Q;
+  pr.objective.lam = lam;
+  status = chisao_arena_bytes(&pr, 1, &p, &nb);
+  printf("%d %d %d %zu\n", (int)status, p.n_osc, p.m, nb);
+  p.m = CHISAO_MAX_MEMORY + 1;
+  printf("%d\n", (int)chisao_arena_bytes(&pr, 1, &p, &nb));
+  printf("%d\n", (int)chisao_step(NULL));
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(lib, tmp_path):
+    """The boundary is usable without Python or C++: the header compiles as strict
+    C11 and a C program linked against the library makes host-side calls."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_chisao.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_chisao"
+    libdir = os.path.dirname(CH.LIB_PATH)
+    cmd = [gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           str(src), "-L", libdir, "-lchisao", f"-Wl,-rpath,{libdir}", "-Wl,--allow-shlib-undefined",
+           "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.split()
+    status, n_osc, m, nbytes = (int(v) for v in lines[:4])
+    assert (status, n_osc, m) == (CH.OK, 3, 10)
+    # x, g (4 x 4 floats) and the histories (2 x 4 x 10 x 4 floats) at least
+    assert nbytes >= 4 * (2 * 4 * 4 + 2 * 4 * 10 * 4)
+    assert int(lines[4]) == CH.ERR_ARG and int(lines[5]) == CH.ERR_ARG
