@@ -195,12 +195,28 @@ chisao_status validate_mode(const chisao_problem* pr, const chisao_params* p, st
   return CHISAO_OK;
 }
 
+// The quadratic's symmetric A as the blocks its binary32 product reads (objectives.cuh:
+// sym_times): with L = dp / 4 lanes per sample, lane l at step k = 0 .. L/2 reads the 4 x 4
+// block A[l][(l + k) mod L] as four float4 columns; entry ((k * 4 + c) * L + l) * 4 + v holds
+// A[4 l + v][4 ((l + k) mod L) + c], so the lanes of a group read one contiguous line per
+// (k, c).  The blocks with 0 < k < L/2 also stand for their transposes.
+size_t quad_sym_elems(int dp) { return (size_t)(dp / 8 + 1) * 4 * dp; }
+
+void quad_sym_table(const std::vector<double>& A, int dp, double* out) {
+  const int L = dp / 4;
+  for (int k = 0; k <= L / 2; ++k)
+    for (int c = 0; c < 4; ++c)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 4; ++v)
+          out[(((size_t)k * 4 + c) * L + l) * 4 + v] = A[(size_t)(4 * l + v) * dp + 4 * ((l + k) % L) + c];
+}
+
 size_t obj_elems(const chisao_problem& pr, int dp, size_t* n0, size_t* n1, size_t* n2, size_t* n3) {
   const size_t K = (size_t)pr.objective.n_comp;
   switch (pr.objective.kind) {
     case CHISAO_OBJ_MIXTURE_DIAG: *n0 = K * dp; *n1 = K * dp; *n2 = K; *n3 = 0; break;
     case CHISAO_OBJ_MIXTURE_FULL: *n0 = K * dp; *n1 = K * dp * dp; *n2 = K; *n3 = K * dp * dp; break;
-    case CHISAO_OBJ_QUADRATIC: *n0 = dp; *n1 = (size_t)dp * dp; *n2 = 0; *n3 = 0; break;
+    case CHISAO_OBJ_QUADRATIC: *n0 = dp; *n1 = (size_t)dp * dp; *n2 = quad_sym_elems(dp); *n3 = 0; break;
     default: *n0 = *n1 = *n2 = *n3 = 0; break;                 // benchmark functions: no constants
   }
   return *n0 + *n1 + *n2 + *n3;
@@ -328,6 +344,7 @@ void prepare_objective(const chisao_problem& pr, int dp, std::vector<double>& a0
         for (int i = 0; i < d; ++i) s += o.Q[(size_t)i * d + a] * o.lam[i] * o.Q[(size_t)i * d + b];
         a1[(size_t)a * dp + b] = s;
       }
+    quad_sym_table(a1, dp, a2.data());
   }
 }
 

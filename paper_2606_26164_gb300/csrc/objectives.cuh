@@ -19,7 +19,9 @@
 // group's vector is staged once in shared memory and each block of V values is
 // one broadcast load (FP64: register shuffles from the owner lane), and the
 // matrix row is read as one V-wide vector contiguous across the group (all
-// groups of a warp read the same row, so the load is shared).
+// groups of a warp read the same row, so the load is shared).  The quadratic's
+// binary32 product uses that A is symmetric and reads about half of it
+// (sym_times).
 #pragma once
 #include <type_traits>
 
@@ -201,11 +203,67 @@ __device__ __forceinline__ void rows_timesn(const float* M, int dp, int d, const
   }
 }
 
+// u = A r for a symmetric A (the quadratic) from its packed block table S: lane l
+// owns block l (coordinates 4l .. 4l+3) of L = LPS blocks and at step k reads
+// A[l][b], b = (l + k) mod L, as four float4 columns (table layout: capi.cu,
+// quad_sym_table).  For 0 < k < L/2 the block serves both triangles: lane l adds
+// A[l][b] r_b to its own outputs and hands A[l][b]^T r_l to lane b, which receives
+// it from lane (b - k) mod L in the same step.  The diagonal block (k = 0) and, for
+// L > 1, the block at k = L/2 (read by both partners for themselves) complete the
+// product: L/2 + 1 blocks per lane instead of L, so a quarter fewer bytes cross
+// the L1 data path per evaluation.  Each output is one chain in a fixed order:
+// per step and column, the own term (packed FMA), then the received term.
+template <int LPS>
+__device__ __forceinline__ void sym_times(const float* S, const float (&r)[4], float (&out)[4],
+                                          const Grp<LPS>& g) {
+  constexpr int L = LPS;
+  __shared__ float4 sstage[256];                  // the largest block of the objective kernels
+  sstage[threadIdx.x] = make_float4(r[0], r[1], r[2], r[3]);
+  __syncwarp(g.mask);
+  const float4* grp = sstage + (threadIdx.x - g.l);
+  const float4* tab = reinterpret_cast<const float4*>(S) + g.l;
+  float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  // one step: the block's four columns one at a time (own term with the packed FMA;
+  // with `both` also the transposed term, sent to its owner at once and added to the
+  // receiver's output c after that column's own term)
+  auto step = [&](int k, bool both) {
+    const float4 rb = grp[(g.l + k) & (L - 1)];
+    const float rv[4] = {rb.x, rb.y, rb.z, rb.w};
+    const int src = (g.l - k) & (L - 1);
+    const float4* tk = tab + k * (4 * L);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 a = __ldg(tk + c * L);
+      const float2 r2 = make_float2(rv[c], rv[c]);
+      acc[0] = __ffma2_rn(make_float2(a.x, a.y), r2, acc[0]);
+      acc[1] = __ffma2_rn(make_float2(a.z, a.w), r2, acc[1]);
+      if (both) {
+        const float t = fmaf(a.w, r[3], fmaf(a.z, r[2], fmaf(a.y, r[1], a.x * r[0])));
+        const float rc = __shfl_sync(g.mask, t, src, L);
+        if (c & 1) acc[c >> 1].y += rc; else acc[c >> 1].x += rc;
+      }
+    }
+  };
+  step(0, false);
+#pragma unroll 1
+  for (int k = 1; 2 * k < L; ++k) step(k, true);
+  if (L > 1) step(L / 2, false);
+  __syncwarp(g.mask);                             // the stage is reused by the next product
+  out[0] = acc[0].x;
+  out[1] = acc[0].y;
+  out[2] = acc[1].x;
+  out[3] = acc[1].y;
+}
+
 template <int KIND>
 struct Obj;
 
 // Objectives that evaluate two points of one lane group sharing their parameter loads
-// (binary32 value and gradient; each point's arithmetic exactly that of value_grad).
+// (binary32 value and gradient).  Each point's arithmetic is that of a single
+// evaluation in row order: value_grad's own for the diagonal mixture; for the
+// quadratic, whose value_grad sums the symmetric block product (sym_times) in another
+// order, the row walk of rows_times, so there the results can differ from
+// value_grad's in the last bits.
 template <int KIND>
 struct HasPair : std::false_type {};
 // ... and several points (value_grad_multi<NP>) sharing one pass over them.
@@ -353,7 +411,10 @@ struct Obj<OBJ_QUADRATIC> {
     ldg_vec<T, V>(o.p0 + V * g.l, c);
 #pragma unroll
     for (int v = 0; v < V; ++v) r[v] = x[v] - c[v];
-    rows_times<T, V, LPS>(o.p1, o.dp, o.d, r, u, g);                 // A symmetric: row j = column j
+    if constexpr (std::is_same<T, float>::value && V == 4)
+      sym_times<LPS>(o.p2, r, u, g);                                  // half the off-diagonal blocks
+    else
+      rows_times<T, V, LPS>(o.p1, o.dp, o.d, r, u, g);               // A symmetric: row j = column j
     T acc = T(0);
 #pragma unroll
     for (int v = 0; v < V; ++v) acc = fma(r[v], u[v], acc);
