@@ -28,6 +28,10 @@ PROBS = {
     "full_d33": lambda n: I.small_full_mixture(33, 6, n, seed=6),
     "quad_d7": lambda n: I.small_quadratic(7, n, seed=7),
     "quad_d64": lambda n: I.small_quadratic(64, n, seed=8, cond=1e4),
+    # the symmetric block product at every lane count: 1, 4 and 8 lanes per sample
+    "quad_d3": lambda n: I.small_quadratic(3, n, seed=9),
+    "quad_d12": lambda n: I.small_quadratic(12, n, seed=10, cond=1e3),
+    "quad_d27": lambda n: I.small_quadratic(27, n, seed=11, cond=1e3),
 }
 U32 = 2.0 ** -24
 
@@ -130,7 +134,7 @@ def test_fd64_gradient(name):
     model.close()
 
 
-@pytest.mark.parametrize("name", ["mix_d2", "mix_d16", "quad_d7"])
+@pytest.mark.parametrize("name", ["mix_d2", "mix_d16", "quad_d7", "quad_d27"])
 def test_fd32_gradient(name):
     prob = PROBS[name](517)
     P = M.Params(grad_mode=M.GRAD_FD32)
@@ -190,7 +194,7 @@ def _armijo_margin(prob, st, P, Pd, alpha):
 
 
 @pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64, M.GRAD_FD32])
-@pytest.mark.parametrize("name", ["mix_d5", "mix_d16", "quad_d7", "full_d3"])
+@pytest.mark.parametrize("name", ["mix_d5", "mix_d16", "quad_d7", "quad_d12", "full_d3"])
 def test_lbfgs_iteration(name, mode):
     """One Phase-1 iteration (direction, Armijo search, new gradient, history
     push) from the same binary32 state on both sides."""
