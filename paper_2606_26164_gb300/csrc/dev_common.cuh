@@ -42,7 +42,8 @@ constexpr unsigned TAG_RM = 1, TAG_RM_DIR = 2, TAG_GR_MAT = 3, TAG_GR_T = 4,
 //   MIXTURE_DIAG: p0 = mu [K][dp], p1 = 1/sigma^2 [K][dp], p2 = c [K]
 //   MIXTURE_FULL: p0 = mu [K][dp], p1 = L^-1 [K][dp][dp] row-major,
 //                 p3 = (L^-1)^T [K][dp][dp], p2 = c [K]
-//   QUADRATIC:    p0 = center [dp], p1 = A = Q^T diag(lam) Q [dp][dp]
+//   QUADRATIC:    p0 = center [dp], p1 = A = Q^T diag(lam) Q [dp][dp],
+//                 p2 = A's blocks packed for the symmetric product [(dp/8 + 1) * 4 * dp]
 // with c_k = log w_k - log|L_k| - (d/2) log(2 pi).
 template <typename T>
 struct ObjParams {
