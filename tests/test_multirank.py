@@ -48,3 +48,27 @@ def test_two_ranks_over_gloo():
     assert res[0][0] == res[1][0] == 2.5
     assert res[0][1] == res[1][1] == 1000 * 4 * 2 / 2.5
     assert res[1][2]
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """Rank 0 of the reference arm prints one JSON line with the bench's metric keys,
+    "impl": "reference", a cpu_baseline that describes the run and an e2e with no
+    host-device traffic (the oracle runs on the host)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        workload, grad, steps, warmup = "mixture4_d2", "adjoint", 2, 1
+    bench.reference_arm(Args, 1, 0)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0 and d["higher_is_better"]
+    assert d["config"]["workload"] == "mixture4_d2"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
