@@ -219,3 +219,15 @@ def test_underflowing_descent_product_keeps_the_history():
     st2.f = M.evaluate(prob, st2.x)
     M.lbfgs_iterations(prob, st2, P, 1, fresh_gradient=False)
     assert st2.hlen[0] == 0
+
+
+@pytest.mark.parametrize("eps,kept", [(2e-10, True), (0.5e-10, False), (-0.5e-10, False), (-1.0, False)])
+def test_curvature_pair_threshold(eps, kept):
+    """The reading of the curvature skip: a pair is kept iff s^T y > 1e-10 |s| |y|,
+    checked on both sides of the threshold and for slightly negative curvature."""
+    P = M.Params(m=3)
+    st = M.new_state(np.zeros((1, 2)), P.m)
+    s = np.array([[1.0, 0.0]])
+    y = np.array([[eps, 1.0]])                       # s^T y = eps, |s| |y| = sqrt(1 + eps^2)
+    ok = M.push_pair(st, np.array([0]), s, y, P)
+    assert bool(ok[0]) == kept and st.hlen[0] == int(kept)

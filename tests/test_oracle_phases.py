@@ -355,3 +355,84 @@ def test_reseed_children_uniform_along_their_rays(n_unfrozen, mode):
     ratio = t[keep] / _exit_distance(parents[keep], u, p.lo, p.hi)
     assert keep.sum() > 0.99 * nfree and (ratio <= 1 + 1e-12).all()
     assert stats.kstest(ratio, "uniform").pvalue > 1e-3
+
+
+# --------------------------------------------------------------------- boundaries of the readings
+
+@pytest.mark.parametrize("n_unfrozen,mode", [(5, M.RESEED_RM), (4, M.RESEED_GR)])
+def test_repulse_monkey_needs_at_least_five_unfrozen(n_unfrozen, mode):
+    """Sec. 3.2.4 reading: Repulse Monkey when 5 or more samples are unfrozen,
+    Golden Rooster below that -- the boundary case itself."""
+    p, st = _reseed_setup(n_unfrozen=n_unfrozen)
+    M.reseed(p, st, M.Params(seed=3), cycle=1)
+    assert st.last_reseed == mode
+
+
+def test_golden_rooster_sign_alternates_after_every_peak_and_axis():
+    """With S survivors in d dimensions, slots r and r + S d use the same peak and
+    the same column of Q with opposite signs: their children leave the peak in
+    opposite directions along one line (S = 3, d = 2, 9 free slots)."""
+    p, st = _reseed_setup(n_unfrozen=2, d=2, N=14)
+    x_before = st.x.copy()
+    surv = np.flatnonzero(st.stuck)
+    S, d = surv.size, 2
+    assert S * d < 9
+    M.reseed(p, st, M.Params(seed=8), cycle=1)
+    assert st.last_reseed == M.RESEED_GR
+    ranked = surv[np.lexsort((surv, -st.f[surv]))]
+    for r in range(9 - S * d):
+        peak = x_before[ranked[r % S]]
+        a = st.x[1 + r] - peak
+        b = st.x[1 + r + S * d] - peak
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert cos == pytest.approx(-1.0, abs=1e-12), (r, cos)
+
+
+def test_hlc_draws_fresh_perturbations_every_step():
+    """Eq. 5 averages over new perturbations at every step.  On a quadratic each
+    step is x + alpha (grad f(x) + sigma H zbar_t) (Appendix B), so the random
+    parts alpha sigma H zbar_t of two consecutive steps are uncorrelated across
+    samples when the draws are fresh (and identical when they are reused)."""
+    N, d = 2000, 3
+    p, st = _quad_state(N=N, d=d)
+    A = p.objective.arrays["Q"].T @ np.diag(p.objective.arrays["lam"]) @ p.objective.arrays["Q"]
+    c = p.objective.arrays["center"]
+
+    def grad(x):
+        return -2.0 * (x - c) @ A
+
+    one = M.State(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.__dict__.items()})
+    x0 = st.x.copy()
+    s1, a1 = M.hlc(p, one, M.Params(n_cloud=1, M=8, grad_mode=M.GRAD_ADJOINT, seed=4), cycle=1)
+    s2, a2 = M.hlc(p, st, M.Params(n_cloud=2, M=8, grad_mode=M.GRAD_ADJOINT, seed=4), cycle=1)
+    assert (s1, a1) == (s2, a2)
+    x1, x2 = one.x, st.x
+    r1 = (x1 - x0 - a1 * grad(x0)).ravel()
+    r2 = (x2 - x1 - a2 * grad(x1)).ravel()
+    assert np.abs(r1).max() > 0 and np.abs(r2).max() > 0
+    corr = np.corrcoef(r1, r2)[0, 1]
+    assert abs(corr) < 0.1, corr
+
+
+def test_anti_convergence_velocity_zeroed_where_the_box_stopped_it():
+    """Eq. 6 with the box: the velocity of a clamped coordinate is zeroed, so when
+    the gradient there reverses the next step starts from rest.  1-D mixture of unit
+    components at 5 and 14 (outside the box [-10, 10]), alpha = 2, mu = 0.9, from
+    x = 7: step 1 overshoots past 10 and is clamped; at 10 the outside component
+    dominates, and step 2 is -alpha f'(10) with no momentum term."""
+    w = np.array([0.5, 0.5])
+    mu_k = np.array([5.0, 14.0])
+    obj = I.Objective(1, 1, {"weights": w, "means": mu_k[:, None], "sigmas": np.ones((2, 1))})
+    p = I.Problem(1, 1, np.array([-10.0]), np.array([10.0]), obj, np.zeros((1, 1), np.float32), 1e-6, 1.0)
+    st = M.new_state(np.array([[7.0]]), 2)
+    M.anti_converge(p, st, M.Params(n_anti=2, mu=0.9, alpha=2.0, grad_mode=M.GRAD_ADJOINT))
+    # f'(x) = sum_k r_k (mu_k - x), r the responsibilities (equal weights and widths)
+    lc = -0.5 * (10.0 - mu_k) ** 2
+    r = np.exp(lc - lc.max())
+    r /= r.sum()
+    fp10 = float(r @ (mu_k - 10.0))
+    lc7 = -0.5 * (7.0 - mu_k) ** 2
+    r7 = np.exp(lc7 - lc7.max())
+    r7 /= r7.sum()
+    assert 7.0 - 2.0 * float(r7 @ (mu_k - 7.0)) > 10.0      # step 1 leaves the box
+    np.testing.assert_allclose(st.x[0, 0], 10.0 - 2.0 * fp10, rtol=1e-12)
