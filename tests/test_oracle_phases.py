@@ -436,3 +436,18 @@ def test_anti_convergence_velocity_zeroed_where_the_box_stopped_it():
     r7 /= r7.sum()
     assert 7.0 - 2.0 * float(r7 @ (mu_k - 7.0)) > 10.0      # step 1 leaves the box
     np.testing.assert_allclose(st.x[0, 0], 10.0 - 2.0 * fp10, rtol=1e-12)
+
+
+def test_carry_tiger_enumeration_hand_case_d2():
+    """The anchor enumeration of the Carry Tiger reading, by hand for d = 2: sample i
+    has class i mod 3 and counter j = i div 3; face slots take face q = j mod 2d, axis
+    q div 2, sign - for even q and + for odd q; edge slots leave axis j mod d free."""
+    from oracle import seeding as SD
+    E, _ = SD.carry_tiger_directions(2, 12, seed=5)
+    faces = E[0::3]
+    np.testing.assert_array_equal(faces, [[-1, 0], [1, 0], [0, -1], [0, 1]])
+    edges = E[1::3]
+    free = [0, 1, 0, 1]
+    for e, a in zip(edges, free):
+        assert e[a] == 0 and abs(e[1 - a]) == 1
+    assert np.all(np.abs(E[2::3]) == 1)
