@@ -12,7 +12,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# name -> [(exact text in oracle/method.py, replacement), ...]
+# name -> [(exact text, replacement), ...] in oracle/method.py, or in the module the
+# name starts with ("objectives.py: ...")
 MUTANTS = {
     "momentum sign (Eq. 6)": [("V = P.mu * V - alpha * G", "V = P.mu * V + alpha * G")],
     "dedup distance <= instead of < (Eq. 4)": [("close = D < eps", "close = D <= eps")],
@@ -42,6 +43,15 @@ MUTANTS = {
     "rho = s^T y instead of its reciprocal": [("st.rho[j, 0] = 1.0 / sy[ok]", "st.rho[j, 0] = sy[ok]")],
     "trial points not projected onto the box": [
         ("Xt = np.clip(X[idx] + a[:, None] * Pd[idx], lo, hi)", "Xt = X[idx] + a[:, None] * Pd[idx]")],
+    "objectives.py: diagonal score without the square of sigma": [
+        ("score = -R / (sig[None] ** 2)", "score = -R / sig[None]")],
+    "objectives.py: Hessian without the mean-score term": [("return H - np.outer(gbar, gbar)", "return H")],
+    "seeding.py: Carry Tiger face signs swapped": [
+        ("np.where(q % 2 == 1, 1.0, -1.0)", "np.where(q % 2 == 1, -1.0, 1.0)")],
+    "seeding.py: Carry Tiger edge frees the next axis": [
+        ("E[edge, j[edge] % d] = 0.0", "E[edge, (j[edge] + 1) % d] = 0.0")],
+    "benchmarks.py: Trid neighbour term sign": [
+        ("+ (X[:, 1:] * X[:, :-1]).sum(axis=1)", "- (X[:, 1:] * X[:, :-1]).sum(axis=1)")],
 }
 
 
@@ -55,8 +65,9 @@ def _scratch_copy(dst):
         shutil.copy(os.path.join(ROOT, "paper_2606_26164_gb300", f), pkg)
 
 
-def _plant(dst, edits):
-    path = os.path.join(dst, "oracle", "method.py")
+def _plant(dst, name, edits):
+    module = name.split(": ")[0] if ": " in name else "method.py"
+    path = os.path.join(dst, "oracle", module)
     src = open(path).read()
     for old, new in edits:
         assert src.count(old) == 1, f"mutation site not unique or missing: {old!r}"
@@ -83,6 +94,6 @@ def test_unmutated_copy_passes(tmp_path):
 @pytest.mark.parametrize("name", list(MUTANTS))
 def test_each_planted_mistake_fails_a_pin(name, tmp_path):
     _scratch_copy(str(tmp_path))
-    _plant(str(tmp_path), MUTANTS[name])
+    _plant(str(tmp_path), name, MUTANTS[name])
     rc, out = _pin_suite(str(tmp_path))
     assert rc == 1, f"mutant survived the pins ({name}):\n{out}"
