@@ -157,3 +157,18 @@ def test_noisy_evaluation_adds_scaled_draw():
     X = p.x0.astype(np.float64)
     f = M.evaluate(p, X, seed=9)
     np.testing.assert_allclose(f - OB.value(p.objective, X), 0.5 * PX.point_noise(9, 0, X), rtol=1e-9, atol=1e-9)
+
+
+def test_normals_of_one_block_are_independent():
+    """The four normals of one Philox block come from two Box-Muller pairs on
+    disjoint words, so the angle of (z0, z1) carries no information about the
+    radius of (z2, z3) (and vice versa): rank correlations near zero.  A generator
+    that reused a word across the pairs would make them functions of each other."""
+    from scipy import stats
+    z = PX.normal_rows(21, np.arange(20000), 4, PX.TAG_HLC, 1, 0, 0, 0)
+    ang01 = np.mod(np.arctan2(z[:, 1], z[:, 0]), 2 * np.pi)
+    ang23 = np.mod(np.arctan2(z[:, 3], z[:, 2]), 2 * np.pi)
+    rad01 = z[:, 0] ** 2 + z[:, 1] ** 2
+    rad23 = z[:, 2] ** 2 + z[:, 3] ** 2
+    for a, b in ((ang01, rad23), (ang23, rad01), (ang01, ang23), (rad01, rad23)):
+        assert abs(stats.spearmanr(a, b)[0]) < 0.05
