@@ -50,6 +50,11 @@ MUTANTS = {
         ("np.where(q % 2 == 1, 1.0, -1.0)", "np.where(q % 2 == 1, -1.0, 1.0)")],
     "seeding.py: Carry Tiger edge frees the next axis": [
         ("E[edge, j[edge] % d] = 0.0", "E[edge, (j[edge] + 1) % d] = 0.0")],
+    "philox.py: the two Box-Muller pairs share a word": [
+        ("a01 = 2.0 * np.pi * u[..., 1]", "a01 = 2.0 * np.pi * u[..., 2]")],
+    "philox.py: Philox multiplier": [("MUL0, MUL1 = 0xD2511F53, 0xCD9E8D57", "MUL0, MUL1 = 0xD2511F53, 0xCD9E8D55")],
+    "modes.py: quality gate on delta instead of log delta": [
+        ("if c[1] >= fmax + np.log(delta)]", "if c[1] >= fmax + delta]")],
     "benchmarks.py: Trid neighbour term sign": [
         ("+ (X[:, 1:] * X[:, :-1]).sum(axis=1)", "- (X[:, 1:] * X[:, :-1]).sum(axis=1)")],
 }
