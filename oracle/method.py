@@ -540,6 +540,29 @@ def cycle(prob, st: State, P: Params, prob_index: int = 0, last: Optional[bool] 
     return st
 
 
+def refine(prob, st: State, P: Params, n_refine: int):
+    """Final refinement of the returned modes when the cycles ran on a lower-precision
+    objective (the tensor-core mixture of BF16-rounded factors).  The paper has no such
+    step; its reading: after the last cycle's Phase 3, each survivor (stuck and not
+    removed) takes n_refine more Phase 1 iterations (Sec. 3.2.1, Eq. 2) on `prob`'s
+    exact objective, starting from a fresh value and gradient at its point and keeping
+    its L-BFGS history (Sec. 3.2.3 preserves it).  No other sample changes, and no stick
+    test or deduplication follows: the refined survivors are the mode set."""
+    idx = np.flatnonzero(st.stuck & ~st.removed)
+    if n_refine <= 0 or idx.size == 0:
+        return st
+    sub = State(x=st.x[idx].copy(), f=st.f[idx].copy(), g=st.g[idx].copy(), S=st.S[idx].copy(),
+                Y=st.Y[idx].copy(), rho=st.rho[idx].copy(), hlen=st.hlen[idx].copy(),
+                stuck=np.ones(idx.size, bool), removed=np.zeros(idx.size, bool))
+    lbfgs_iterations(prob, sub, P, n_refine, fresh_gradient=True)
+    st.x[idx], st.f[idx], st.g[idx] = sub.x, sub.f, sub.g
+    st.S[idx], st.Y[idx], st.rho[idx], st.hlen[idx] = sub.S, sub.Y, sub.rho, sub.hlen
+    st.evals += sub.evals
+    st.grads += sub.grads
+    st.ls_fail += sub.ls_fail
+    return st
+
+
 def run(prob, P: Params, prob_index: int = 0):
     st = new_state(prob.x0, P.m)
     for _ in range(P.n_osc):

@@ -231,3 +231,57 @@ def test_curvature_pair_threshold(eps, kept):
     y = np.array([[eps, 1.0]])                       # s^T y = eps, |s| |y| = sqrt(1 + eps^2)
     ok = M.push_pair(st, np.array([0]), s, y, P)
     assert bool(ok[0]) == kept and st.hlen[0] == int(kept)
+
+
+def _conjugate_pairs(rng, B, d):
+    S = []
+    for v in rng.standard_normal((d, d)):                 # B-orthogonalise (Gram-Schmidt)
+        for s in S:
+            v = v - (s @ B @ v) / (s @ B @ s) * s
+        S.append(v)
+    return [(s, B @ s) for s in S[::-1]]
+
+
+def test_refine_with_kept_history_takes_the_newton_step():
+    """Final refinement (reading of the FP32 polish of tensor-core modes): a survivor of
+    the quadratic f = -(x - c)^T A (x - c) whose kept history holds d A-conjugate pairs
+    (y = 2 A s for F = -f) has H = (2A)^-1, so one refinement iteration is the Newton
+    step and lands on c (alpha = 1 passes Armijo).  A cleared history would take a
+    steepest-descent step instead; a non-survivor or a removed sample must not move."""
+    d = 4
+    rng = np.random.default_rng(21)
+    prob = I.small_quadratic(d, 3, seed=5, cond=50.0)
+    A = prob.objective.arrays["Q"].T @ np.diag(prob.objective.arrays["lam"]) @ prob.objective.arrays["Q"]
+    c = prob.objective.arrays["center"]
+    st = _state_with_pairs([_conjugate_pairs(rng, 2.0 * A, d)] * 3, d, d)
+    st.x = c + rng.uniform(-1.0, 1.0, (3, d))
+    x_before = st.x.copy()
+    st.stuck = np.array([True, False, True])
+    st.removed = np.array([False, False, True])
+    st.stuck &= ~st.removed
+    M.refine(prob, st, M.Params(m=d, grad_mode=M.GRAD_ADJOINT), 1)
+    np.testing.assert_allclose(st.x[0], c, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(st.x[1:], x_before[1:])
+    assert st.hlen[0] == d and st.hlen[1] == d
+
+
+def test_refine_reaches_a_stationary_point_of_the_exact_objective():
+    """Cycles on the tensor-core objective (BF16-rounded precision factors) stop at that
+    objective's modes; refinement on the exact mixture moves each survivor to a point
+    where the exact gradient vanishes (the definition of a mode), starting from the
+    kept history of the lower-precision run."""
+    from oracle import objectives as OB
+    prob = I.small_full_mixture(6, 3, 40, seed=3, box=4.0)
+    tprob = I.Problem(prob.d, prob.n, prob.lo, prob.hi, OB.tensor_core_objective(prob.objective), prob.x0,
+                      prob.eps_grad, prob.sigma_mode)
+    P = M.Params(m=6, grad_mode=M.GRAD_ADJOINT, n_conv=200, eps_grad=1e-6)
+    st = M.new_state(prob.x0, P.m)
+    M.lbfgs_iterations(tprob, st, P, 200)
+    # the split input x_hi + x_lo (relative residual 2^-17) leaves a gradient floor near 1e-5
+    st.stuck = np.abs(st.g).max(axis=1) < 1e-4
+    assert st.stuck.sum() >= 5
+    g_exact = np.abs(OB.grad(prob.objective, st.x[st.stuck])).max(axis=1)
+    assert g_exact.max() > 1e-6                         # not yet modes of the exact objective
+    M.refine(prob, st, P, 50)
+    g_after = np.abs(OB.grad(prob.objective, st.x[st.stuck])).max(axis=1)
+    assert g_after.max() < 1e-9

@@ -43,6 +43,14 @@ MUTANTS = {
     "rho = s^T y instead of its reciprocal": [("st.rho[j, 0] = 1.0 / sy[ok]", "st.rho[j, 0] = sy[ok]")],
     "trial points not projected onto the box": [
         ("Xt = np.clip(X[idx] + a[:, None] * Pd[idx], lo, hi)", "Xt = X[idx] + a[:, None] * Pd[idx]")],
+    "refinement clears the kept history": [
+        ("lbfgs_iterations(prob, sub, P, n_refine, fresh_gradient=True)",
+         "sub.hlen[:] = 0\n    lbfgs_iterations(prob, sub, P, n_refine, fresh_gradient=True)")],
+    "refinement moves every sample, not only the survivors": [
+        ("idx = np.flatnonzero(st.stuck & ~st.removed)", "idx = np.arange(st.x.shape[0])")],
+    "refinement keeps the stale gradient of the lower-precision objective": [
+        ("lbfgs_iterations(prob, sub, P, n_refine, fresh_gradient=True)",
+         "lbfgs_iterations(prob, sub, P, n_refine, fresh_gradient=False)")],
     "objectives.py: diagonal score without the square of sigma": [
         ("score = -R / (sig[None] ** 2)", "score = -R / sig[None]")],
     "objectives.py: Hessian without the mean-score term": [("return H - np.outer(gbar, gbar)", "return H")],
