@@ -30,7 +30,8 @@ EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chis
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
            "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
-           "chisao_widths", "chisao_selftest_wait", "chisao_autotune", "chisao_measure_fma_peak"]
+           "chisao_widths", "chisao_selftest_wait", "chisao_autotune", "chisao_measure_fma_peak", "chisao_init",
+           "chisao_stats"]
 
 
 class CParams(C.Structure):
@@ -156,6 +157,8 @@ def library() -> C.CDLL:
         lib.chisao_arena_bytes.argtypes = [C.POINTER(CProblem), C.c_int32, C.POINTER(CParams), C.POINTER(C.c_size_t)]
         lib.chisao_create.argtypes = [C.POINTER(CProblem), C.c_int32, C.POINTER(CParams), vp, C.c_size_t, vp,
                                       C.POINTER(vp)]
+        lib.chisao_init.argtypes = [C.POINTER(CProblem), C.c_int32, C.POINTER(CParams), vp, C.POINTER(vp)]
+        lib.chisao_stats.argtypes = [vp, C.c_int32, C.POINTER(CCounters)]
         lib.chisao_step.argtypes = [vp]
         lib.chisao_load_population.argtypes = [vp, C.c_int32, C.POINTER(C.c_float)]
         lib.chisao_seed.argtypes = [vp, C.c_int32, C.c_int32]
@@ -344,9 +347,12 @@ class Chisao:
         return {name: getattr(c, name) for name, _ in CCounters._fields_}
 
     def eval(self, prob: int, x, grad_mode: int = GRAD_ADJOINT, want_grad: bool = True):
-        """f (and grad f) at device points x (a CUDA float32 tensor [n, d])."""
+        """f (and grad f) at device points x (a CUDA float32 tensor [n, d], d = the
+        problem's dimension; non-contiguous inputs are copied).  Raises ChisaoError,
+        launching nothing, for any other dtype, device or shape."""
         import torch
-        x = x.contiguous()
+        self._check_points(prob, x)
+        x = x.detach().contiguous()
         n = x.shape[0]
         f = torch.empty(n, dtype=torch.float32, device=x.device)
         g = torch.empty_like(x) if want_grad else None
@@ -355,6 +361,21 @@ class Chisao:
                                           g.data_ptr() if g is not None else None, grad_mode), "chisao_eval")
         torch.cuda.current_stream().wait_stream(self._stream)
         return f, g
+
+    def _check_points(self, prob: int, x):
+        """The kernels read and write rows of exactly d binary32 values on the device."""
+        import torch
+        if not 0 <= prob < len(self.problems):
+            raise ChisaoError(f"problem index {prob} out of range")
+        d = self.problems[prob].d
+        if not isinstance(x, torch.Tensor):
+            raise ChisaoError("points must be a torch tensor")
+        if not x.is_cuda:
+            raise ChisaoError("points must be on the CUDA device")
+        if x.dtype != torch.float32:
+            raise ChisaoError(f"points must be float32, got {x.dtype}")
+        if x.dim() != 2 or x.shape[1] != d:
+            raise ChisaoError(f"points must have shape [n, {d}], got {tuple(x.shape)}")
 
     def synchronize(self):
         self._stream.synchronize()
@@ -418,24 +439,38 @@ def pack_bits(mask: np.ndarray) -> np.ndarray:
     return np.packbits(b, bitorder="little").view(np.uint32)
 
 
+def _objective_function():
+    """The torch.autograd.Function over the library's objective (built once)."""
+    import torch
+
+    class _ChisaoObjectiveFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, model, prob, xin):
+            f, g = model.eval(prob, xin, GRAD_ADJOINT, want_grad=True)
+            ctx.save_for_backward(g)
+            return f
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return None, None, gout[:, None] * g
+
+    return _ChisaoObjectiveFn
+
+
+_OBJECTIVE_FN = None
+
+
 class ChisaoObjective:
-    """torch.autograd.Function over the library's objective: forward = value,
-    backward = the hand-written adjoint (exact gradient) times grad_output."""
+    """torch.autograd.Function over the library's objective: forward = the value
+    f(x) of problem `prob` at the rows of x ([n, d] float32 on the device), backward =
+    grad_output times the hand-written adjoint gradient (exact; the analytic-gradient
+    alternative to finite differences of Sec. 3.1), both from one chisao_eval call."""
 
     @staticmethod
     def apply(model: Chisao, prob: int, x):
-        import torch
-
-        class _Fn(torch.autograd.Function):
-            @staticmethod
-            def forward(ctx, xin):
-                f, g = model.eval(prob, xin.detach(), GRAD_ADJOINT, want_grad=True)
-                ctx.save_for_backward(g)
-                return f
-
-            @staticmethod
-            def backward(ctx, gout):
-                (g,) = ctx.saved_tensors
-                return gout[:, None] * g
-
-        return _Fn.apply(x)
+        global _OBJECTIVE_FN
+        if _OBJECTIVE_FN is None:
+            _OBJECTIVE_FN = _objective_function()
+        model._check_points(prob, x)
+        return _OBJECTIVE_FN.apply(model, prob, x)

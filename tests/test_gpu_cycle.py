@@ -180,24 +180,47 @@ def test_determinism_and_graph_equivalence():
 
 
 def test_full_size_quadratic_step_properties():
-    """quadratic_d64 at N=65536 in the benchmark's launch configuration: Phase 1
-    never decreases f; sampled rows match the oracle's Phase 1 on the same rows
-    (Phase 1 is independent per sample) to 1e-3 of their distance moved."""
+    """quadratic_d64 at N = 65536 in the benchmark's launch configuration (the Phase 1
+    kernel over every sample, condition 1e4).  Three iterations, each launched on the
+    whole population from the state the previous one left; on 512 sampled rows every
+    iteration matches the oracle's one iteration from the same binary32 state to 1e-5
+    of the step (rows where binary32 and FP64 decide an Armijo test differently take
+    a power-of-two multiple of the oracle's step, at most 2 %).  Then the fused launch
+    of the benchmark (n_conv = 18 iterations in one kernel): f never decreases, f and
+    the gradient it stores are the objective's at the point it stores (1e-5; the
+    gradient at the objective parity bound), every stored pair is curved with
+    rho = 1 / s^T y; and a full non-final cycle runs."""
+    from test_gpu_kernels import assert_grad_close, grad_term_scale, value_term_scale
     prob = I.quadratic_d64()
     P = M.Params(n_osc=1000, m=10, eps_grad=0.05, grad_mode=M.GRAD_ADJOINT, seed=3)
     model = U.open_ctx(prob, P)
-    x0 = model.get(0, CH.FIELD_X)[:, :64].astype(np.float64)
-    f0 = OB.value(prob.objective, x0)
-    model.run_phase(0, CH.PHASE_LBFGS, 3)
+    rows = np.sort(np.random.default_rng(0).choice(prob.n, 512, replace=False))
+    sub = I.Problem(64, rows.size, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad,
+                    prob.sigma_mode)
+    st = U.read_state(model, prob, P.m, rows=rows)
+    for it in range(3):
+        model.run_phase(0, CH.PHASE_LBFGS, 1 if it == 0 else -1)
+        got = U.read_state(model, prob, P.m, rows=rows)
+        ref = M.State(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.__dict__.items()})
+        M.lbfgs_iterations(sub, ref, P, 1, fresh_gradient=(it == 0))
+        U.assert_phase1_step(st, got, ref)
+        if it > 0:                                    # the first launch evaluates f itself
+            assert np.all(got.f >= st.f - 1e-6 * np.abs(st.f))
+        st = got
+    x_before = model.get(0, CH.FIELD_X)[:, :64].astype(np.float64)
+    f_before = model.get(0, CH.FIELD_F).astype(np.float64)
+    model.run_phase(0, CH.PHASE_LBFGS, -P.n_conv_for(64))
     st = U.read_state(model, prob, P.m)
-    assert np.all(st.f >= f0.astype(np.float32) - 1e-6 * np.abs(f0))
-    rows = np.random.default_rng(0).choice(prob.n, 48, replace=False)
-    sub = I.Problem(64, 48, prob.lo, prob.hi, prob.objective, prob.x0[rows], prob.eps_grad, prob.sigma_mode)
-    ref = M.new_state(x0[rows], P.m)
-    M.lbfgs_iterations(sub, ref, P, 3)
-    move = np.abs(ref.x - x0[rows]).max(axis=1)
-    err = np.abs(st.x[rows] - ref.x).max(axis=1)
-    assert np.median(err / move) <= 1e-3
+    assert np.all(st.f >= f_before - 1e-6 * np.abs(f_before))
+    assert np.any(np.abs(st.x - x_before).max(axis=1) > 0)
+    f_ref = OB.value(prob.objective, st.x)
+    assert np.all(np.abs(st.f - f_ref) <= 1e-5 * (value_term_scale(prob, st.x) + 1.0))
+    assert_grad_close(st.g[rows], OB.grad(prob.objective, st.x[rows]), grad_term_scale(prob, st.x[rows]), 1e-5)
+    for k in range(P.m):
+        live = st.hlen > k
+        sy = np.einsum("nd,nd->n", st.S[live, k], st.Y[live, k])
+        assert np.all(sy > 0)
+        np.testing.assert_allclose(st.rho[live, k], 1.0 / sy, rtol=4 * 2.0 ** -24)
     model.step()                                      # a full non-final cycle runs
     c = model.counters(0)
     assert c["cycles"] == 1 and c["evals"] > 0 and c["ls_fail"] <= c["ls_trials"]
