@@ -223,16 +223,29 @@ void chisao_default_params(chisao_params *p);
 chisao_status chisao_arena_bytes(const chisao_problem *probs, int32_t n_probs,
                                  const chisao_params *params, size_t *bytes);
 
-/* Create a context: validate, carve the device state out of `arena` (device,
- * >= chisao_arena_bytes, 256-byte aligned; it stays owned by the caller and
- * must outlive the context) or, when arena is NULL, allocate it with
- * cudaMalloc; copy objectives and initial populations; bind `cuda_stream`
- * (a cudaStream_t, NULL for the legacy default stream).  *out receives the
- * context.  Synchronous. */
+/* Create a context.  Its inputs are those of Algorithm 1: the objective f
+ * over the bounded domain Theta (Sec. 3.1, the problem statement), an initial
+ * population that the caller provides (Sec. 3.1: arbitrary), and the
+ * hyperparameters of Table 1 (chisao_params); several independent problems may
+ * share one context.  Validates everything (CHISAO_ERR_ARG, with a message),
+ * carves the device state out of `arena` (device, >= chisao_arena_bytes,
+ * 256-byte aligned; it stays owned by the caller and must outlive the
+ * context) or, when arena is NULL, allocates it with cudaMalloc
+ * (CHISAO_ERR_OOM on failure); copies objectives and initial populations;
+ * binds `cuda_stream` (a cudaStream_t, NULL for the legacy default stream).
+ * *out receives the context (NULL on failure).  Synchronous. */
 chisao_status chisao_create(const chisao_problem *probs, int32_t n_probs,
                             const chisao_params *params, void *arena,
                             size_t arena_bytes, void *cuda_stream,
                             chisao_ctx **out);
+
+/* chisao_create with the library allocating its own device memory: the
+ * initialisation of Algorithm 1 (the problems of Sec. 3.1, the population
+ * given by the caller, the Table 1 parameters) under its short name.  Same
+ * arguments, errors and ownership as chisao_create with arena = NULL. */
+chisao_status chisao_init(const chisao_problem *probs, int32_t n_probs,
+                          const chisao_params *params, void *cuda_stream,
+                          chisao_ctx **out);
 
 /* One oscillation cycle (Algorithm 1, one iteration of its outer loop) for
  * every problem: asynchronous on the context's stream.  The n_osc-th call runs
@@ -316,6 +329,12 @@ chisao_status chisao_widths(chisao_ctx *c, int32_t prob, float *w_out, float *co
  * device flag is cleared and CHISAO_ERR_TIMEOUT is returned. */
 chisao_status chisao_get_counters(chisao_ctx *c, int32_t prob, chisao_counters *out);
 
+/* The same counters under their short name (identical behaviour and errors):
+ * evaluations, line-search trials, the stuck count and K_lost of Algorithm 1's
+ * Phases 2-3, the reseeding strategy of Phase 4 (Sec. 3.2.4) and the step
+ * sizes of Phases 5-6. */
+chisao_status chisao_stats(chisao_ctx *c, int32_t prob, chisao_counters *out);
+
 /* Test hook for that failure path: one kernel waits, with the library's bounded
  * wait, on a shared-memory barrier nothing arrives on; after budget_ns (1 .. 10^10)
  * it raises problem `prob`'s device error flag and returns.  Asynchronous. */
@@ -382,14 +401,16 @@ chisao_status chisao_set_gr_state(chisao_ctx *c, int32_t prob, int32_t enabled,
 /* ---------------------------------------------------------------------------
  * Allocation-free deduplication.
  *
- * The paper has no counterpart to this entry point: it exists for callers
- * that cannot allocate device memory and so cannot create a context -- code
- * running while a CUDA graph is captured, hosts whose allocator owns the whole
- * device, loops where a cudaMalloc/cudaFree would synchronize the GPU.  It runs
- * the Phase 3 decision (a stuck x_j is removed when another stuck x_i ranks
- * above it, f descending then index ascending, and every |x_ik - x_jk| <
- * eps_dup, compared in binary32) on caller buffers only, and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory and so cannot create a context: a host
+ * application whose own memory pool has reserved the whole device and forbids
+ * side allocations, a plug-in that is handed only its input and output
+ * buffers, or a latency-critical loop in which a cudaMalloc/cudaFree pair
+ * would synchronize the device.  It runs the Phase 3 decision (a stuck x_j is
+ * removed when another stuck x_i ranks above it, f descending then index
+ * ascending, and every |x_ik - x_jk| < eps_dup, compared in binary32) on
+ * caller buffers only, and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
  *
  *   x_dev       device float [n][d], row-major, d in 1..CHISAO_MAX_DIM
  *   f_dev       device float [n]
@@ -402,13 +423,23 @@ chisao_status chisao_set_gr_state(chisao_ctx *c, int32_t prob, int32_t enabled,
  * counters, about 1 MiB) is one file-scope device array per GPU, held by every
  * GPU that loads the library until the process exits.  n above
  * CHISAO_DEDUP_NOALLOC_MAX_N returns CHISAO_ERR_CAPACITY without launching
- * anything; bad pointers or sizes return CHISAO_ERR_ARG.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current: make that first call before any stream capture.  All
- * calls on a device share the one array and each call starts by clearing the
- * counters it needs, so calls whose kernels overlap on the GPU (different
- * streams, or different host threads) race and must be serialized by the
- * caller.  Asynchronous on cuda_stream. */
+ * anything; bad pointers or sizes return CHISAO_ERR_ARG.
+ *
+ * Cost: unlike the context's spatial-hash dedup, each of the S stuck samples
+ * scans the whole stuck list (S warps x S candidates, O(S^2 d)): about 1e10
+ * candidate tests at S = 10^5 and 7e10 at the limit, seconds of GPU time.
+ * Use it for stuck sets of a few ten thousand at most; larger sets belong to
+ * the context path.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset) invalidates the kept address: do not call this
+ * entry point again in a process that has reset the device.  All calls on a
+ * device share the one array and each call starts by clearing the counters
+ * it needs, so calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race and must be serialized by the caller.
+ * Asynchronous on cuda_stream. */
 #define CHISAO_DEDUP_NOALLOC_MAX_N (1 << 18)
 chisao_status chisao_dedup_noalloc(const float *x_dev, int32_t d, int64_t n,
                                    const float *f_dev, const uint32_t *stuck_dev,

@@ -912,6 +912,11 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
   return CHISAO_OK;
 }
 
+chisao_status chisao_init(const chisao_problem* probs, int32_t n_probs, const chisao_params* params,
+                          void* cuda_stream, chisao_ctx** out) {
+  return chisao_create(probs, n_probs, params, nullptr, 0, cuda_stream, out);
+}
+
 chisao_status chisao_load_population(chisao_ctx* c, int32_t prob, const float* x_host) {
   chisao_status s = check_prob(c, prob);
   if (s != CHISAO_OK) return s;
@@ -1169,6 +1174,10 @@ chisao_status chisao_get_counters(chisao_ctx* c, int32_t prob, chisao_counters* 
                                            std::to_string(cnt.err) + ", now cleared)");
   }
   return CHISAO_OK;
+}
+
+chisao_status chisao_stats(chisao_ctx* c, int32_t prob, chisao_counters* out) {
+  return chisao_get_counters(c, prob, out);
 }
 
 chisao_status chisao_selftest_wait(chisao_ctx* c, int32_t prob, int64_t budget_ns) {

@@ -2,13 +2,15 @@
 // that cannot allocate device memory.
 //
 // The context-based path keeps the compacted list of stuck samples in memory
-// that chisao_create carves out.  Some callers cannot create a context: code
-// that runs while a CUDA graph is being captured (cudaMalloc is not allowed
-// there), hosts whose own allocator owns the whole device and forbids side
-// allocations, and latency-critical loops where a cudaMalloc/cudaFree pair
-// would synchronize the device.  This entry point takes only caller buffers;
-// its scratch (the stuck list and two counters) is a file-scope __device__
-// array that exists once per GPU for as long as the library stays loaded.
+// that chisao_create carves out.  Some callers cannot create a context: hosts
+// whose own memory pool has reserved the whole device and forbids side
+// allocations, plug-ins that are handed only their input and output buffers,
+// and latency-critical loops where a cudaMalloc/cudaFree pair would
+// synchronize the device.  This entry point takes only caller buffers; its
+// scratch (the stuck list and two counters) is a file-scope __device__ array
+// that exists once per GPU for as long as the library stays loaded.  Its
+// pairwise scan is O(S^2 d) in the stuck count S (the context path's spatial
+// hash is near-linear), which the header states next to the size limit.
 #include <mutex>
 
 #include "../../include/chisao.h"

@@ -70,7 +70,9 @@ def test_arena_bytes_and_argument_checks(lib):
     assert lib.chisao_arena_bytes(probs, 1, C.byref(p), C.byref(nb)) == CH.ERR_ARG
     ctx = C.c_void_p()
     assert lib.chisao_create(probs, 1, C.byref(p), None, 0, None, C.byref(ctx)) == CH.ERR_ARG
+    assert lib.chisao_init(probs, 1, C.byref(p), None, C.byref(ctx)) == CH.ERR_ARG
     assert lib.chisao_step(None) == CH.ERR_ARG
+    assert lib.chisao_stats(None, 0, None) == CH.ERR_ARG
 
 
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
@@ -143,3 +145,36 @@ def test_header_is_plain_c_and_the_library_links_from_c(lib, tmp_path):
     # x, g (4 x 4 floats) and the histories (2 x 4 x 10 x 4 floats) at least
     assert nbytes >= 4 * (2 * 4 * 4 + 2 * 4 * 10 * 4)
     assert int(lines[4]) == CH.ERR_ARG and int(lines[5]) == CH.ERR_ARG
+
+
+def test_eval_rejects_bad_points_before_any_launch(lib):
+    """Chisao.eval / ChisaoObjective check dtype, device and shape on the host (the
+    kernels read and write rows of exactly d binary32 values): a wrong input raises
+    ChisaoError before the library is called."""
+    import torch
+    model = CH.Chisao.__new__(CH.Chisao)           # no device context needed for the checks
+    model.problems = [I.small_mixture(5, 3, 10, seed=0)]
+    calls = []
+
+    class _Spy:
+        def __getattr__(self, name):
+            calls.append(name)
+            raise AssertionError("the library must not be called")
+
+    good = torch.zeros(4, 5, dtype=torch.float32)
+    bad = [torch.zeros(4, 5, dtype=torch.float64), torch.zeros(4, 5, dtype=torch.bfloat16),
+           torch.zeros(4, 4), torch.zeros(20), torch.zeros(4, 6), good, np.zeros((4, 5), np.float32)]
+    orig = CH.library
+    CH.library = lambda: _Spy()
+    try:
+        for x in bad:                                # CPU tensors fail the device test too
+            with pytest.raises(CH.ChisaoError):
+                model.eval(0, x)
+            with pytest.raises(CH.ChisaoError):
+                CH.ChisaoObjective.apply(model, 0, x)
+        with pytest.raises(CH.ChisaoError):
+            model.eval(3, good)
+    finally:
+        CH.library = orig
+    assert calls == []
+    model.ctx = None

@@ -1,8 +1,9 @@
 """chisao_dedup_noalloc against the context-based deduplication.
 
 The allocation-free entry point serves callers that cannot allocate device
-memory (graph capture in progress, a host allocator that owns the device, loops
-that must not synchronize on cudaMalloc/cudaFree).  It must return exactly the
+memory (a host memory pool that has reserved the whole device, a plug-in handed
+only its buffers, loops that must not synchronize on cudaMalloc/cudaFree).  It
+must return exactly the
 masks and counts of the context path (Phase 3 through chisao_run_phase), on two
 calls in a row that share its one static scratch array.  This file is named so
 that pytest collects it last.
