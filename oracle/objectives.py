@@ -69,8 +69,10 @@ def _component_logdens(obj, X):
         score = -R / (sig[None] ** 2)
     elif obj.kind in (OBJ_MIXTURE_PREC, OBJ_MIXTURE_PREC_SPLIT):
         W = A["linv"]
-        Z = np.einsum("kij,nkj->nki", W, R)                # W_k (x - mu_k)
-        score = -np.einsum("kji,nkj->nki", W, Z)           # -W_k^T z_k
+        Rk = R.transpose(1, 0, 2)                          # (K, N, d)
+        Zk = np.matmul(Rk, W.transpose(0, 2, 1))           # rows z = W_k (x - mu_k)
+        Z = Zk.transpose(1, 0, 2)
+        score = -np.matmul(Zk, W).transpose(1, 0, 2)       # rows -W_k^T z_k
         logdet = -np.log(np.abs(np.einsum("kii->ki", W))).sum(axis=1)
     else:
         L = A["chol"]
