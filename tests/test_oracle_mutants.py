@@ -89,8 +89,10 @@ def _plant(dst, name, edits):
 
 
 def _pin_suite(dst):
+    # the pins (the stored-values check in test_oracle_golden.py tests staleness, not arithmetic)
     tests = sorted(f for f in os.listdir(os.path.join(dst, "tests"))
-                   if f.startswith("test_oracle_") and f.endswith(".py") and f != os.path.basename(__file__))
+                   if f.startswith("test_oracle_") and f.endswith(".py")
+                   and f not in (os.path.basename(__file__), "test_oracle_golden.py"))
     env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
     r = subprocess.run([sys.executable, "-m", "pytest", *[os.path.join("tests", t) for t in tests], "-x", "-q",
                         "-m", "not gpu", "-p", "no:cacheprovider"], cwd=dst, env=env, capture_output=True,
