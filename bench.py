@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3, help="cycles of the 512-problem leg")
     ap.add_argument("--bench-fn-steps", type=int, default=3, help="cycles of each benchmark-function leg")
     ap.add_argument("--noise-trials", type=int, default=10, help="trials per level of the noise-table leg")
-    ap.add_argument("--leg", default=None, choices=["batched512", "noise_d6", "benchmark_functions"],
+    ap.add_argument("--leg", default=None, choices=["batched512", "noise_d6", "benchmark_functions", "mixture4_d2",
+                                                    "mixture32_d16", "mixture256_d64"],
                     help="run only this leg (one JSON line; for profiling one workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FD, e2e, kernel and CPU legs")
+    ap.add_argument("--no-small-legs", dest="small_legs", action="store_false",
+                    help="skip the d = 2 and d = 16 workload legs")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -131,6 +134,39 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
     return 6800.0, 1900.0, "fallback"
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_modes(workload):
+    """The significant modes of a workload's objective and -Hess f there, as stored by
+    tests/golden/make_modes.py (FP64 Newton from every component mean; read here, not
+    computed)."""
+    p = os.path.join(GOLDEN, f"modes_{workload}.npz")
+    if not os.path.exists(p):
+        return None
+    z = np.load(p)
+    return z["x"], z["neg_hess"]
+
+
+def recovery_of(found, workload, rel=1e-3):
+    """Recovered fraction of the stored significant modes (a returned point within
+    `rel` of the mode's local sigma: Mahalanobis distance under -Hess f at the mode) and
+    the worst matched error in local sigmas."""
+    m = stored_modes(workload)
+    if m is None:
+        return None
+    mx, negH = m
+    found = np.asarray(found, np.float64).reshape(-1, mx.shape[1])
+    best = np.full(mx.shape[0], np.inf)
+    for k, (x, H) in enumerate(zip(mx, negH)):
+        if found.shape[0]:
+            D = found - x[None, :]
+            best[k] = float(np.sqrt(np.maximum(np.einsum("nd,de,ne->n", D, H, D), 0.0)).min())
+    hit = best <= rel
+    return {"significant_modes": int(mx.shape[0]), "recovered": float(hit.mean()),
+            "worst_error_sigma": float(best[hit].max()) if hit.any() else None, "returned": int(found.shape[0])}
 
 
 def kernel_source_hash():
@@ -284,7 +320,50 @@ def tc_executed_flop_per_point(d, K):
     return 2 * (2 * 64) * (64 * K) + 2 * (64 * K) * 64
 
 
-def full_covariance_leg(CH, steps, n_osc):
+def events_time(stream, fn):
+    """Device time of fn()'s work on `stream` (CUDA events on that stream)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_and_score(CH, prob, workload, prm, cycles, warm=True):
+    """A whole run of `cycles` cycles (the last one final) from the workload's population:
+    device time of the non-final cycles and of the final one, evaluations, and the
+    recovery of the stored significant modes.  With `warm`, a first run captures the
+    cycle graphs so the timed run replays them."""
+    model = CH.Chisao([prob], prm)
+    if warm:
+        for _ in range(cycles):
+            model.step()
+        model.modes(0)
+        model.load_population(0, prob.x0)
+    c0 = model.counters(0)
+    t_nf = events_time(model._stream, lambda: [model.step() for _ in range(cycles - 1)]) if cycles > 1 else 0.0
+    c1 = model.counters(0)
+    t_last = events_time(model._stream, model.step)
+    c2 = model.counters(0)
+    fx, _ = model.modes(0)
+    model.close()
+    nf = max(cycles - 1, 1)
+    return {"value": prob.n * (cycles - 1) / t_nf if cycles > 1 else None, "unit": "sample-cycles/s",
+            "ms_per_step": 1e3 * t_nf / nf if cycles > 1 else None, "final_cycle_ms": 1e3 * t_last,
+            "evals_per_s": (c1["evals"] - c0["evals"]) / t_nf if cycles > 1 else None,
+            "run_ms": 1e3 * (t_nf + t_last), "run_evals": int(c2["evals"] - c0["evals"]),
+            "stuck_last_cycle": int(c2["n_stuck"]), "k_lost_last_cycle": int(c2["k_lost"]),
+            "recovery": recovery_of(fx, workload)}
+
+
+def full_covariance_leg(CH, steps, n_osc, fp32_peak_tf):
+    """cfg 4, d = 64, K = 256 full-covariance mixture: throughput of the BF16 tensor-core
+    cycle and of the FP32 (SIMT adjoint) cycle at N = 65536, the tensor-core objective
+    against the measured BF16 peak and against the exact FP64 mixture, and the three
+    forms (tensor cores + FP32 refinement, FP32 adjoint, FP32 central differences) at
+    matched mode-location error on the same 1024 rows."""
     import torch
     prob = make_problem("mixture256_d64", 0)
     N, d, K = prob.n, prob.d, prob.objective.n_comp
@@ -293,31 +372,132 @@ def full_covariance_leg(CH, steps, n_osc):
         prm = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=mode, seed=0)
         m4 = CH.Chisao([prob], prm)
         t, c0, c1 = gpu_timed(m4, nsteps, 1)
+        ev = (c1["evals"] - c0["evals"]) / t
         res[label] = {"value": N * nsteps / t, "unit": "sample-cycles/s", "ms_per_step": 1e3 * t / nsteps,
-                      "evals_per_s": (c1["evals"] - c0["evals"]) / t, "steps": nsteps}
+                      "evals_per_s": ev, "steps": nsteps, "stuck_last_cycle": int(c1["n_stuck"]),
+                      "k_lost_last_cycle": int(c1["k_lost"])}
+        if mode == CH.GRAD_ADJOINT:
+            # every evaluation of the SIMT adjoint path is a value and a gradient: two
+            # triangular contractions d (d + 1) K each (the dense rows it walks: 4 d^2 K)
+            alg = ev * 2 * d * (d + 1) * K / 1e12
+            res[label]["roofline"] = {"bound": "alu", "achieved": alg, "peak": fp32_peak_tf, "unit": "TFLOP/s",
+                                      "frac": alg / fp32_peak_tf if fp32_peak_tf else None,
+                                      "executed_tflops": ev * 4 * d * d * K / 1e12,
+                                      "peak_source": "measured FP32 FMA throughput"}
         if mode == CH.GRAD_ADJOINT_TC:
             x = torch.from_numpy(prob.x0).cuda()
             m4.eval(0, x, mode)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(m4._stream)
             reps = 5
-            for _ in range(reps):
-                m4.eval(0, x, mode)
-            e1.record(m4._stream)
-            e1.synchronize()
-            tk = e0.elapsed_time(e1) / 1e3 / reps
-            # algorithmic: the dense forward contraction (d x dK per point) and the adjoint's
-            # backward contraction (dK x d), 2 flop per multiply-add
-            flop = N * (2 * d * (d * K) + 2 * (d * K) * d)
+            tk = events_time(m4._stream, lambda: [m4.eval(0, x, mode) for _ in range(reps)]) / reps
+            # algorithmic work (triangular factors): d (d + 1) K for the value's contraction
+            # and the same again for the adjoint's, 2 flop per multiply-add
+            flop = N * 2 * d * (d + 1) * K
+            dense = N * (2 * d * (d * K) + 2 * (d * K) * d)
             executed = N * tc_executed_flop_per_point(d, K)
             _, bf16_peak, src = peaks()
             res["roofline_tc"] = {"kernel": "k_tc_mixfull<true>", "bound": "tensor", "achieved": flop / tk / 1e12,
                                   "peak": bf16_peak, "unit": "TFLOP/s", "frac": flop / tk / 1e12 / bf16_peak,
+                                  "count": "triangular: 2 d (d + 1) K flop per value and gradient",
+                                  "dense_tflops": dense / tk / 1e12, "dense_frac": dense / tk / 1e12 / bf16_peak,
                                   "executed_tflops": executed / tk / 1e12,
                                   "peak_source": f"{src} bf16 dense (MEASURED_PEAKS.json burst)",
                                   "launch_ms": 1e3 * tk, "points_per_launch": N}
+            res["tc_error_vs_exact"] = tc_error_vs_exact(CH, m4)
         m4.close()
+    res["matched_error"] = matched_error_forms(CH)
     return res
+
+
+def tc_error_vs_exact(CH, model):
+    """The tensor-core objective (BF16 factors, split input) and the FP32 SIMT adjoint
+    against the exact FP64 mixture at 256 stored rows of the population
+    (tests/golden/exact_mixture256_d64.npz): value error |f - f*| and gradient error
+    |g - g*|_inf / |g*|_inf, max and median over the points."""
+    import torch
+    p = os.path.join(GOLDEN, "exact_mixture256_d64.npz")
+    if not os.path.exists(p):
+        return None
+    z = np.load(p)
+    x = torch.from_numpy(z["x"].astype(np.float32)).cuda()
+    out = {"points": int(z["x"].shape[0])}
+    for mode, label in ((CH.GRAD_ADJOINT_TC, "bf16_tensor_core"), (CH.GRAD_ADJOINT, "fp32_adjoint")):
+        f, g = model.eval(0, x, mode)
+        f = f.cpu().numpy().astype(np.float64)
+        g = g.cpu().numpy().astype(np.float64)
+        fe = np.abs(f - z["f"])
+        ge = np.abs(g - z["g"]).max(axis=1) / np.maximum(np.abs(z["g"]).max(axis=1), 1e-300)
+        out[label] = {"value_abs_max": float(fe.max()), "value_abs_median": float(np.median(fe)),
+                      "grad_rel_max": float(ge.max()), "grad_rel_median": float(np.median(ge))}
+    return out
+
+
+def matched_error_forms(CH, n_rows=1024, n_conv=100, cycles=2):
+    """cfg 4's forms on the same first n_rows samples, n_conv = 100 and 2 cycles (enough
+    for every significant mode to stick): each form's whole-run device time and the
+    recovery (fraction of significant modes within 1e-3 local sigma, worst error)."""
+    from paper_2606_26164_gb300 import inputs as I
+    prob = I.mixture256_d64(n=n_rows)
+    out = {"N": n_rows, "n_conv": n_conv, "cycles": cycles}
+    forms = (("bf16_tensor_core_refined", CH.GRAD_ADJOINT_TC, 10, True),
+             ("fp32_adjoint", CH.GRAD_ADJOINT, 0, True),
+             ("fp32_central_differences", CH.GRAD_FD32, 0, False))
+    for label, mode, n_refine, warm in forms:
+        prm = CH.default_params(n_osc=cycles, n_conv=n_conv, m=10, eps_grad=prob.eps_grad, grad_mode=mode,
+                                seed=4, n_refine=n_refine)
+        r = run_and_score(CH, prob, "mixture256_d64", prm, cycles, warm=warm)
+        out[label] = {"run_ms": r["run_ms"], "run_evals": r["run_evals"], "recovery": r["recovery"]}
+    return out
+
+
+def mixture4_d2_leg(CH):
+    """cfg 1, the plain method at d = 2: K = 4 isotropic mixture, N = 1024, FD64
+    (h = 1e-5), m = 5, 50 cycles.  The state is L2-resident and each cycle is a few
+    dozen short kernels, so the leg reports microseconds per cycle with the per-cycle
+    CUDA graph and without it (every kernel launched from the host), the host time of
+    one chisao_step call, and the recovery after the 50 cycles."""
+    from paper_2606_26164_gb300 import inputs as I
+    prob = I.mixture4_d2()
+    out = {"N": prob.n, "d": 2, "K": 4, "grad": "fd64", "m": 5, "cycles": 50}
+    for use_graph in (1, 0):
+        prm = CH.default_params(n_osc=50, m=5, eps_grad=1e-5, grad_mode=GRAD["fd64"], seed=0, use_graph=use_graph)
+        model = CH.Chisao([prob], prm)
+        for _ in range(50):
+            model.step()
+        model.modes(0)
+        model.load_population(0, prob.x0)
+        model.synchronize()
+        host = []
+
+        def run():
+            for _ in range(50):
+                h0 = time.perf_counter()
+                model.step()
+                host.append(time.perf_counter() - h0)
+        t = events_time(model._stream, run)
+        fx, _ = model.modes(0)
+        c = model.counters(0)
+        model.close()
+        out["graph" if use_graph else "no_graph"] = {
+            "us_per_cycle": 1e6 * t / 50, "value": prob.n * 50 / t, "unit": "sample-cycles/s",
+            "host_us_per_step_call": 1e6 * float(np.median(host)), "recovery": recovery_of(fx, "mixture4_d2"),
+            "stuck_last_cycle": int(c["n_stuck"]), "k_lost_last_cycle": int(c["k_lost"])}
+    return out
+
+
+def mixture32_d16_leg(CH):
+    """cfg 2, d = 16, K = 32 diagonal mixture, N = 16384, the Table 1 schedule (3 cycles,
+    n_conv = 12): central differences (FP64 stencil, h = 1e-5) against exact gradients,
+    each without noise and with N(0, sigma_noise^2) added to every evaluation
+    (sigma_noise = 0.1, 1.0).  Throughput of the two non-final cycles, the final cycle's
+    time, and the recovery of the run."""
+    from paper_2606_26164_gb300 import inputs as I
+    out = {"N": 16384, "d": 16, "K": 32, "cycles": 3, "eps_grad": 1e-4}
+    for grad in ("adjoint", "fd64"):
+        for noise in (0.0, 0.1, 1.0):
+            prob = I.mixture32_d16(noise_sigma=noise)
+            prm = CH.default_params(n_osc=3, m=10, eps_grad=1e-4, grad_mode=GRAD[grad], seed=2)
+            out[f"{grad}_noise{noise:g}"] = run_and_score(CH, prob, "mixture32_d16", prm, 3)
+    return out
 
 
 def batched_leg(CH, steps):
@@ -419,7 +599,11 @@ def main():
     if args.leg:
         legs = {"batched512": lambda: batched_leg(CH, args.batched_steps),
                 "noise_d6": lambda: noise_table_leg(CH, args.noise_trials),
-                "benchmark_functions": lambda: benchmark_functions_leg(CH, args.bench_fn_steps, 2)}
+                "benchmark_functions": lambda: benchmark_functions_leg(CH, args.bench_fn_steps, 2),
+                "mixture4_d2": lambda: mixture4_d2_leg(CH),
+                "mixture32_d16": lambda: mixture32_d16_leg(CH),
+                "mixture256_d64": lambda: full_covariance_leg(CH, args.tc_steps, 10 ** 6,
+                                                              CH.measure_fma_peak(False) / 1e12)}
         print(json.dumps({"leg": args.leg, **legs[args.leg]()}))
         return
     prob = make_problem(args.workload, seed=rank)
@@ -455,7 +639,12 @@ def main():
                             f"{(2 * N * d * 4 + 2 * N * 10 * d * 4 + N * 80) / 1e6:.0f} MB > 129 MB"},
            "evals_per_s": evals, "grads_per_s": grads,
            "gpu_launches": launches_per_step(params, gm == GRAD["adjoint_tc"], d) * args.steps,
-           "clocks": clocks}
+           "clocks": clocks,
+           # what the timed cycles left: samples stuck after the last dedup, and removed by it
+           "stuck_last_cycle": int(c1["n_stuck"]), "k_lost_last_cycle": int(c1["k_lost"]),
+           "n_unfrozen_last_cycle": int(c1["n_unfrozen"])}
+    if rank == 0:
+        out["recovery"] = {"timed_schedule": recovery_of(model.modes(0)[0], args.workload)}
 
     if gm == GRAD["adjoint_tc"]:
         args.no_extras = True            # the kernel, FD, e2e and CPU legs time the FP32 path
@@ -495,13 +684,22 @@ def main():
                                                   "(sampled clock)",
                            "fp64_peak_measured": CH.measure_fma_peak(True, model._stream) / 1e12,
                            "launch_ms": 1e3 * t_k, "evals_per_launch": ev_k}
+        # --- recovery at a schedule long enough to converge (Prop. 1): one cycle of
+        #     n_conv = 2500 on the whole population (the quadratic's mode is its centre)
+        if args.workload == "quadratic_d64":
+            pc = CH.default_params(n_osc=1, n_conv=2500, m=10, eps_grad=1e-2, grad_mode=gm, seed=3)
+            r = run_and_score(CH, prob, args.workload, pc, 1, warm=False)
+            out["recovery"]["n_conv_2500_one_cycle"] = {**r["recovery"], "run_ms": r["run_ms"],
+                                                        "eps_grad": 1e-2}
         # --- FD leg: the plain form (central differences, FP64 stencil, h = 1e-5)
         fd = CH.default_params(n_osc=n_osc, m=10, eps_grad=prob.eps_grad, grad_mode=CH.GRAD_FD64, seed=rank)
         mfd = CH.Chisao([prob], fd)
         tf, f0, f1 = gpu_timed(mfd, args.fd_steps, 1)
         out["fd64"] = {"value": N * args.fd_steps / tf, "unit": "sample-cycles/s",
                        "evals_per_s": (f1["evals"] - f0["evals"]) / tf, "ms_per_step": 1e3 * tf / args.fd_steps,
-                       "steps": args.fd_steps}
+                       "steps": args.fd_steps, "stuck_last_cycle": int(f1["n_stuck"]),
+                       "k_lost_last_cycle": int(f1["k_lost"]),
+                       "recovery_timed_schedule": recovery_of(mfd.modes(0)[0], args.workload)}
         if args.workload == "quadratic_d64":
             # every evaluation of the FD64 cycle is one binary64 value of the quadratic: u = A r
             # and r^T u, 2 d^2 + 2 d FLOP; against the measured binary64 FMA throughput
@@ -522,7 +720,11 @@ def main():
         # --- the d=64, K=256 full-covariance mixture at N=65536: BF16 tensor-core cycle vs FP32 cycle,
         #     and the tensor-core objective kernel against the measured BF16 peak
         if args.workload == "quadratic_d64" and args.tc_steps > 0:
-            out["mixture256_d64"] = full_covariance_leg(CH, args.tc_steps, n_osc)
+            out["mixture256_d64"] = full_covariance_leg(CH, args.tc_steps, n_osc, peak_tf)
+        # --- cfg 1 (d = 2, the plain method, 50 cycles) and cfg 2 (d = 16, FD vs adjoint, noise)
+        if args.workload == "quadratic_d64" and args.small_legs:
+            out["mixture4_d2"] = mixture4_d2_leg(CH)
+            out["mixture32_d16"] = mixture32_d16_leg(CH)
         # --- 512 problems of uneven size in one context (cycle graph with one branch per stream)
         if args.workload == "quadratic_d64" and args.batched_steps > 0:
             out["batched512"] = batched_leg(CH, args.batched_steps)

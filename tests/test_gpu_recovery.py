@@ -8,7 +8,9 @@ the means need not reach every maximum of an overlapping mixture) and points
 that are not local maxima at all (errors).
 
 Each case prints one RECOVERY line (run with -s to see them); the assertions are
-floors below the measured values, and no returned point may be a non-maximum."""
+floors just below the measured values (1/11 = 0.091 of the d = 16 modes at the Table 1
+schedule, all of them with n_conv = 40, all five of the d = 64 full-covariance modes,
+a mean of 0.432 over the 512 problems), and no returned point may be a non-maximum."""
 import numpy as np
 import pytest
 
@@ -73,8 +75,8 @@ def test_recovery_mixture4_d2():
     assert frac == 1.0 and other == 0 and bad == 0
 
 
-@pytest.mark.parametrize("noise,n_conv,n_osc,floor", [(0.0, 0, 3, 0.05), (0.0, 0, 30, 0.05), (0.0, 40, 4, 0.9),
-                                                      (0.1, 40, 4, 0.0)])
+@pytest.mark.parametrize("noise,n_conv,n_osc,floor", [(0.0, 0, 3, 0.09), (0.0, 0, 30, 0.09), (0.0, 40, 4, 1.0),
+                                                      (0.1, 40, 4, 0.09)])
 def test_recovery_mixture32_d16(noise, n_conv, n_osc, floor):
     """d = 16, K = 32 diagonal mixture, N = 16384, exact gradients.  With the Table 1
     rule n_conv = max(10, 3 log2 d) = 12 the median |grad f| after Phase 1 is still
@@ -112,7 +114,7 @@ def test_recovery_mixture256_d64_tensor_cores():
     (fx,) = _run([prob], P, grad_mode=CH.GRAD_ADJOINT_TC, n_refine=10)
     k, frac, worst, other, bad = _score(prob, fx)
     _report("mixture256_d64 tensor cores", k, frac, worst, fx.shape[0], other, bad)
-    assert frac >= 0.8 and bad == 0
+    assert frac == 1.0 and bad == 0
 
 
 def test_recovery_batched512():
@@ -132,4 +134,4 @@ def test_recovery_batched512():
         total_modes += k
         returned += fx.shape[0]
     _report("batched512 (mean over problems)", total_modes, float(np.mean(fracs)), worst, returned, other, bad)
-    assert np.mean(fracs) >= 0.3 and bad <= 0.002 * returned
+    assert np.mean(fracs) >= 0.43 and bad <= 0.002 * returned
