@@ -315,9 +315,14 @@ def gpu_timed(model, steps, warmup):
 
 
 def tc_executed_flop_per_point(d, K):
-    """Tensor-core flop the kernel issues per point: Z over the split input (K = 2 x 64)
-    and G = Y V, both over the padded dimension 64."""
-    return 2 * (2 * 64) * (64 * K) + 2 * (64 * K) * 64
+    """Tensor-core flop the kernel issues per point (2 per multiply-add), per group of
+    two components over the padded dimension 64 in four 16-wide slabs: Z over the split
+    input, input K-chunk c meeting the rows of slabs >= c (N = 32 (4 - c)), twice; the
+    bias block (K = 16, N = 128); G = Y V, y K-chunk c meeting the outputs of slabs <= c
+    (N = 16 (c + 1)), per component."""
+    z = 2 * sum(32 * (4 - c) * 16 for c in range(4)) + 128 * 16
+    gr = 2 * sum(16 * (c + 1) * 16 for c in range(4))
+    return 2 * (z + gr) * ((K + 1) // 2)
 
 
 def events_time(stream, fn):

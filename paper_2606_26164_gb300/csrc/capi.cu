@@ -277,11 +277,15 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
     E.ft = b.take<float>(n);
     E.gt = b.take<float>(n * dp);
     E.a0 = b.take<float>(n);
-    E.list[0] = b.take<int>(n);
-    E.list[1] = b.take<int>(n);
-    E.cnt = b.take<int>((size_t)prm.T_ls + 1);
-    E.xp = b.take<float>((size_t)prm.M * n * dp);
-    E.gp = b.take<float>((size_t)prm.M * n * dp);
+    E.list0 = b.take<int>(n);
+    E.mlist[0] = b.take<int>(n);
+    E.mlist[1] = b.take<int>(n);
+    E.cnt = b.take<int>(2 * ((size_t)ls_rounds(prm.T_ls) + 1));
+    E.iota = b.take<int>(2 * LS_BATCH * n);
+    E.fm = b.take<float>(2 * LS_BATCH * n);
+    const size_t xrows = (size_t)std::max(prm.M, 2 * LS_BATCH) * n;
+    E.xp = b.take<float>(xrows * dp);
+    E.gp = b.take<float>(xrows * dp);
     E.vel = b.take<float>(n * dp);
   }
 }
@@ -424,18 +428,29 @@ cudaError_t tc_eval_rows(const ProbHost& ph, const float* x, float* f, float* g,
                            count);
 }
 
-// n_iter L-BFGS iterations (Phase 1) with T_ls line-search rounds each.
+// n_iter L-BFGS iterations (Phase 1).  Per iteration: the direction kernel writes
+// the first trial point of every moving sample; round 0 evaluates them and accepts
+// or hands each failing sample on with its next LS_BATCH trial points; each later
+// round evaluates all pending trial points in one call (rows 0 .. 4 count - 1 of
+// its buffer, through the identity row list) and accepts the first passing trial.
 cudaError_t enqueue_phase1_tc(const ProbHost& ph, int n_iter, bool fresh, cudaStream_t st) {
   const ProbDev& P = ph.dev;
   const ExtBuf& E = ph.ext;
+  const int R = ls_rounds(ph.sp.T_ls);
+  const size_t brows = (size_t)LS_BATCH * P.n;          // rows of one trial-point buffer
   cudaError_t e;
   if (fresh && (e = tc_eval_rows(ph, P.x, P.f, P.g, P.n, nullptr, nullptr, st)) != cudaSuccess) return e;
   for (int it = 0; it < n_iter; ++it) {
-    if ((e = cudaMemsetAsync(E.cnt, 0, sizeof(int) * (ph.sp.T_ls + 1), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(E.cnt, 0, sizeof(int) * 2 * (R + 1), st)) != cudaSuccess) return e;
     if ((e = launch_ext(EXT_DIR, P, ph.sp, E, (fresh && it == 0) ? 1 : 0, st)) != cudaSuccess) return e;
-    for (int t = 0; t < ph.sp.T_ls; ++t) {
-      if ((e = tc_eval_rows(ph, E.xt, E.ft, E.gt, P.n, E.list[t & 1], E.cnt + t, st)) != cudaSuccess) return e;
-      if ((e = launch_ext(EXT_ACCEPT, P, ph.sp, E, t, st)) != cudaSuccess) return e;
+    if ((e = tc_eval_rows(ph, E.xt, E.ft, E.gt, P.n, E.list0, E.cnt, st)) != cudaSuccess) return e;
+    if ((e = launch_ext(EXT_ACCEPT, P, ph.sp, E, 0, st)) != cudaSuccess) return e;
+    for (int r = 1; r < R; ++r) {
+      const size_t o = (size_t)((r - 1) & 1) * brows;   // buffer written by the previous round
+      if ((e = tc_eval_rows(ph, E.xp + o * ph.dp, E.fm + o, E.gp + o * ph.dp, (int)brows, E.iota,
+                            E.cnt + (R + 1) + r, st)) != cudaSuccess)
+        return e;
+      if ((e = launch_ext(EXT_ACCEPT_MULTI, P, ph.sp, E, r, st)) != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -872,6 +887,8 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
       if (cudaMemcpy(ph.tc_weights, tcw.data(), tcw.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         st = cuda_fail(c, cudaGetLastError(), "tensor-core weight upload");
     }
+    if (ph.tc && launch_ext(EXT_IOTA, P, ph.sp, ph.ext, 0, c->stream) != cudaSuccess)
+      st = cuda_fail(c, cudaGetLastError(), "row list of the line-search rounds");
     to32(a0, f0); to32(a1, f1); to32(a2, f2); to32(a3, f3);
     auto up = [&](const void* dst, const void* src, size_t bytes) {
       if (bytes && cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)

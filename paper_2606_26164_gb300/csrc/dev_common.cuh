@@ -147,20 +147,30 @@ enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HL
 constexpr int GRAD_GIVEN = 9;
 
 // Buffers of the batched-evaluator (tensor-core) path.
+// Trial steps evaluated per sample in each line-search round after the first (the
+// batched-evaluator Phase 1): round r >= 1 evaluates alpha0 2^-t for the next LS_BATCH
+// values of t at once, and the first passing one wins.
+constexpr int LS_BATCH = 4;
+__host__ __device__ constexpr int ls_rounds(int T_ls) { return 1 + (T_ls - 1 + LS_BATCH - 1) / LS_BATCH; }
+
 struct ExtBuf {
   float* p;        // [n][dp] search directions
-  float* xt;       // [n][dp] trial points
-  float* ft;       // [n] trial values
-  float* gt;       // [n][dp] trial gradients
+  float* xt;       // [n][dp] first trial points (round 0)
+  float* ft;       // [n] their values
+  float* gt;       // [n][dp] their gradients
   float* a0;       // [n] initial steps
-  int* list[2];    // pending samples of the current / next line-search round
-  int* cnt;        // [T_ls + 1] pending count of each round
-  float* xp;       // [M n][dp] HLC perturbed points
-  float* gp;       // [M n][dp] their gradients
+  int* list0;      // samples pending in round 0
+  int* mlist[2];   // samples pending in a later round (double-buffered by round parity)
+  int* cnt;        // [ls_rounds + 1] pending samples of each round, then [ls_rounds + 1] trial rows
+  int* iota;       // [2 LS_BATCH n] 0, 1, 2, ...: the row list of a later round's trial points
+  float* fm;       // [2 LS_BATCH n] values of the later rounds' trial points
+  float* xp;       // [max(M, 2 LS_BATCH) n][dp] HLC perturbed points; the later line-search
+                   //   rounds' trial points (buffer b at rows b LS_BATCH n, LS_BATCH rows per sample)
+  float* gp;       // the same shape: their gradients
   float* vel;      // [n][dp] anti-convergence velocity
 };
 enum ExtKernelId { EXT_DIR = 0, EXT_ACCEPT = 1, EXT_HLC_POINTS = 2, EXT_HLC_STEP = 3, EXT_ANTI_STEP = 4,
-                   EXT_SCALES = 5 };
+                   EXT_SCALES = 5, EXT_ACCEPT_MULTI = 6, EXT_IOTA = 7 };
 
 // Caller points for plain objective evaluation.
 struct EvalArgs {

@@ -7,10 +7,14 @@
 // Phase 1 per L-BFGS iteration (same rules as the fused k_phase1):
 //   k_ext_dir     two-loop direction from the history in HBM, descent check,
 //                 first trial point x + alpha0 p (box-projected), pending list;
-//   T_ls rounds of [evaluator on the pending trial points -> k_ext_accept]:
-//                 Armijo test; accepted samples take the point, value and
-//                 gradient and push (s, y, rho) into the history; the others
-//                 get the next, halved trial point on the next round's list.
+//   round 0:      evaluator on the pending trial points -> k_ext_accept: Armijo
+//                 test; accepted samples take the point, value and gradient and
+//                 push (s, y, rho) into the history; each of the others gets its
+//                 next LS_BATCH trial points alpha0 2^-t, t = 1 .. LS_BATCH;
+//   rounds r >= 1: evaluator on all those points at once -> k_ext_accept_multi:
+//                 the first passing trial (the largest alpha) is accepted, which is
+//                 the step sequential backtracking takes; a sample with none gets
+//                 the next LS_BATCH trial points, until T_ls trials are spent.
 //   Lists are filled with atomics; every result is per sample, so the order of
 //   a list changes nothing.
 // Phase 5: k_ext_hlc_points writes x + sigma z_k for all M perturbations, the
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
       st_vec<V>(E.xt + (size_t)i * DP + j0, c);
       if (g.l == 0) {
         E.a0[i] = a0;
-        E.list[0][atomicAdd(&E.cnt[0], 1)] = i;
+        E.list0[atomicAdd(&E.cnt[0], 1)] = i;
       }
     }
     if (g.l == 0 && count_start) ev = 1;
@@ -70,19 +74,103 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
   block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
 }
 
+// An accepted trial point c (value -Ft, gradient -Gt of F) of sample i: the pair
+// (s, y) = (c - x, Gt - G) is pushed when curved (s^T y summed from exact products in
+// double-single, rho = 1 / s^T y finite), shifting the stored pairs one slot back
+// (slot 0 newest); then x, grad f and f take the trial's values.
+template <int V, int LPS>
+__device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams& S, int i, int j0, int DP,
+                                              const float (&x)[V], const float (&G)[V], const float (&c)[V],
+                                              const float (&Gt)[V], float Ft, const Grp<LPS>& g) {
+  float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    sv[v] = c[v] - x[v];
+    yv[v] = Gt[v] - G[v];
+    const float pr = sv[v] * yv[v];
+    ff_add(syh, syl, pr, fmaf(sv[v], yv[v], -pr));
+    ss = fmaf(sv[v], sv[v], ss);
+    yy = fmaf(yv[v], yv[v], yy);
+  }
+  g.ff_sum(syh, syl);
+  const float sy = syh + syl;
+  ss = g.sum(ss);
+  yy = g.sum(yy);
+  if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && 1.0f / sy <= FLT_MAX) {
+    const int len = P.hlen[i];
+    for (int k = min(len, S.m - 1); k > 0; --k) {      // shift the pairs one slot back
+      const size_t o = ((size_t)i * MMAX + k) * DP + j0;
+      float a[V], b[V];
+      ld_vec<V>(P.hs + o - DP, a);
+      ld_vec<V>(P.hy + o - DP, b);
+      st_vec<V>(P.hs + o, a);
+      st_vec<V>(P.hy + o, b);
+      if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = P.hrho[(size_t)i * MMAX + k - 1];
+    }
+    const size_t o0 = (size_t)i * MMAX * DP + j0;
+    st_vec<V>(P.hs + o0, sv);
+    st_vec<V>(P.hy + o0, yv);
+    if (g.l == 0) {
+      P.hrho[(size_t)i * MMAX] = 1.0f / sy;
+      P.hlen[i] = min(len + 1, S.m);
+    }
+  }
+  float gout[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) gout[v] = -Gt[v];
+  st_vec<V>(P.x + (size_t)i * DP + j0, c);
+  st_vec<V>(P.g + (size_t)i * DP + j0, gout);
+  if (g.l == 0) P.f[i] = -Ft;
+}
+
+// Sample i failed every trial so far, the last being t0 - 1: it goes on the list of
+// round r with its trials t0 .. t0 + LS_BATCH - 1 (rows LS_BATCH slot + q of the
+// round's buffer; a trial past T_ls is written as x and never looked at), or, with no
+// trial left, its search fails (history cleared, x unchanged).  Returns 1 on failure.
+template <int V, int LPS>
+__device__ __forceinline__ int ext_hand_on(const ProbDev& P, const StepParams& S, const ExtBuf& E, int i, int j0,
+                                           int DP, int r, int t0, const float (&x)[V], const Grp<LPS>& g) {
+  if (t0 >= S.T_ls) {
+    if (g.l == 0) P.hlen[i] = 0;
+    return 1;
+  }
+  const int R = ls_rounds(S.T_ls);
+  int slot = 0;
+  if (g.l == 0) {
+    slot = atomicAdd(&E.cnt[r], 1);
+    atomicAdd(&E.cnt[R + 1 + r], LS_BATCH);
+    E.mlist[(r - 1) & 1][slot] = i;
+  }
+  slot = __shfl_sync(g.mask, slot, 0, LPS);
+  float p[V], lo[V], hi[V];
+  ld_vec<V>(E.p + (size_t)i * DP + j0, p);
+  ld_vec<V>(P.lo + j0, lo);
+  ld_vec<V>(P.hi + j0, hi);
+  const float a0 = E.a0[i];
+  const size_t base = (size_t)((r - 1) & 1) * LS_BATCH * P.n + (size_t)LS_BATCH * slot;
+#pragma unroll
+  for (int q = 0; q < LS_BATCH; ++q) {
+    const float a = t0 + q < S.T_ls ? ldexpf(a0, -(t0 + q)) : 0.f;
+    float c[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) c[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
+    st_vec<V>(E.xp + (base + q) * DP + j0, c);
+  }
+  return 0;
+}
+
+// Round 0: the first trial point of every sample the direction kernel listed.
 template <int DP>
-__global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, ExtBuf E, int t) {
+__global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, ExtBuf E) {
   constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
-  const int cur = t & 1;
-  const int pending = E.cnt[t];
-  // a grid of at most 16 blocks per SM strides over the round's list (after the first
-  // round the lists are short or empty, so most launches end at once)
+  const int pending = E.cnt[0];
+  // a grid of at most 16 blocks per SM strides over the list
   if ((int)(((size_t)blockIdx.x * blockDim.x) / LPS) >= pending) return;
   const int stride = (int)(((size_t)gridDim.x * blockDim.x) / LPS);
   unsigned long long tr = 0, fl = 0;
   for (int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS); jj < pending; jj += stride) {
-    const int i = E.list[cur][jj];
+    const int i = E.list0[jj];
     const int j0 = V * g.l;
     float x[V], G[V], c[V], Gt[V];
     ld_vec<V>(P.x + (size_t)i * DP + j0, x);
@@ -100,66 +188,76 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
     const float dec = g.sum(dl);
     if (g.l == 0) tr += 1;
     if (Ft <= F + (float)S.c1 * dec) {
-      float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        sv[v] = c[v] - x[v];
-        yv[v] = Gt[v] - G[v];
-        const float pr = sv[v] * yv[v];
-        ff_add(syh, syl, pr, fmaf(sv[v], yv[v], -pr));
-        ss = fmaf(sv[v], sv[v], ss);
-        yy = fmaf(yv[v], yv[v], yy);
-      }
-      g.ff_sum(syh, syl);
-      const float sy = syh + syl;
-      ss = g.sum(ss);
-      yy = g.sum(yy);
-      if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && 1.0f / sy <= FLT_MAX) {
-        const int len = P.hlen[i];
-        for (int k = min(len, S.m - 1); k > 0; --k) {      // shift the pairs one slot back
-          const size_t o = ((size_t)i * MMAX + k) * DP + j0;
-          float a[V], b[V];
-          ld_vec<V>(P.hs + o - DP, a);
-          ld_vec<V>(P.hy + o - DP, b);
-          st_vec<V>(P.hs + o, a);
-          st_vec<V>(P.hy + o, b);
-          if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = P.hrho[(size_t)i * MMAX + k - 1];
-        }
-        const size_t o0 = (size_t)i * MMAX * DP + j0;
-        st_vec<V>(P.hs + o0, sv);
-        st_vec<V>(P.hy + o0, yv);
-        if (g.l == 0) {
-          P.hrho[(size_t)i * MMAX] = 1.0f / sy;
-          P.hlen[i] = min(len + 1, S.m);
-        }
-      }
-      float gout[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) gout[v] = -Gt[v];
-      st_vec<V>(P.x + (size_t)i * DP + j0, c);
-      st_vec<V>(P.g + (size_t)i * DP + j0, gout);
-      if (g.l == 0) P.f[i] = -Ft;
-    } else if (t + 1 < S.T_ls) {
-      float p[V], lo[V], hi[V];
-      ld_vec<V>(E.p + (size_t)i * DP + j0, p);
-      ld_vec<V>(P.lo + j0, lo);
-      ld_vec<V>(P.hi + j0, hi);
-      const float a = ldexpf(E.a0[i], -(t + 1));
-#pragma unroll
-      for (int v = 0; v < V; ++v) c[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
-      st_vec<V>(E.xt + (size_t)i * DP + j0, c);
-      if (g.l == 0) E.list[cur ^ 1][atomicAdd(&E.cnt[t + 1], 1)] = i;
+      ext_take_step<V, LPS>(P, S, i, j0, DP, x, G, c, Gt, Ft, g);
     } else {
-      if (g.l == 0) {
-        P.hlen[i] = 0;
-        fl += 1;
-      }
+      const int f = ext_hand_on<V, LPS>(P, S, E, i, j0, DP, 1, 1, x, g);
+      if (g.l == 0) fl += (unsigned long long)f;
     }
   }
   block_add_u64<NT_OBJ>(tr, &P.cnt->ls_trials);
   block_add_u64<NT_OBJ>(tr, &P.cnt->evals);
   block_add_u64<NT_OBJ>(tr, &P.cnt->grads);
   block_add_u64<NT_OBJ>(fl, &P.cnt->ls_fail);
+}
+
+// Round r >= 1: the trials t = 1 + (r - 1) LS_BATCH + q of every listed sample, all
+// evaluated; the first that passes Armijo is taken.
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_accept_multi(ProbDev P, StepParams S, ExtBuf E, int r) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int pending = E.cnt[r];
+  if ((int)(((size_t)blockIdx.x * blockDim.x) / LPS) >= pending) return;
+  const int stride = (int)(((size_t)gridDim.x * blockDim.x) / LPS);
+  const int t0 = 1 + (r - 1) * LS_BATCH;
+  unsigned long long tr = 0, ev = 0, fl = 0;
+  for (int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS); jj < pending; jj += stride) {
+    const int i = E.mlist[(r - 1) & 1][jj];
+    const int j0 = V * g.l;
+    const size_t base = (size_t)((r - 1) & 1) * LS_BATCH * P.n + (size_t)LS_BATCH * jj;
+    float x[V], G[V];
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = -G[v];
+    const float F = -P.f[i];
+    if (g.l == 0) {
+      ev += LS_BATCH;
+      tr += (unsigned long long)min(LS_BATCH, S.T_ls - t0);
+    }
+    bool done = false;
+    for (int q = 0; q < LS_BATCH && t0 + q < S.T_ls; ++q) {
+      float c[V], Gt[V];
+      ld_vec<V>(E.xp + (base + q) * DP + j0, c);
+      ld_vec<V>(E.gp + (base + q) * DP + j0, Gt);
+      float dl = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        Gt[v] = -Gt[v];
+        dl += G[v] * (c[v] - x[v]);
+      }
+      const float Ft = -E.fm[base + q];
+      const float dec = g.sum(dl);
+      if (Ft <= F + (float)S.c1 * dec) {
+        ext_take_step<V, LPS>(P, S, i, j0, DP, x, G, c, Gt, Ft, g);
+        done = true;
+        break;
+      }
+    }
+    if (!done) {
+      const int f = ext_hand_on<V, LPS>(P, S, E, i, j0, DP, r + 1, t0 + LS_BATCH, x, g);
+      if (g.l == 0) fl += (unsigned long long)f;
+    }
+  }
+  block_add_u64<NT_OBJ>(tr, &P.cnt->ls_trials);
+  block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
+  block_add_u64<NT_OBJ>(fl, &P.cnt->ls_fail);
+}
+
+__global__ void k_ext_iota(int* __restrict__ a, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = (int)t;
 }
 
 // x + sigma z_k for k < M (row k n + i of xp); frozen samples write x itself.
@@ -342,7 +440,8 @@ static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& 
   const unsigned blocks = (unsigned)(((long long)P.n * LPS + NT_OBJ - 1) / NT_OBJ);
   switch (which) {
     case EXT_DIR: k_ext_dir<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
-    case EXT_ACCEPT: {
+    case EXT_ACCEPT:
+    case EXT_ACCEPT_MULTI: {
       static int sms = 0;                              // SM count of the device (queried once)
       if (sms == 0) {
         int dev = 0;
@@ -351,7 +450,15 @@ static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& 
           sms = 152;
       }
       const unsigned cap = (unsigned)(16 * sms);
-      k_ext_accept<DP><<<blocks < cap ? blocks : cap, NT_OBJ, 0, st>>>(P, S, E, arg);
+      if (which == EXT_ACCEPT)
+        k_ext_accept<DP><<<blocks < cap ? blocks : cap, NT_OBJ, 0, st>>>(P, S, E);
+      else
+        k_ext_accept_multi<DP><<<blocks < cap ? blocks : cap, NT_OBJ, 0, st>>>(P, S, E, arg);
+      break;
+    }
+    case EXT_IOTA: {
+      const long long rows = 2ll * LS_BATCH * P.n;
+      k_ext_iota<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(E.iota, rows);
       break;
     }
     case EXT_HLC_POINTS: k_ext_hlc_points<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E, arg); break;
