@@ -14,9 +14,9 @@
 // are the BF16-rounded L_k^-1 (evaluated at the split input) up to FP32
 // accumulation.  The gradient is grad f = -sum_k r_k W_k^T z_k, r = softmax(lc),
 // formed in the same pass: the weights y = e^(lc_k - m_ref) z_k go to tensor memory
-// as BF16 and G += Y V accumulates on the tensor cores (V = the same rows of W with
-// the output coordinate as the N dimension); G is rescaled when the reference m_ref
-// rises, and normalised by the final sum.
+// as BF16 (Y, two buffers) and G += Y V accumulates on the tensor cores (V = the same
+// rows of W with the output coordinate as the N dimension); G is rescaled when the
+// reference m_ref rises, and normalised by the final sum.
 //
 // The factors are lower-triangular, so only the blocks on or below the diagonal
 // are multiplied: the output rows of a group's factor tile are ordered by 16-row
@@ -27,10 +27,11 @@
 //
 // Operand tiles are stored in global memory already in the canonical K-major,
 // non-swizzled shared-memory layout (8 x 16-byte core matrices), so each one
-// arrives with a single cp.async.bulk.  Every mbarrier wait is bounded by a
-// clock budget; on timeout the kernel raises the device error flag, every role
-// stops issuing work, waits for its copies and MMAs in flight, and the tensor
-// memory is still released.
+// arrives with a single cp.async.bulk; each group's log-constants are read by the
+// epilogue straight from global memory, one group ahead.  Every mbarrier wait is
+// bounded by a clock budget; on timeout the kernel raises the device error flag,
+// every role stops issuing work, waits for its copies and MMAs in flight, and the
+// tensor memory is still released.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -161,15 +162,15 @@ constexpr int NV = 3;                      // stages of the V-tile ring
 // Barriers in shared memory (index into the array after the tiles).
 enum : int {
   B_WFULL = 0,                 // [NW] factor tile, bias tile and constants of a group landed
-  B_WEMPTY = B_WFULL + NW,     // [NW] read by the Z MMAs and the constants by the epilogue
+  B_WEMPTY = B_WFULL + NW,     // [NW] read by the Z MMAs
   B_VFULL = B_WEMPTY + NW,     // [NV] V tile of a group landed
   B_VEMPTY = B_VFULL + NV,     // [NV] read by the gradient MMAs
-  B_ZFULL = B_VEMPTY + NV,     // [2] Z of a group of parity b in TMEM buffer b
-  B_ZEMPTY = B_ZFULL + 2,      // [2] value-only kernel: Z buffer b read into registers by all eight
-                               //     epilogue warps (with gradients the buffer is free once the
-                               //     gradient MMAs that read its weights finished: B_G2DONE)
-  B_YFULL = B_ZEMPTY + 2,      // [2] weights of buffer b written (eight warps)
-  B_G2DONE = B_YFULL + 2,      // [2] gradient MMAs reading buffer b finished
+  B_ZFULL = B_VEMPTY + NV,     // Z of the current group in TMEM
+  B_ZEMPTY = B_ZFULL + 1,      // [2] Z of a group of parity b read into registers by all eight epilogue
+                               //     warps (one barrier per parity: each Z issuer then waits at most one
+                               //     phase past one it has seen, so a parity wait cannot alias)
+  B_YFULL = B_ZEMPTY + 2,      // [2] Y buffer b written (eight warps)
+  B_G2DONE = B_YFULL + 2,      // [2] gradient MMAs reading Y buffer b finished
   B_XREADY = B_G2DONE + 2,     // split input tile written (eight warps)
   B_DRAIN = B_XREADY + 1,      // [3] every MMA of issuer i finished
   NBARS = B_DRAIN + 3
@@ -186,13 +187,11 @@ constexpr int OFF_BAR = OFF_XCH + XCH_BYTES;
 constexpr int SMEM2_BYTES = OFF_BAR + NBARS * 8 + 8;      // + TMEM address, abort flag
 static_assert(WC_BYTES % 1024 == 0 && VT_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned tiles");
 static_assert(SMEM2_BYTES <= 232448, "shared memory per block");
-// TMEM columns: two Z buffers of TN columns (groups of parity b in buffer b; each
-// component's BF16 weights y, two K-elements per column, overwrite the first 8 of the 16
-// columns of each of its Z slabs once the epilogue has read them), and the gradient
-// accumulator of component h for the groups of parity b at COL_G + 64 (2b + h)
-constexpr uint32_t COL_Z = 0, COL_G = 2 * TN;
-static_assert(COL_G + 4 * 64 <= TMEM_COLS, "tensor memory columns");
-// TMEM column (from the buffer start) of component h's slab s of z, and of its y K-chunk s
+// TMEM columns: Z, the gradient accumulator of component h for the groups of parity b
+// at COL_G + 64 (2b + h), and Y buffer b (BF16 weights, two K-elements per column)
+constexpr uint32_t COL_Z = 0, COL_G = TN, COL_Y = TN + 256;
+static_assert(COL_Y + 2 * 64 <= TMEM_COLS, "tensor memory columns");
+// Z column of component h's slab s of z
 __host__ __device__ constexpr uint32_t zcol(int h, int s) { return (uint32_t)zrow(h, 16 * s); }
 constexpr float TAU = 16.f;                // lazy rescale: Y weights stay below e^TAU
 
@@ -252,11 +251,6 @@ __device__ __forceinline__ void tmem_pin16(uint32_t (&r)[16]) {
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
                  "+r"(r[15]));
 }
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-               : "memory");
-}
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
@@ -290,27 +284,25 @@ __device__ __forceinline__ void tmem_scale64(uint32_t taddr, float s) {
 // One CTA = one tile of 128 points; the components go in groups of two (parity b = g & 1):
 //   warp 0 (one thread) bulk-copies each group's factor tile, bias tile and constants
 //   into a ring of NW stages and its V tile into a ring of NV stages;
-//   warp 1 (one thread) issues Z = [x_hi|x_lo|1] [W|W|-b]^T into TMEM buffer b, only
-//   the nonzero triangle of each K-chunk; two buffers, so the next group's Z runs
-//   while the epilogue works on the current one;
+//   warp 1 (one thread) issues Z = [x_hi|x_lo|1] [W|W|-b]^T into TMEM, only the nonzero
+//   triangle of each K-chunk (the bias enters the contraction through a K block of ones
+//   against the exact three-term BF16 split of -b, so z leaves the tensor cores centred);
 //   warps 2 and 3 (one thread each, groups of parity 0 and 1) issue
-//   G_{h,b} += Y_h V_h (h = the group's first or second component), Y read from the
-//   Z buffer b where the epilogue wrote it, the largest K-chunk first so the first
-//   MMA of an accumulator covers all its columns.  Spreading the issue over three
-//   threads matters: a thread that issued MMAs finds its next barrier operation held
-//   until they ran, so each gradient issuer only waits on barriers whose MMAs finished
-//   long ago, and the gradient MMAs fill the tensor pipe while the epilogue works.
-//   Within a parity the gradient MMAs stay in group order, so the sums are
-//   deterministic; the Z buffer b is taken by group g + 2 only after the gradient
-//   MMAs of group g (which read its weights) finished;
+//   G_{h,b} += Y_h V_h (h = the group's first or second component), Y read from TMEM
+//   buffer b.  Spreading the issue over three threads matters: a thread that issued
+//   MMAs finds its next barrier operation held until they ran, so each gradient issuer
+//   only waits on barriers whose MMAs finished long ago, and the gradient MMAs fill the
+//   tensor pipe while the next Z waits for its buffer.  Within a parity the gradient
+//   MMAs stay in group order (group g's weights are written only after those of g - 2
+//   were consumed), so the sums are deterministic;
 //   warps 4-11 are two warpgroups, one per component of the group, each covering the
 //   four TMEM lane quadrants (one point per thread): they read z, fold the component
-//   into a log-sum-exp and write the gradient weights e^(lc - m_ref) z as BF16 over
-//   their own z columns.  Each warpgroup keeps one reference m_ref, sum and pair of
-//   accumulators per group parity: m_ref is raised only when a component exceeds it
-//   by TAU, the rows of that parity's accumulator then being rescaled in place, which
-//   needs only the gradient MMAs of the same parity two groups back.  The four
-//   partial results are combined at the end.
+//   into a log-sum-exp and write the gradient weights e^(lc - m_ref) z as BF16 into
+//   TMEM.  Each warpgroup keeps one reference m_ref, sum and pair of accumulators per
+//   group parity: m_ref is raised only when a component exceeds it by TAU, the rows of
+//   that parity's accumulator then being rescaled in place, which needs only the
+//   gradient MMAs of the same parity two groups back (also what frees the Y buffer).
+//   The four partial results are combined at the end.
 template <bool GRAD>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -326,14 +318,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   if (t == 0) {
     for (int i = 0; i < NW; ++i) {
       mbar_init(&bars[B_WFULL + i], 1);
-      mbar_init(&bars[B_WEMPTY + i], 1 + 8);
+      mbar_init(&bars[B_WEMPTY + i], 1);
     }
     for (int i = 0; i < NV; ++i) {
       mbar_init(&bars[B_VFULL + i], 1);
       mbar_init(&bars[B_VEMPTY + i], 1);
     }
+    mbar_init(&bars[B_ZFULL], 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&bars[B_ZFULL + b], 1);
       mbar_init(&bars[B_ZEMPTY + b], 8);
       mbar_init(&bars[B_YFULL + b], 8);
       mbar_init(&bars[B_G2DONE + b], 1);
@@ -392,24 +384,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       bool issued = false;
       if (mbar_wait_ab(&bars[B_XREADY], 0, a.err, abort_flag)) {
         for (int g = 0; g < ng; ++g) {
-          const int s = g % NW, b = g & 1;
+          const int s = g % NW;
           if (!mbar_wait_ab(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) break;
-          // buffer b is free once group g - 2 is done with it: its weights consumed by the
-          // gradient MMAs (value only: its z read by the epilogue)
-          if (g >= 2 && !mbar_wait_ab(&bars[(GRAD ? B_G2DONE : B_ZEMPTY) + b], ((g - 2) >> 1) & 1, a.err,
-                                      abort_flag))
-            break;
+          if (g >= 1 && !mbar_wait_ab(&bars[B_ZEMPTY + ((g - 1) & 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) break;
           tc_fence_after();
           const uint32_t bW = smem_u32(sm + OFF_W + s * WC_BYTES);
-          const uint32_t dz = tmem + COL_Z + (uint32_t)(TN * b);
 #pragma unroll
           for (int hl = 0; hl < 2; ++hl)               // x_hi then x_lo against the same factor tile
 #pragma unroll
             for (int c = 0; c < NSLAB; ++c)            // K-chunk c meets the rows of slabs >= c
-              mma_bf16(dz, sdesc(aX + hl * A_BYTES + c * 256, 128, 1024), sdesc(bW + c * 256, 128, 1024),
+              mma_bf16(tmem + COL_Z, sdesc(aX + hl * A_BYTES + c * 256, 128, 1024), sdesc(bW + c * 256, 128, 1024),
                        idesc_bf16(TM, zn_of_chunk(c)), (hl | c) ? 1u : 0u);
-          mma_bf16(dz, sdesc(aOnes, 128, 256), sdesc(bW + W_BYTES, 128, 256), idF, 1u);   // - b
-          mma_commit(&bars[B_ZFULL + b]);
+          mma_bf16(tmem + COL_Z, sdesc(aOnes, 128, 256), sdesc(bW + W_BYTES, 128, 256), idF, 1u);   // - b
+          mma_commit(&bars[B_ZFULL]);
           mma_commit(&bars[B_WEMPTY + s]);
           issued = true;
         }
@@ -430,13 +417,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         if (!mbar_wait_ab(&bars[B_VFULL + s], (g / NV) & 1, a.err, abort_flag)) break;
         tc_fence_after();
         const uint32_t bV = smem_u32(sm + OFF_V + s * VT_BYTES);
-        const uint32_t zb = tmem + COL_Z + (uint32_t)(TN * b);
+        const uint32_t aY = tmem + COL_Y + 64u * (uint32_t)b;
         const uint32_t dg = tmem + COL_G + 128u * (uint32_t)b;
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int c = NSLAB - 1; c >= 0; --c)         // y K-chunk c meets outputs j <= 16 c + 15
-            mma_bf16_ts(dg + 64u * h, zb + zcol(h, c), sdesc(bV + (h * NSLAB + c) * 256, 128, 2048),
+            mma_bf16_ts(dg + 64u * h, aY + 32u * h + 8u * c, sdesc(bV + (h * NSLAB + c) * 256, 128, 2048),
                         idesc_bf16(TM, gn_of_chunk(c)), (g >= 2 || c < NSLAB - 1) ? 1u : 0u);
         mma_commit(&bars[B_G2DONE + b]);
         mma_commit(&bars[B_VEMPTY + s]);
@@ -488,18 +475,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       if (lane == 0) mbar_arrive(&bars[B_XREADY]);
     }
 
+    const float* cst_ptr = reinterpret_cast<const float*>(a.gblk + W_BYTES + BT_BYTES) + h;
+    float cst_next = __ldg(cst_ptr);
     float mref0 = -CUDART_INF_F, mref1 = -CUDART_INF_F, ssum0 = 0.f, ssum1 = 0.f;   // per group parity
     bool ok = true;
     for (int g = 0; g < ng; ++g) {
       const int b = g & 1, s = g % NW;
-      if (!warp_wait(&bars[B_ZFULL + b], (g >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
+      if (!warp_wait(&bars[B_ZFULL], g & 1, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      const uint32_t zb = tl + COL_Z + (uint32_t)(TN * b);
       float z[64];
       {
         uint32_t r[NSLAB][16];
 #pragma unroll
-        for (int c = 0; c < NSLAB; ++c) tmem_ld16_async(zb + zcol(h, c), r[c]);
+        for (int c = 0; c < NSLAB; ++c) tmem_ld16_async(tl + COL_Z + zcol(h, c), r[c]);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < NSLAB; ++c) {
@@ -508,26 +496,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
           for (int e = 0; e < 16; ++e) z[16 * c + e] = __uint_as_float(r[c][e]);
         }
       }
-      if (!GRAD) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars[B_ZEMPTY + b]);  // buffer b may take group g + 2
-      }
-
-      // the constants landed with the factor tile; the stage cannot be refilled before
-      // this warp's arrival on B_WEMPTY below, so the phase waited for is still the current one
-      if (!warp_wait(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) { ok = false; break; }
-      const float cst = reinterpret_cast<const float*>(sm + OFF_W + s * WC_BYTES + W_BYTES + BT_BYTES)[h];
+      tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars[B_WEMPTY + s]);   // constants of this stage read
-      float2 qa = make_float2(0.f, 0.f), qb = qa;        // two packed chains: four partial sums
+      if (lane == 0) mbar_arrive(&bars[B_ZEMPTY + b]);   // Z may take the next group
+
+      // the log-constant of this group, read from global memory one group ahead (the factor
+      // ring then depends on the Z MMAs alone)
+      const float cst = cst_next;
+      if (g + 1 < ng) cst_next = __ldg(cst_ptr + (size_t)(g + 1) * (GBLK_BYTES / 4));
+      float2 qa = make_float2(0.f, 0.f), qb = qa, qc = qa, qd = qa;   // four packed chains
 #pragma unroll
-      for (int e = 0; e < 64; e += 4) {
+      for (int e = 0; e < 64; e += 8) {
         const float2 z0 = make_float2(z[e], z[e + 1]), z1 = make_float2(z[e + 2], z[e + 3]);
+        const float2 z2 = make_float2(z[e + 4], z[e + 5]), z3 = make_float2(z[e + 6], z[e + 7]);
         qa = __ffma2_rn(z0, z0, qa);
         qb = __ffma2_rn(z1, z1, qb);
+        qc = __ffma2_rn(z2, z2, qc);
+        qd = __ffma2_rn(z3, z3, qd);
       }
-      const float lc = cst - 0.5f * ((qa.x + qa.y) + (qb.x + qb.y));
+      const float lc = cst - 0.5f * (((qa.x + qa.y) + (qb.x + qb.y)) + ((qc.x + qc.y) + (qd.x + qd.y)));
 
       if (!GRAD) {
         if (lc > mref0) {
@@ -549,8 +536,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         }
         mr = lc;
       }
-      // the parity-b accumulators may be rescaled once the gradient MMAs of group g - 2
-      // finished (the Z issuer waited for them before filling buffer b, so this passes)
+      // Y buffer b and the parity-b accumulators are free once the gradient MMAs of group
+      // g - 2 finished
       if (g >= 2 && !warp_wait(&bars[B_G2DONE + b], ((g - 2) >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
       if (__any_sync(0xffffffffu, resc)) tmem_scale64(tl + COL_G + 128u * b + 64u * h, scale);
@@ -563,14 +550,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         mref0 = mr;
         ssum0 = ss;
       }
-      // the weights of K-chunk c over the first 8 of this component's 16 z columns of slab c
-      // (read above by this warp; the other warpgroup's columns are not touched)
+      {
+        uint32_t y[32];
 #pragma unroll
-      for (int c = 0; c < NSLAB; ++c) {
-        uint32_t y[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = pack_bf16x2(r * z[16 * c + 2 * e], r * z[16 * c + 2 * e + 1]);
-        tmem_st8(zb + zcol(h, c), y);
+        for (int e = 0; e < 32; ++e) {
+          const float2 w = __fmul2_rn(make_float2(z[2 * e], z[2 * e + 1]), make_float2(r, r));
+          y[e] = pack_bf16x2(w.x, w.y);
+        }
+        tmem_st32(tl + COL_Y + 64u * (uint32_t)b + 32u * h, y);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -699,11 +686,10 @@ static double host_bf2d(uint16_t h) {
 
 // Operand blocks of the tensor-core objective from the FP64 inverse Cholesky
 // factors linv[K][d][d] (lower-triangular), means mu[K][d] and log-weights: per
-// group of CG components the BF16 factor tile (rows = output coordinates in the
-// slab-major order of zrow, K = input coordinate), the bias tile holding -W mu (from
-// the rounded W, in binary32) as three BF16 terms whose sum is exact (same rows), the
-// log-constants, and the V tile (rows = input coordinate, K = component-major output
-// coordinate).
+// group of CG components the BF16 factor tile (rows = component-major output
+// coordinates, K = input coordinate), the bias tile holding -W mu (from the rounded W,
+// in binary32) as three BF16 terms whose sum is exact, the log-constants, and the V
+// tile (rows = input coordinate, K = component-major output coordinate).
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out) {
   using namespace tc;
