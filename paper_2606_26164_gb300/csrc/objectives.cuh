@@ -273,19 +273,41 @@ struct HasMulti : std::false_type {};
 // ------------------------------------------------------------ diagonal mixture
 template <>
 struct Obj<OBJ_MIXTURE_DIAG> {
+  // The components go in steps of CK: their parameter loads, the lane's share of each
+  // |A^(1/2)(x - mu_k)|^2 and the CK group sums are independent and overlap; the
+  // log-sum-exp then takes them in component order.  Every operation and its order is
+  // that of one component at a time, so the results are the same bits.
+  static constexpr int CK = 4;
+  template <typename T, int V, int LPS>
+  static __device__ __forceinline__ void comp_terms(const ObjParams<T>& o, int k, const T (&x)[V], T& q,
+                                                    T (&sc)[V], const Grp<LPS>& g) {
+    T mk[V], ak[V];
+    ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
+    ldg_vec<T, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
+    q = T(0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T r = x[v] - mk[v];
+      q = fma(ak[v] * r, r, q);
+      sc[v] = -ak[v] * r;
+    }
+  }
   template <typename T, int V, int LPS>
   static __device__ __forceinline__ T value(const ObjParams<T>& o, const T (&x)[V], const Grp<LPS>& g) {
     T m = -CUDART_INF, s = T(0);
-    for (int k = 0; k < o.K; ++k) {
-      T mk[V], ak[V];
-      ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
-      ldg_vec<T, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
-      T q = T(0);
+    int k = 0;
+    for (; k + CK <= o.K; k += CK) {
+      T q[CK], sc[CK][V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const T r = x[v] - mk[v];
-        q = fma(ak[v] * r, r, q);
-      }
+      for (int c = 0; c < CK; ++c) comp_terms<T, V, LPS>(o, k + c, x, q[c], sc[c], g);
+#pragma unroll
+      for (int c = 0; c < CK; ++c) q[c] = g.sum(q[c]);
+#pragma unroll
+      for (int c = 0; c < CK; ++c) lse_push(m, s, __ldg(o.p2 + k + c) - T(0.5) * q[c]);
+    }
+    for (; k < o.K; ++k) {
+      T q, sc[V];
+      comp_terms<T, V, LPS>(o, k, x, q, sc, g);
       q = g.sum(q);
       lse_push(m, s, __ldg(o.p2 + k) - T(0.5) * q);
     }
@@ -297,17 +319,19 @@ struct Obj<OBJ_MIXTURE_DIAG> {
     T m = -CUDART_INF, s = T(0), G[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) G[v] = T(0);
-    for (int k = 0; k < o.K; ++k) {
-      T mk[V], ak[V], sc[V];
-      ldg_vec<T, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
-      ldg_vec<T, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
-      T q = T(0);
+    int k = 0;
+    for (; k + CK <= o.K; k += CK) {
+      T q[CK], sc[CK][V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const T r = x[v] - mk[v];
-        q = fma(ak[v] * r, r, q);
-        sc[v] = -ak[v] * r;
-      }
+      for (int c = 0; c < CK; ++c) comp_terms<T, V, LPS>(o, k + c, x, q[c], sc[c], g);
+#pragma unroll
+      for (int c = 0; c < CK; ++c) q[c] = g.sum(q[c]);
+#pragma unroll
+      for (int c = 0; c < CK; ++c) lse_push_grad<T, V>(m, s, G, __ldg(o.p2 + k + c) - T(0.5) * q[c], sc[c]);
+    }
+    for (; k < o.K; ++k) {
+      T q, sc[V];
+      comp_terms<T, V, LPS>(o, k, x, q, sc, g);
       q = g.sum(q);
       lse_push_grad<T, V>(m, s, G, __ldg(o.p2 + k) - T(0.5) * q, sc);
     }
@@ -322,7 +346,38 @@ struct Obj<OBJ_MIXTURE_DIAG> {
     float m1 = -CUDART_INF_F, s1 = 0.f, G1[V], m2 = -CUDART_INF_F, s2 = 0.f, G2[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) G1[v] = G2[v] = 0.f;
-    for (int k = 0; k < o.K; ++k) {
+    constexpr int CP = CK / 2;                        // two points share each component's loads
+    int k = 0;
+    for (; k + CP <= o.K; k += CP) {
+      float q1[CP], q2[CP], sc1[CP][V], sc2[CP][V];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        float mk[V], ak[V];
+        ldg_vec<float, V>(o.p0 + (size_t)(k + c) * o.dp + V * g.l, mk);
+        ldg_vec<float, V>(o.p1 + (size_t)(k + c) * o.dp + V * g.l, ak);
+        q1[c] = q2[c] = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const float r1 = x1[v] - mk[v], r2 = x2[v] - mk[v];
+          q1[c] = fmaf(ak[v] * r1, r1, q1[c]);
+          q2[c] = fmaf(ak[v] * r2, r2, q2[c]);
+          sc1[c][v] = -ak[v] * r1;
+          sc2[c][v] = -ak[v] * r2;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        q1[c] = g.sum(q1[c]);
+        q2[c] = g.sum(q2[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        const float ck = __ldg(o.p2 + k + c);
+        lse_push_grad<float, V>(m1, s1, G1, ck - 0.5f * q1[c], sc1[c]);
+        lse_push_grad<float, V>(m2, s2, G2, ck - 0.5f * q2[c], sc2[c]);
+      }
+    }
+    for (; k < o.K; ++k) {
       float mk[V], ak[V], sc1[V], sc2[V];
       ldg_vec<float, V>(o.p0 + (size_t)k * o.dp + V * g.l, mk);
       ldg_vec<float, V>(o.p1 + (size_t)k * o.dp + V * g.l, ak);
