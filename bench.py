@@ -517,8 +517,16 @@ def batched_leg(CH, steps):
     t, _, _ = gpu_timed(model, steps, 1)
     n_total = sum(p.n for p in probs)
     model.close()
+    # kernel launches of one non-final cycle: grouped, the objective-independent steps of all
+    # problems are one launch per kernel (begin 1, freeze 3, dedup 5 + one per padded
+    # dimension, reseed 3 + one per padded dimension, end 1) and each (kind, padded dimension)
+    # group runs Phase 1 (1) and Phases 5-6 with their scale passes (6); per problem, every
+    # problem launches the single-problem cycle
+    pads = {max(4, 1 << (p.d - 1).bit_length()) for p in probs}
+    launches = (13 + 7 * len(pads) + 2 * len(pads)) if tune["grouped"] else KERNELS_PER_STEP * len(probs)
     return {"problems": len(probs), "samples": n_total, "value": n_total * steps / t, "unit": "sample-cycles/s",
-            "ms_per_step": 1e3 * t / steps, "steps": steps, "grad": "adjoint", "autotune": tune}
+            "ms_per_step": 1e3 * t / steps, "steps": steps, "grad": "adjoint", "autotune": tune,
+            "launches_per_cycle": launches}
 
 
 def benchmark_functions_leg(CH, steps, n_osc):

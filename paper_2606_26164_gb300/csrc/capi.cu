@@ -89,6 +89,8 @@ struct chisao_ctx {
   std::vector<int> branch_of;              // problem -> branch
   std::vector<Group> groups;               // grouped Phase 1 / 5 / 6 launches (empty: per problem)
   bool groups_enabled = true;              // chisao_autotune's choice
+  AllTabs all{};                           // grouped launches of the per-problem steps
+  void* all_mem = nullptr;
   std::string err;
 };
 
@@ -560,21 +562,12 @@ cudaError_t forked(chisao_ctx* c, F&& f) {
   return cudaSuccess;
 }
 
-// One cycle with grouped launches: the per-problem steps (release, freeze, dedup,
-// reseed, cycle end) run on the problems' branch streams; Phase 1, and then the scale
-// passes with Phases 5 and 6, run as one chain of launches per group (the groups on
-// separate branches), with joins in between, since every phase needs the previous one
-// of the same problem.
+// One cycle with grouped launches: the objective-independent steps (release, freeze,
+// dedup, reseed, cycle end) of all problems run as one launch per kernel on the context
+// stream; Phase 1, and then the scale passes with Phases 5 and 6, run as one chain of
+// launches per group (the groups on separate branches), with joins in between, since
+// every phase needs the previous one of the same problem.
 cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
-  auto per_problem = [&](auto&& body) {
-    return forked(c, [&]() -> cudaError_t {
-      for (size_t q = 0; q < c->probs.size(); ++q) {
-        const cudaError_t e = body(c->probs[q], c->branch[c->branch_of[q]]);
-        if (e != cudaSuccess) return e;
-      }
-      return cudaSuccess;
-    });
-  };
   auto per_group = [&](auto&& body) {
     return forked(c, [&]() -> cudaError_t {
       for (size_t k = 0; k < c->groups.size(); ++k) {
@@ -585,21 +578,17 @@ cudaError_t enqueue_cycle_grouped(chisao_ctx* c, bool last) {
     });
   };
   cudaError_t e;
-  if ((e = per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_begin(ph.dev, s); })) !=
-      cudaSuccess)
-    return e;
+  // the objective-independent steps of all problems are one launch per kernel on the
+  // context stream; the per-group objective phases run on the branches
+  if ((e = launch_cycle_begin_all(c->all, c->stream)) != cudaSuccess) return e;
   if ((e = per_group([](const Group& gr, cudaStream_t s) { return launch_grouped(OKID_PHASE1, gr, s); })) !=
       cudaSuccess)
     return e;                                                                               // Phase 1
-  if ((e = per_problem([last](const ProbHost& ph, cudaStream_t s) {                        // Phases 2-4
-         cudaError_t r;
-         if ((r = launch_freeze(ph.dev, ph.sp, s)) != cudaSuccess) return r;
-         if ((r = launch_dedup(ph.dev, ph.sp, s)) != cudaSuccess) return r;
-         return last ? cudaSuccess : launch_reseed(ph.dev, ph.sp, s);
-       })) != cudaSuccess)
-    return e;
+  if ((e = launch_freeze_all(c->all, c->stream)) != cudaSuccess) return e;                // Phase 2
+  if ((e = launch_dedup_all(c->all, c->stream)) != cudaSuccess) return e;                 // Phase 3
+  if (!last && (e = launch_reseed_all(c->all, c->stream)) != cudaSuccess) return e;       // Phase 4
   if (!last && (e = per_group(enqueue_explore_group)) != cudaSuccess) return e;            // Phases 5-6
-  return per_problem([](const ProbHost& ph, cudaStream_t s) { return launch_cycle_end(ph.dev, s); });
+  return launch_cycle_end_all(c->all, c->stream);
 }
 
 // One oscillation cycle of every problem: independent problems on the branch streams.
@@ -735,7 +724,13 @@ cudaError_t make_groups(chisao_ctx* c) {
     gr.tab_sc.blk_count = at(6);
     gr.tab_sc.blk_prob = at(7);
   }
-  return cudaSuccess;
+  std::vector<ProbDev> pd(nq);
+  std::vector<StepParams> sp(nq);
+  for (int q = 0; q < nq; ++q) {
+    pd[q] = c->probs[q].dev;
+    sp[q] = c->probs[q].sp;
+  }
+  return build_all_tabs(pd, sp, &c->all_mem, &c->all);
 }
 
 chisao_status check_prob(chisao_ctx* c, int32_t prob) {
@@ -1240,6 +1235,7 @@ void chisao_destroy(chisao_ctx* c) {
   free_branches(c);
   for (Group& gr : c->groups)
     if (gr.mem) cudaFree(gr.mem);
+  if (c->all_mem) cudaFree(c->all_mem);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -139,6 +139,32 @@ struct GroupTab {
   const int* blk_count;         // blocks of problem q in this launch
 };
 
+// One launch over several problems for the objective-independent kernels: entry j of
+// the launch's problem list (problem qidx[j], or j itself when qidx is null) owns blocks
+// first[j] .. first[j + 1] - 1; each per-problem body gets its block index and block
+// count within its problem, so it computes exactly what its own launch would.
+struct AllTab {
+  const ProbDev* probs;          // [problems]
+  const StepParams* sps;         // [problems]
+  const int* first;              // [n + 1] prefix sums of the entries' block counts
+  const int* qidx;               // [n] or null
+  int n;
+};
+struct BlkPos {
+  int q;
+  unsigned b, nb;
+};
+__device__ __forceinline__ BlkPos all_pos(const AllTab& T) {
+  const int bx = (int)blockIdx.x;
+  int lo = 0, hi = T.n - 1;                  // the last entry whose first block is <= bx
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (T.first[mid] <= bx) lo = mid;
+    else hi = mid - 1;
+  }
+  return {T.qidx ? T.qidx[lo] : lo, (unsigned)(bx - T.first[lo]), (unsigned)(T.first[lo + 1] - T.first[lo])};
+}
+
 enum ObjKernelId { OKID_PHASE1 = 0, OKID_DIRECTION = 1, OKID_SCALES = 2, OKID_HLC = 3, OKID_ANTI = 4, OKID_EVAL = 5,
                    OKID_REFINE = 6 };
 

@@ -84,4 +84,22 @@ cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, cons
 int scale_blocks(const ProbDev& P);
 size_t gr_qr_smem(int d);
 
+// Launch tables of the objective-independent kernels of a cycle over all problems of a
+// context (phase_kernels.cu): one grouped launch per kernel instead of one per problem,
+// each problem running the blocks its own launch would.
+struct AllTabs {
+  AllTab begin, fmax, lin, one, hclear, hspread;   // one entry per problem
+  AllTab dp2[5];                                   // problems of padded dimension 4 << k
+  unsigned nb_begin = 0, nb_fmax = 0, nb_lin = 0, nb_one = 0, nb_hclear = 0, nb_hspread = 0, nb_dp2[5] = {};
+  size_t qr_smem = 0;                              // the Golden Rooster QR's shared memory
+};
+// Builds the tables in one device allocation *mem (the caller frees it).
+cudaError_t build_all_tabs(const std::vector<ProbDev>& pd, const std::vector<StepParams>& sp, void** mem,
+                           AllTabs* out);
+cudaError_t launch_cycle_begin_all(const AllTabs& A, cudaStream_t st);
+cudaError_t launch_cycle_end_all(const AllTabs& A, cudaStream_t st);
+cudaError_t launch_freeze_all(const AllTabs& A, cudaStream_t st);   // Phase 2: f_max, stick mask, stuck list
+cudaError_t launch_dedup_all(const AllTabs& A, cudaStream_t st);    // Phase 3 and the sample lists
+cudaError_t launch_reseed_all(const AllTabs& A, cudaStream_t st);   // Phase 4
+
 }  // namespace chisao

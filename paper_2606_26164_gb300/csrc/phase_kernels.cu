@@ -14,21 +14,37 @@ constexpr int NT_LIN = 256;       // threads of the elementwise kernels
 constexpr int NT_ONE = 1024;      // threads of the single-block kernels
 
 // ------------------------------------------------------------ cycle bookkeeping
-__global__ void k_cycle_begin(ProbDev P) {
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < P.nwords; w += gridDim.x * blockDim.x) {
+// Every kernel below is a body taking its block index b and block count nb within the
+// problem, wrapped once as a launch over one problem (b = blockIdx.x, nb = gridDim.x)
+// and once as a launch over all the problems of a context (the *_all kernels: the block's
+// problem and position from the launch's AllTab), which computes the same bits.
+#define CHISAO_ALL_KERNEL(NAME, NT, BODY_CALL)                              \
+  __global__ void __launch_bounds__(NT) NAME##_all(AllTab T) {             \
+    const BlkPos pos = all_pos(T);                                        \
+    const ProbDev& P = T.probs[pos.q];                                    \
+    const StepParams& S = T.sps[pos.q];                                   \
+    (void)S;                                                              \
+    BODY_CALL;                                                            \
+  }
+
+__device__ __forceinline__ void cycle_begin_body(const ProbDev& P, unsigned b, unsigned nb) {
+  for (int w = b * blockDim.x + threadIdx.x; w < P.nwords; w += nb * blockDim.x) {
     P.stuck[w] = 0u;                 // Phase 1: release all
     P.removed[w] = 0u;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (b == 0 && threadIdx.x == 0) {
     P.cnt->fmax_key = 0u;
     P.cnt->n_stuck0 = 0;
     P.cnt->reseed_mode = RESEED_NONE;
   }
 }
+__global__ void k_cycle_begin(ProbDev P) { cycle_begin_body(P, blockIdx.x, gridDim.x); }
+CHISAO_ALL_KERNEL(k_cycle_begin, 256, cycle_begin_body(P, pos.b, pos.nb))
 
 __global__ void k_cycle_end(ProbDev P) {
   if (threadIdx.x == 0) P.cnt->cycle += 1;
 }
+CHISAO_ALL_KERNEL(k_cycle_end, 32, if (threadIdx.x == 0) P.cnt->cycle += 1)
 
 __global__ void k_set_cycle(ProbDev P, int completed) {
   if (threadIdx.x == 0) P.cnt->cycle = completed;
@@ -36,19 +52,21 @@ __global__ void k_set_cycle(ProbDev P, int completed) {
 
 // ------------------------------------------------------------ Phase 2
 // f_max over the finite f (max is order-independent, so atomics are exact).
-__global__ void __launch_bounds__(NT_LIN) k_fmax(ProbDev P) {
+__device__ __forceinline__ void fmax_body(const ProbDev& P, unsigned b, unsigned nb) {
   unsigned key = 0u;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (int i = b * blockDim.x + threadIdx.x; i < P.n; i += nb * blockDim.x) {
     const float v = P.f[i];
     if (isfinite(v)) key = max(key, fkey(v));
   }
   block_max_key<NT_LIN>(key, &P.cnt->fmax_key);
 }
+__global__ void __launch_bounds__(NT_LIN) k_fmax(ProbDev P) { fmax_body(P, blockIdx.x, gridDim.x); }
+CHISAO_ALL_KERNEL(k_fmax, NT_LIN, fmax_body(P, pos.b, pos.nb))
 
 // stuck_i = (|g_i|_inf < eps_grad) and (f_i >= fl(f_max + log delta)), binary32
 // compares; one warp ballot per 32 samples writes one mask word.
-__global__ void __launch_bounds__(NT_LIN) k_freeze(ProbDev P, StepParams S) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void freeze_body(const ProbDev& P, const StepParams& S, unsigned blk) {
+  const int i = blk * blockDim.x + threadIdx.x;
   const unsigned key = P.cnt->fmax_key;
   const float fmax = key ? fkey_inv(key) : -CUDART_INF_F;
   const float thr = fmax + S.log_delta;
@@ -72,6 +90,8 @@ __global__ void __launch_bounds__(NT_LIN) k_freeze(ProbDev P, StepParams S) {
   }
   if (i == 0) P.cnt->fmax = fmax;
 }
+__global__ void __launch_bounds__(NT_LIN) k_freeze(ProbDev P, StepParams S) { freeze_body(P, S, blockIdx.x); }
+CHISAO_ALL_KERNEL(k_freeze, NT_LIN, freeze_body(P, S, pos.b))
 
 // ------------------------------------------------------------ ordered compaction
 // One block; thread t owns a contiguous run of mask words; a block scan of the
@@ -112,14 +132,16 @@ __device__ __forceinline__ unsigned valid_mask(const ProbDev& P, int w) {
   return rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
 }
 
-__global__ void __launch_bounds__(NT_ONE) k_compact_stuck(ProbDev P) {
+__device__ __forceinline__ void compact_stuck_body(const ProbDev& P) {
   const int S = block_compact(P.nwords, [&](int w) { return P.stuck[w]; }, P.l_stuck);
   if (threadIdx.x == 0) P.cnt->n_stuck0 = S;
 }
+__global__ void __launch_bounds__(NT_ONE) k_compact_stuck(ProbDev P) { compact_stuck_body(P); }
+CHISAO_ALL_KERNEL(k_compact_stuck, NT_ONE, compact_stuck_body(P))
 
 // After deduplication: stuck &= ~removed, then the free-slot list (removed),
 // the unfrozen list (neither stuck nor removed) and the survivor list.
-__global__ void __launch_bounds__(NT_ONE) k_compact_dedup(ProbDev P) {
+__device__ __forceinline__ void compact_dedup_body(const ProbDev& P) {
   for (int w = threadIdx.x; w < P.nwords; w += NT_ONE) P.stuck[w] &= ~P.removed[w];
   __syncthreads();
   const int K = block_compact(P.nwords, [&](int w) { return P.removed[w]; }, P.l_free);
@@ -135,6 +157,8 @@ __global__ void __launch_bounds__(NT_ONE) k_compact_dedup(ProbDev P) {
     c->n_stuck = S;
   }
 }
+__global__ void __launch_bounds__(NT_ONE) k_compact_dedup(ProbDev P) { compact_dedup_body(P); }
+CHISAO_ALL_KERNEL(k_compact_dedup, NT_ONE, compact_dedup_body(P))
 
 // ------------------------------------------------------------ Phase 3
 // For every stuck x_j: removed iff some other stuck x_i ranks above it
@@ -171,10 +195,10 @@ __device__ __forceinline__ long long cell_of(float x, float lo, double h) {
 }
 
 // table slots empty, coordinate spreads reset
-__global__ void __launch_bounds__(NT_LIN) k_hash_clear(ProbDev P) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void hash_clear_body(const ProbDev& P, unsigned b, unsigned nb) {
+  const int t = b * blockDim.x + threadIdx.x;
   if (P.cnt->n_stuck0 == 0) return;
-  for (int s = t; s <= P.hmask; s += gridDim.x * blockDim.x) {
+  for (int s = t; s <= P.hmask; s += nb * blockDim.x) {
     P.hkey[s] = HASH_EMPTY;
     P.hbest[s] = 0ull;
     P.hhead[s] = -1;
@@ -184,10 +208,12 @@ __global__ void __launch_bounds__(NT_LIN) k_hash_clear(ProbDev P) {
     P.hspread[P.dp + t] = 0u;
   }
 }
+__global__ void __launch_bounds__(NT_LIN) k_hash_clear(ProbDev P) { hash_clear_body(P, blockIdx.x, gridDim.x); }
+CHISAO_ALL_KERNEL(k_hash_clear, NT_LIN, hash_clear_body(P, pos.b, pos.nb))
 
 // per-coordinate min and max over the stuck set
-__global__ void __launch_bounds__(NT_LIN) k_hash_spread(ProbDev P) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void hash_spread_body(const ProbDev& P, unsigned b) {
+  const long long t = (long long)b * blockDim.x + threadIdx.x;
   const int Sn = P.cnt->n_stuck0;
   if (t >= (long long)Sn * P.d) return;
   const int jj = (int)(t / P.d), a = (int)(t % P.d);
@@ -195,9 +221,11 @@ __global__ void __launch_bounds__(NT_LIN) k_hash_spread(ProbDev P) {
   atomicMin(&P.hspread[a], k);
   atomicMax(&P.hspread[P.dp + a], k);
 }
+__global__ void __launch_bounds__(NT_LIN) k_hash_spread(ProbDev P) { hash_spread_body(P, blockIdx.x); }
+CHISAO_ALL_KERNEL(k_hash_spread, NT_LIN, hash_spread_body(P, pos.b))
 
 // the (up to) three coordinates of largest spread, largest first (ties: lower index)
-__global__ void k_hash_axes(ProbDev P) {
+__device__ __forceinline__ void hash_axes_body(const ProbDev& P) {
   if (threadIdx.x != 0 || P.cnt->n_stuck0 == 0) return;
   int ax[3] = {-1, -1, -1};
   float sp[3] = {-1.f, -1.f, -1.f};
@@ -217,6 +245,8 @@ __global__ void k_hash_axes(ProbDev P) {
   }
   for (int r = 0; r < 3; ++r) P.haxes[r] = ax[r];
 }
+__global__ void k_hash_axes(ProbDev P) { hash_axes_body(P); }
+CHISAO_ALL_KERNEL(k_hash_axes, 32, hash_axes_body(P))
 
 __device__ __forceinline__ void sample_cells(const ProbDev& P, int i, double h, long long (&c)[3]) {
 #pragma unroll
@@ -234,8 +264,8 @@ __device__ __forceinline__ unsigned long long rank_key(float f, int i) {
 }
 
 // file every stuck sample under its cell key; each cell also keeps its top-ranked member
-__global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S) {
-  const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void hash_insert_body(const ProbDev& P, const StepParams& S, unsigned b) {
+  const int jj = b * blockDim.x + threadIdx.x;
   if (jj >= P.cnt->n_stuck0) return;
   const double h = (double)S.eps_dup * (1.0 + 1e-6);
   long long c[3];
@@ -251,12 +281,14 @@ __global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S)
   P.hnext[jj] = atomicExch(&P.hhead[slot], jj);
   atomicMax(&P.hbest[slot], rank_key(P.f[j], j));
 }
+__global__ void __launch_bounds__(NT_LIN) k_hash_insert(ProbDev P, StepParams S) { hash_insert_body(P, S, blockIdx.x); }
+CHISAO_ALL_KERNEL(k_hash_insert, NT_LIN, hash_insert_body(P, S, pos.b))
 
 template <int DP>
-__global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
+__device__ __forceinline__ void dedup_body(const ProbDev& P, const StepParams& S, unsigned b) {
   constexpr int LPS = DP / 2;
   const Grp<LPS> g;
-  const int jj = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int jj = (int)(((size_t)b * blockDim.x + threadIdx.x) / LPS);
   const int Sn = P.cnt->n_stuck0;
   if (jj >= Sn) return;
   const int j = P.l_stuck[jj];
@@ -314,6 +346,10 @@ __global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) {
       }
   if (rem && g.l == 0) atomicOr(&P.removed[j >> 5], 1u << (j & 31));
 }
+template <int DP>
+__global__ void __launch_bounds__(128) k_dedup_impl(ProbDev P, StepParams S) { dedup_body<DP>(P, S, blockIdx.x); }
+template <int DP>
+CHISAO_ALL_KERNEL(k_dedup_impl, 128, dedup_body<DP>(P, S, pos.b))
 
 // ------------------------------------------------------------ initial populations
 // Uniform: x_a = lo_a + u (hi_a - lo_a), u from the TAG_SEED stream (c0 = sample,
@@ -364,7 +400,7 @@ __global__ void __launch_bounds__(NT_LIN) k_seed(ProbDev P, StepParams S, int me
 //   Rooster while enabled and some survivor exists; it disables itself after
 //   gr_patience successive generations whose survivor count did not grow;
 //   otherwise a uniform redraw.
-__global__ void k_reseed_decide(ProbDev P, StepParams S) {
+__device__ __forceinline__ void reseed_decide_body(const ProbDev& P, const StepParams& S) {
   if (threadIdx.x != 0) return;
   Counters* c = P.cnt;
   const int K = c->n_free, U = c->n_unfrozen, Sv = c->n_surv;
@@ -385,12 +421,14 @@ __global__ void k_reseed_decide(ProbDev P, StepParams S) {
   }
   c->reseed_mode = mode;
 }
+__global__ void k_reseed_decide(ProbDev P, StepParams S) { reseed_decide_body(P, S); }
+CHISAO_ALL_KERNEL(k_reseed_decide, 32, reseed_decide_body(P, S))
 
 // Survivors ranked by (f desc, index asc): rank_j = #{i : i above j}.
-__global__ void __launch_bounds__(NT_LIN) k_gr_rank(ProbDev P) {
+__device__ __forceinline__ void gr_rank_body(const ProbDev& P, unsigned b) {
   if (P.cnt->reseed_mode != RESEED_GR) return;
   const int Sv = P.cnt->n_surv;
-  const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jj = b * blockDim.x + threadIdx.x;
   if (jj >= Sv) return;
   const int j = P.l_surv[jj];
   const float fj = P.f[j];
@@ -402,12 +440,14 @@ __global__ void __launch_bounds__(NT_LIN) k_gr_rank(ProbDev P) {
   }
   P.l_rank[r] = j;
 }
+__global__ void __launch_bounds__(NT_LIN) k_gr_rank(ProbDev P) { gr_rank_body(P, blockIdx.x); }
+CHISAO_ALL_KERNEL(k_gr_rank, NT_LIN, gr_rank_body(P, pos.b))
 
 // One Gaussian d x d matrix per Golden Rooster generation (FP64 Box-Muller on
 // the GR stream, row i / column block b), its Householder QR (Golub & Van
 // Loan, Algorithm 5.2.1) with Q accumulated explicitly, columns of Q flipped
 // so that diag(R) > 0.  Q is written column-major to grq.
-__global__ void __launch_bounds__(NT_LIN) k_gr_qr(ProbDev P, StepParams S) {
+__device__ __forceinline__ void gr_qr_body(const ProbDev& P, const StepParams& S) {
   if (P.cnt->reseed_mode != RESEED_GR) return;
   extern __shared__ double sm[];
   const int d = P.d;
@@ -485,6 +525,8 @@ __global__ void __launch_bounds__(NT_LIN) k_gr_qr(ProbDev P, StepParams S) {
     P.grq[c * d + r] = sg * Q[r * d + c];
   }
 }
+__global__ void __launch_bounds__(NT_LIN) k_gr_qr(ProbDev P, StepParams S) { gr_qr_body(P, S); }
+CHISAO_ALL_KERNEL(k_gr_qr, NT_LIN, gr_qr_body(P, S))
 
 // Largest t >= 0 keeping p + t u inside the box, reduced over the group.
 template <int LPS>
@@ -503,12 +545,12 @@ __device__ __forceinline__ float ray_exit(float p0, float p1, float u0, float u1
 
 // Fill free slot r (r-th removed sample in index order) by the chosen strategy.
 template <int DP>
-__global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
+__device__ __forceinline__ void reseed_body(const ProbDev& P, const StepParams& S, unsigned b) {
   constexpr int LPS = DP / 2;
   const Grp<LPS> g;
   const int mode = P.cnt->reseed_mode;
   const int K = P.cnt->n_free;
-  const int r = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  const int r = (int)(((size_t)b * blockDim.x + threadIdx.x) / LPS);
   if (mode == RESEED_NONE || r >= K) return;
   const int slot = P.l_free[r];
   const int d = P.d, j0 = 2 * g.l;
@@ -557,6 +599,10 @@ __global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) {
   *reinterpret_cast<float2*>(P.x + (size_t)slot * DP + j0) = make_float2(c0, c1);
   if (g.l == 0) P.hlen[slot] = 0;
 }
+template <int DP>
+__global__ void __launch_bounds__(128) k_reseed(ProbDev P, StepParams S) { reseed_body<DP>(P, S, blockIdx.x); }
+template <int DP>
+CHISAO_ALL_KERNEL(k_reseed, 128, reseed_body<DP>(P, S, pos.b))
 
 // ------------------------------------------------------------ Phase 5/6 scales
 // Fixed-order sum of the per-block partials, then
@@ -725,7 +771,9 @@ cudaError_t launch_dedup(const ProbDev& P, const StepParams& S, cudaStream_t st)
 size_t gr_qr_smem(int d) { return sizeof(double) * (2 * (size_t)d * d + 2 * (size_t)d); }
 
 cudaError_t prepare_kernel_attributes() {
-  return cudaFuncSetAttribute(k_gr_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gr_qr_smem(64));
+  const cudaError_t e = cudaFuncSetAttribute(k_gr_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gr_qr_smem(64));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gr_qr_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gr_qr_smem(64));
 }
 
 template <int DP>
@@ -746,6 +794,134 @@ cudaError_t launch_reseed(const ProbDev& P, const StepParams& S, cudaStream_t st
     case 64: reseed_dp<64>(P, S, st); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ launches over all problems
+// Each table lists the problems (or, for the kernels templated on the padded dimension,
+// the problems of one dp) with the block count their own launch would use, so every
+// problem runs the same blocks as on its own.
+static int dp_slot(int dp) {
+  int k = 0;
+  while ((4 << k) < dp) ++k;
+  return k;
+}
+
+cudaError_t build_all_tabs(const std::vector<ProbDev>& pd, const std::vector<StepParams>& sp, void** mem,
+                           AllTabs* out) {
+  const int nq = (int)pd.size();
+  std::vector<std::vector<int>> firsts;              // one per table, in the order of `tabs` below
+  std::vector<std::vector<int>> qidx;
+  auto table = [&](auto blocks_of, const std::vector<int>& members) {
+    std::vector<int> f(1, 0);
+    for (int q : members) f.push_back(f.back() + (int)blocks_of(pd[q]));
+    firsts.push_back(f);
+    qidx.push_back(members);
+  };
+  std::vector<int> all(nq);
+  for (int q = 0; q < nq; ++q) all[q] = q;
+  table([](const ProbDev& P) { return lin_blocks(P.nwords, NT_LIN); }, all);                              // begin
+  table([](const ProbDev& P) { const unsigned nb = lin_blocks(P.n, NT_LIN); return nb < 1216 ? nb : 1216u; }, all);
+  table([](const ProbDev& P) { return lin_blocks(P.n, NT_LIN); }, all);                                   // lin
+  table([](const ProbDev&) { return 1u; }, all);                                                          // one
+  table([](const ProbDev& P) {
+    return (unsigned)std::min<long long>(lin_blocks((long long)P.hmask + 1, NT_LIN), 1024); }, all);      // hclear
+  table([](const ProbDev& P) { return lin_blocks((long long)P.n * P.d, NT_LIN); }, all);                  // hspread
+  for (int k = 0; k < 5; ++k) {
+    std::vector<int> m;
+    for (int q = 0; q < nq; ++q)
+      if (dp_slot(pd[q].dp) == k) m.push_back(q);
+    table([](const ProbDev& P) { return lin_blocks((long long)P.n * (P.dp / 2), 128); }, m);              // dp2
+  }
+  size_t total = 0;
+  auto up = [](size_t o) { return (o + 255) / 256 * 256; };
+  const size_t off_pd = total;
+  total = up(total + nq * sizeof(ProbDev));
+  const size_t off_sp = total;
+  total = up(total + nq * sizeof(StepParams));
+  std::vector<size_t> off_f(firsts.size()), off_q(firsts.size());
+  for (size_t t = 0; t < firsts.size(); ++t) {
+    off_f[t] = total;
+    total = up(total + firsts[t].size() * sizeof(int));
+    off_q[t] = total;
+    total = up(total + std::max<size_t>(qidx[t].size(), 1) * sizeof(int));
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(mem, total)) != cudaSuccess) return e;
+  char* base = static_cast<char*>(*mem);
+  if ((e = cudaMemcpy(base + off_pd, pd.data(), nq * sizeof(ProbDev), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(base + off_sp, sp.data(), nq * sizeof(StepParams), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  AllTab* tabs[] = {&out->begin, &out->fmax, &out->lin, &out->one, &out->hclear, &out->hspread, &out->dp2[0],
+                    &out->dp2[1], &out->dp2[2], &out->dp2[3], &out->dp2[4]};
+  unsigned* blocks[] = {&out->nb_begin, &out->nb_fmax, &out->nb_lin, &out->nb_one, &out->nb_hclear, &out->nb_hspread,
+                        &out->nb_dp2[0], &out->nb_dp2[1], &out->nb_dp2[2], &out->nb_dp2[3], &out->nb_dp2[4]};
+  for (size_t t = 0; t < firsts.size(); ++t) {
+    if ((e = cudaMemcpy(base + off_f[t], firsts[t].data(), firsts[t].size() * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+    if (!qidx[t].empty() && (e = cudaMemcpy(base + off_q[t], qidx[t].data(), qidx[t].size() * sizeof(int),
+                                            cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+    AllTab& T = *tabs[t];
+    T.probs = reinterpret_cast<const ProbDev*>(base + off_pd);
+    T.sps = reinterpret_cast<const StepParams*>(base + off_sp);
+    T.first = reinterpret_cast<const int*>(base + off_f[t]);
+    T.qidx = t >= 6 ? reinterpret_cast<const int*>(base + off_q[t]) : nullptr;
+    T.n = (int)qidx[t].size();
+    *blocks[t] = (unsigned)firsts[t].back();
+  }
+  int dmax = 1;
+  for (const ProbDev& P : pd) dmax = std::max(dmax, P.d);
+  out->qr_smem = gr_qr_smem(dmax);
+  return cudaSuccess;
+}
+
+cudaError_t launch_cycle_begin_all(const AllTabs& A, cudaStream_t st) {
+  k_cycle_begin_all<<<A.nb_begin, NT_LIN, 0, st>>>(A.begin);
+  return cudaGetLastError();
+}
+cudaError_t launch_cycle_end_all(const AllTabs& A, cudaStream_t st) {
+  k_cycle_end_all<<<A.nb_one, 32, 0, st>>>(A.one);
+  return cudaGetLastError();
+}
+cudaError_t launch_freeze_all(const AllTabs& A, cudaStream_t st) {
+  k_fmax_all<<<A.nb_fmax, NT_LIN, 0, st>>>(A.fmax);
+  k_freeze_all<<<A.nb_lin, NT_LIN, 0, st>>>(A.lin);
+  k_compact_stuck_all<<<A.nb_one, NT_ONE, 0, st>>>(A.one);
+  return cudaGetLastError();
+}
+template <int DP>
+static void dedup_all_dp(const AllTabs& A, int k, cudaStream_t st) {
+  if (A.dp2[k].n > 0) k_dedup_impl_all<DP><<<A.nb_dp2[k], 128, 0, st>>>(A.dp2[k]);
+}
+template <int DP>
+static void reseed_all_dp(const AllTabs& A, int k, cudaStream_t st) {
+  if (A.dp2[k].n > 0) k_reseed_all<DP><<<A.nb_dp2[k], 128, 0, st>>>(A.dp2[k]);
+}
+// Phase 3 of every problem (the masks were cleared at the cycle's start).
+cudaError_t launch_dedup_all(const AllTabs& A, cudaStream_t st) {
+  k_hash_clear_all<<<A.nb_hclear, NT_LIN, 0, st>>>(A.hclear);
+  k_hash_spread_all<<<A.nb_hspread, NT_LIN, 0, st>>>(A.hspread);
+  k_hash_axes_all<<<A.nb_one, 32, 0, st>>>(A.one);
+  k_hash_insert_all<<<A.nb_lin, NT_LIN, 0, st>>>(A.lin);
+  dedup_all_dp<4>(A, 0, st);
+  dedup_all_dp<8>(A, 1, st);
+  dedup_all_dp<16>(A, 2, st);
+  dedup_all_dp<32>(A, 3, st);
+  dedup_all_dp<64>(A, 4, st);
+  k_compact_dedup_all<<<A.nb_one, NT_ONE, 0, st>>>(A.one);
+  return cudaGetLastError();
+}
+cudaError_t launch_reseed_all(const AllTabs& A, cudaStream_t st) {
+  k_reseed_decide_all<<<A.nb_one, 32, 0, st>>>(A.one);
+  k_gr_rank_all<<<A.nb_lin, NT_LIN, 0, st>>>(A.lin);
+  k_gr_qr_all<<<A.nb_one, NT_LIN, A.qr_smem, st>>>(A.one);
+  reseed_all_dp<4>(A, 0, st);
+  reseed_all_dp<8>(A, 1, st);
+  reseed_all_dp<16>(A, 2, st);
+  reseed_all_dp<32>(A, 3, st);
+  reseed_all_dp<64>(A, 4, st);
   return cudaGetLastError();
 }
 
