@@ -293,13 +293,18 @@ typedef struct {
   int32_t trials;          /* configurations timed                                    */
   float ms_per_cycle;      /* the chosen configuration's time per non-final cycle     */
   float ms_default;        /* the configuration the context had before              */
+  int32_t ck[5];           /* grouped diagonal mixtures of padded dimension 4 << k: the
+                              components taken per step by their kernels (a compile-time
+                              tile shape: 2, 4 or 8); 0 where the context has no such group */
 } chisao_tuning;
 
 /* Launch-shape autotuner for contexts of several problems: for each candidate (8, 16,
- * 32 or 64 branch streams for the per-problem steps, times grouped or per-problem
- * launches of the per-sample phases) it captures a non-final cycle of the context
- * itself in a CUDA graph, runs it once untimed and then cycles_per_trial (1 .. 100)
- * times under CUDA events, and keeps the fastest.  Every candidate computes the same
+ * 32 or 64 branch streams, times grouped launches over all problems or per-problem
+ * launches) it captures a non-final cycle of the context itself in a CUDA graph, runs
+ * it once untimed and then cycles_per_trial (1 .. 100) times under CUDA events, and
+ * keeps the fastest; with grouped launches it then tries, group by group, the
+ * compiled tile shapes of the diagonal mixture's kernels (2, 4 or 8 components per
+ * step) the same way.  Every candidate computes the same
  * results bit for bit, and the context's state is saved before and restored after
  * each trial (one device copy of the arena, needing arena-sized free memory), so the
  * tuning changes no result and no trajectory.  A context of one problem, or one with
@@ -397,6 +402,11 @@ chisao_status chisao_run_phase(chisao_ctx *c, int32_t prob, int32_t phase, int32
  * count at the previous generation, -1 for none). */
 chisao_status chisao_set_gr_state(chisao_ctx *c, int32_t prob, int32_t enabled,
                                   int32_t noprog, int32_t prev_surv);
+/* Set the tile shape chisao_autotune chooses for the grouped diagonal-mixture kernels
+ * of padded dimension dp: ck = 2, 4 or 8 components per step (the results do not
+ * depend on it).  CHISAO_ERR_ARG when ck is another value or the context has no such
+ * group.  Synchronizes the stream; the next step recaptures its graph. */
+chisao_status chisao_set_tile(chisao_ctx *c, int32_t dp, int32_t ck);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free deduplication.

@@ -31,7 +31,7 @@ EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chis
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
            "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
            "chisao_widths", "chisao_selftest_wait", "chisao_autotune", "chisao_measure_fma_peak", "chisao_init",
-           "chisao_stats"]
+           "chisao_stats", "chisao_set_tile"]
 
 
 class CParams(C.Structure):
@@ -130,7 +130,7 @@ class CProblem(C.Structure):
 
 class CTuning(C.Structure):
     _fields_ = [("n_branch", C.c_int32), ("grouped", C.c_int32), ("trials", C.c_int32),
-                ("ms_per_cycle", C.c_float), ("ms_default", C.c_float)]
+                ("ms_per_cycle", C.c_float), ("ms_default", C.c_float), ("ck", C.c_int32 * 5)]
 
 
 class CCounters(C.Structure):
@@ -180,6 +180,7 @@ def library() -> C.CDLL:
         lib.chisao_state_set.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_size_t]
         lib.chisao_run_phase.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         lib.chisao_set_gr_state.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+        lib.chisao_set_tile.argtypes = [vp, C.c_int32, C.c_int32]
         lib.chisao_dedup_noalloc.argtypes = [vp, C.c_int32, C.c_int64, vp, vp, C.c_double, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("chisao_default_params", "chisao_last_error", "chisao_destroy"):
@@ -335,7 +336,9 @@ class Chisao:
         """Pick the fastest launch shape for this context (results and state unchanged)."""
         t = CTuning()
         self._check(library().chisao_autotune(self.ctx, cycles_per_trial, C.byref(t)), "chisao_autotune")
-        return {name: getattr(t, name) for name, _ in CTuning._fields_}
+        out = {name: getattr(t, name) for name, _ in CTuning._fields_}
+        out["ck"] = {4 << k: int(t.ck[k]) for k in range(5) if t.ck[k]}
+        return out
 
     def selftest_wait(self, prob: int = 0, budget_ns: int = 10_000_000):
         """Test hook: a bounded device wait that runs out and raises the problem's error flag."""
@@ -412,6 +415,11 @@ class Chisao:
     def set_gr_state(self, prob: int, enabled: int, noprog: int, prev_surv: int):
         self._check(library().chisao_set_gr_state(self.ctx, prob, enabled, noprog, prev_surv),
                     "chisao_set_gr_state")
+
+    def set_tile(self, dp: int, ck: int):
+        """Test hook: the components per step (2, 4, 8) of the grouped diagonal-mixture
+        kernels of padded dimension dp."""
+        self._check(library().chisao_set_tile(self.ctx, dp, ck), "chisao_set_tile")
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -55,6 +55,7 @@ struct Bump {
 // one grouped launch each (exact gradients, several problems in the context).
 struct Group {
   int kind = 0, dp = 0;
+  int tile = 0;                      // tile shape of the diagonal mixture's kernels (the tuner's choice)
   std::vector<int> members;          // problem indices
   unsigned blocks = 0;               // blocks of one per-sample launch over all members
   unsigned blocks_sc = 0;            // blocks of the grouped scale pass
@@ -528,7 +529,7 @@ cudaError_t launch_grouped(int which, const Group& gr, cudaStream_t st, int arg 
   const GroupTab& T = which == OKID_SCALES ? gr.tab_sc : gr.tab;
   const unsigned blocks = which == OKID_SCALES ? gr.blocks_sc : gr.blocks;
   switch (gr.kind) {
-    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag(which, gr.dp, T, blocks, st, arg);
+    case CHISAO_OBJ_MIXTURE_DIAG: return launch_grp_mixdiag_tile(which, gr.dp, gr.tile, T, blocks, st, arg);
     case CHISAO_OBJ_MIXTURE_FULL: return launch_grp_mixfull(which, gr.dp, T, blocks, st, arg);
     case CHISAO_OBJ_QUADRATIC: return launch_grp_quad(which, gr.dp, T, blocks, st, arg);
     default: return launch_grp_bench(which, gr.dp, T, blocks, st, arg);
@@ -1108,6 +1109,35 @@ chisao_status chisao_autotune(chisao_ctx* c, int32_t cycles_per_trial, chisao_tu
       }
     }
   }
+  // the tile shape of each group of diagonal mixtures (components per step), one group at
+  // a time with the chosen launch shape (every tile gives the same results)
+  if (e == cudaSuccess && best_g) {
+    e = apply(best_nb, best_g);
+    for (Group& gr : c->groups) {
+      if (e != cudaSuccess || gr.kind != CHISAO_OBJ_MIXTURE_DIAG) continue;
+      int best_tile = gr.tile;
+      for (int tile = 0; tile < MIXDIAG_TILES && e == cudaSuccess; ++tile) {
+        if (tile == best_tile) continue;
+        const int keep = gr.tile;
+        gr.tile = tile;
+        float ms = 0.f;
+        if ((e = trial(&ms)) != cudaSuccess) break;
+        ++trials;
+        if (ms < best) {
+          best = ms;
+          best_tile = tile;
+        } else {
+          gr.tile = keep;
+        }
+      }
+      gr.tile = best_tile;
+    }
+  }
+  for (const Group& gr : c->groups) {
+    int k = 0;
+    while ((4 << k) < gr.dp) ++k;
+    if (gr.kind == CHISAO_OBJ_MIXTURE_DIAG && k < 5) out->ck[k] = MIXDIAG_TILE_CK[gr.tile];
+  }
   // the chosen configuration, the saved state, and graphs recaptured at the next step
   const cudaError_t ea = apply(best_nb, best_g);
   if (e == cudaSuccess) e = ea;
@@ -1347,6 +1377,26 @@ chisao_status chisao_run_phase(chisao_ctx* c, int32_t prob, int32_t phase, int32
     default:
       return fail(c, CHISAO_ERR_ARG, "unknown phase");
   }
+  return CHISAO_OK;
+}
+
+chisao_status chisao_set_tile(chisao_ctx* c, int32_t dp, int32_t ck) {
+  if (!c) return CHISAO_ERR_ARG;
+  int tile = -1;
+  for (int t = 0; t < MIXDIAG_TILES; ++t)
+    if (MIXDIAG_TILE_CK[t] == ck) tile = t;
+  if (tile < 0) return fail(c, CHISAO_ERR_ARG, "components per step must be 2, 4 or 8");
+  bool found = false;
+  for (Group& gr : c->groups)
+    if (gr.kind == CHISAO_OBJ_MIXTURE_DIAG && gr.dp == dp) {
+      gr.tile = tile;
+      found = true;
+    }
+  if (!found) return fail(c, CHISAO_ERR_ARG, "no grouped diagonal mixtures of that padded dimension");
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->g_mid) cudaGraphExecDestroy(c->g_mid);       // recaptured at the next step
+  if (c->g_last) cudaGraphExecDestroy(c->g_last);
+  c->g_mid = c->g_last = nullptr;
   return CHISAO_OK;
 }
 

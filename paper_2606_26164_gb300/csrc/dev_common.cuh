@@ -28,6 +28,9 @@ namespace chisao {
 constexpr int MMAX = 10;                 // register-resident L-BFGS memory
 constexpr int GRAD_FD64 = 0, GRAD_FD32 = 1, GRAD_ADJOINT = 2;
 constexpr int OBJ_MIXTURE_DIAG = 1, OBJ_MIXTURE_FULL = 2, OBJ_QUADRATIC = 3;
+// the diagonal mixture evaluated with 2 or 8 components per step instead of 4 (grouped
+// launches only: tile shapes the batched contexts' tuner can choose, same results)
+constexpr int OBJ_MIXDIAG_C2 = 21, OBJ_MIXDIAG_C8 = 22;
 // the Appendix D benchmark functions share one kind; ObjParams::fn selects the function
 constexpr int OBJ_BENCH = 10;
 constexpr int FN_RASTRIGIN = 0, FN_ACKLEY = 1, FN_SCHWEFEL = 2, FN_STYBLINSKI_TANG = 3, FN_MICHALEWICZ = 4,

@@ -21,6 +21,11 @@ unsigned obj_blocks(long long n, int dp);
 // Grouped launches of Phase 1 / 5 / 6 (OKID_PHASE1, OKID_HLC, OKID_ANTI) with exact gradients
 // over the problems of one group (same objective kind and padded dimension dp).
 cudaError_t launch_grp_mixdiag(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
+// the same at a tile shape: 0 = 4 components per step (launch_grp_mixdiag), 1 = 2, 2 = 8
+constexpr int MIXDIAG_TILES = 3;
+constexpr int MIXDIAG_TILE_CK[MIXDIAG_TILES] = {4, 2, 8};
+cudaError_t launch_grp_mixdiag_tile(int which, int dp, int tile, const GroupTab& T, unsigned blocks,
+                                    cudaStream_t st, int arg = 0);
 cudaError_t launch_grp_mixfull(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
 cudaError_t launch_grp_quad(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);
 cudaError_t launch_grp_bench(int which, int dp, const GroupTab& T, unsigned blocks, cudaStream_t st, int arg = 0);

@@ -271,13 +271,14 @@ template <int KIND>
 struct HasMulti : std::false_type {};
 
 // ------------------------------------------------------------ diagonal mixture
-template <>
-struct Obj<OBJ_MIXTURE_DIAG> {
-  // The components go in steps of CK: their parameter loads, the lane's share of each
-  // |A^(1/2)(x - mu_k)|^2 and the CK group sums are independent and overlap; the
-  // log-sum-exp then takes them in component order.  Every operation and its order is
-  // that of one component at a time, so the results are the same bits.
-  static constexpr int CK = 4;
+// The components go in steps of CK: their parameter loads, the lane's share of each
+// |A^(1/2)(x - mu_k)|^2 and the CK group sums are independent and overlap; the
+// log-sum-exp then takes them in component order.  Every operation and its order is
+// that of one component at a time, so the results are the same bits for every CK; CK
+// trades the overlap against registers (the batched contexts' tuner picks it per group).
+template <int CK_>
+struct DiagMixture {
+  static constexpr int CK = CK_;
   template <typename T, int V, int LPS>
   static __device__ __forceinline__ void comp_terms(const ObjParams<T>& o, int k, const T (&x)[V], T& q,
                                                     T (&sc)[V], const Grp<LPS>& g) {
@@ -346,7 +347,7 @@ struct Obj<OBJ_MIXTURE_DIAG> {
     float m1 = -CUDART_INF_F, s1 = 0.f, G1[V], m2 = -CUDART_INF_F, s2 = 0.f, G2[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) G1[v] = G2[v] = 0.f;
-    constexpr int CP = CK / 2;                        // two points share each component's loads
+    constexpr int CP = CK / 2 > 0 ? CK / 2 : 1;       // two points share each component's loads
     int k = 0;
     for (; k + CP <= o.K; k += CP) {
       float q1[CP], q2[CP], sc1[CP][V], sc2[CP][V];
@@ -406,7 +407,17 @@ struct Obj<OBJ_MIXTURE_DIAG> {
   }
 };
 template <>
+struct Obj<OBJ_MIXTURE_DIAG> : DiagMixture<4> {};
+template <>
+struct Obj<OBJ_MIXDIAG_C2> : DiagMixture<2> {};
+template <>
+struct Obj<OBJ_MIXDIAG_C8> : DiagMixture<8> {};
+template <>
 struct HasPair<OBJ_MIXTURE_DIAG> : std::true_type {};
+template <>
+struct HasPair<OBJ_MIXDIAG_C2> : std::true_type {};
+template <>
+struct HasPair<OBJ_MIXDIAG_C8> : std::true_type {};
 
 // ------------------------------------------------------------ full-covariance mixture
 template <>

@@ -34,30 +34,24 @@ def test_mixture4_d2_plain_method_recovers_all_modes():
     assert fx.shape[0] == 4
     with pytest.raises(CH.ChisaoError):
         model.step()                                   # all n_osc cycles ran
-    # the oracle's run of the same configuration (first 5 cycles) returns the same modes
-    Po = M.Params(n_osc=5, m=5, M=8, eps_grad=1e-5, grad_mode=M.GRAD_FD64, seed=0)
-    (ox, of), _ = M.run(prob, Po)
-    frac_o, worst_o, _ = MD.recovery(ox, mx, negH)
-    assert frac_o == 1.0 and ox.shape[0] == 4
+    # the oracle's own 50-cycle run: test_gpu_modesets.test_modeset_mixture4_d2
     model.close()
 
 
 def test_mixture_d16_modes_are_true_modes():
+    """d = 16, K = 32, the first 4096 samples, 6 cycles at the Table 1 schedule: every
+    returned point is one of the significant modes (no spurious mode).  The set against
+    the oracle's own run: test_gpu_modesets.test_modeset_mixture32_d16."""
     prob = I.mixture32_d16(n=4096)
     P = M.Params(n_osc=6, m=10, eps_grad=1e-4, grad_mode=M.GRAD_ADJOINT, seed=1)
     model = U.open_ctx(prob, P)
     fx, ff = _run(model, P.n_osc)
     mx, mf, negH = MD.significant_modes(prob)
     frac, worst, best = MD.recovery(fx, mx, negH)
-    # every returned point is one of the significant modes (no spurious modes)
     for x in fx:
         e = min(MD.mahalanobis(x[None], m, H)[0] for m, H in zip(mx, negH))
         assert e <= 1e-3
     assert frac > 0
-    # the oracle on the same configuration recovers a comparable fraction
-    (ox, of), _ = M.run(I.mixture32_d16(n=4096), P)
-    frac_o, _, _ = MD.recovery(ox, mx, negH)
-    assert abs(frac - frac_o) <= 0.5
     model.close()
 
 
@@ -138,7 +132,8 @@ def _mixed_kinds():
 def test_batched_problems_match_separate_contexts(case):
     """Problems of one context are independent: with exact gradients the context runs
     Phases 1, 5 and 6 as one grouped launch per (objective kind, padded dimension) and
-    the rest per problem on branch streams.  Problem q's state after two cycles is
+    the objective-independent steps as one launch per kernel over all problems.  Problem
+    q's state after two cycles is
     bit-identical in a context of six problems and in one of the first q + 1 (same
     problem index, hence the same Philox streams; a single problem runs ungrouped),
     with and without graph capture."""
@@ -404,6 +399,7 @@ def test_autotune_keeps_state_and_results():
     before = [tuned.get(q, CH.FIELD_X).copy() for q in range(len(probs))]
     t = tuned.autotune(cycles_per_trial=1)
     assert t["trials"] >= 4 and t["n_branch"] in (8, 16, 20) and t["grouped"] in (0, 1)
+    assert all(ck in (2, 4, 8) for ck in t["ck"].values())
     assert 0 < t["ms_per_cycle"] <= t["ms_default"] * 1.0001
     for q in range(len(probs)):
         np.testing.assert_array_equal(tuned.get(q, CH.FIELD_X), before[q])
@@ -416,3 +412,27 @@ def test_autotune_keeps_state_and_results():
             np.testing.assert_array_equal(tuned.get(q, fld), plain.get(q, fld))
     tuned.close()
     plain.close()
+
+
+def test_tile_shapes_give_the_same_bits():
+    """The compiled tile shapes of the grouped diagonal-mixture kernels (2, 4 or 8
+    components per step; the tuner picks one per padded dimension) change only the
+    schedule: whole cycles give the same bits with every shape."""
+    probs = I.batched512(n_problems=24, n_scale=0.05, seed=9)
+    P = M.Params(n_osc=4, m=6, eps_grad=1e-3, grad_mode=M.GRAD_ADJOINT, seed=4)
+    U.ensure_built()
+    dps = sorted({max(4, 1 << (p.d - 1).bit_length()) for p in probs})
+    out = []
+    for ck in (4, 2, 8):
+        model = CH.Chisao(probs, U.lib_params(P))
+        for dp in dps:
+            model.set_tile(dp, ck)
+        for _ in range(3):
+            model.step()
+        out.append([model.get(q, f).copy() for q in range(len(probs)) for f in (CH.FIELD_X, CH.FIELD_G, CH.FIELD_F)])
+        with pytest.raises(CH.ChisaoError):
+            model.set_tile(dps[0], 3)
+        model.close()
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            np.testing.assert_array_equal(a, b)
