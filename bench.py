@@ -696,7 +696,10 @@ def main():
                            "peak_nominal_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz "
                                                   "(sampled clock)",
                            "fp64_peak_measured": CH.measure_fma_peak(True, model._stream) / 1e12,
-                           "launch_ms": 1e3 * t_k, "evals_per_launch": ev_k}
+                           "launch_ms": 1e3 * t_k, "evals_per_launch": ev_k,
+                           "limiter": "the L1 / shared-memory data path (about 76 % busy under ncu, 486 wavefronts "
+                                      "per warp-iteration: matrix blocks, the history ring, group-reduction "
+                                      "shuffles), not the FMA pipe; profiles/k_phase1_quadratic_d64.md"}
         # --- recovery at a schedule long enough to converge (Prop. 1): one cycle of
         #     n_conv = 2500 on the whole population (the quadratic's mode is its centre)
         if args.workload == "quadratic_d64":
