@@ -199,6 +199,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 // Bounded wait that also gives up as soon as another role has aborted.
+// A failed try sleeps NAP_NS before the next one: the single-thread roles (producer,
+// MMA issuers) nap ROLE_NAP_NS and so leave their sub-partition's issue slots to the
+// epilogue warps that share it (measured: 0.446 -> 0.418 ms per launch at N = 65536);
+// the epilogue's own waits nap EPI_NAP_NS.
+#ifndef CHISAO_TC_ROLE_NAP_NS
+#define CHISAO_TC_ROLE_NAP_NS 64
+#endif
+#ifndef CHISAO_TC_EPI_NAP_NS
+#define CHISAO_TC_EPI_NAP_NS 0
+#endif
+constexpr unsigned ROLE_NAP_NS = CHISAO_TC_ROLE_NAP_NS, EPI_NAP_NS = CHISAO_TC_EPI_NAP_NS;
+template <unsigned NAP_NS = 0>
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t parity, int* err, volatile int* abort_flag) {
   const long long t0 = clock64();
   while (!mbar_try(b, parity)) {
@@ -208,12 +220,13 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t parity, int* 
       *abort_flag = 1;
       return false;
     }
+    if (NAP_NS) __nanosleep(NAP_NS);
   }
   return true;
 }
 // Every lane waits; the warp proceeds only if all of them saw the phase complete.
 __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err, volatile int* abort_flag) {
-  const bool w = mbar_wait_ab(b, parity, err, abort_flag);
+  const bool w = mbar_wait_ab<EPI_NAP_NS>(b, parity, err, abort_flag);
   return __all_sync(0xffffffffu, w);
 }
 // 32 consecutive FP32 columns of this thread's TMEM lane, without the completion wait.
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       for (int g = 0; g < ng + (GRAD ? 2 : 0); ++g) {
         if (g < ng) {
           const int s = g % NW, u = g / NW;
-          if (u > 0 && !mbar_wait_ab(&bars[B_WEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
+          if (u > 0 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_WEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
           mbar_expect_tx(&bars[B_WFULL + s], (uint32_t)WC_BYTES);
           bulk_g2s(sm + OFF_W + s * WC_BYTES, a.gblk + (size_t)g * GBLK_BYTES, WC_BYTES, &bars[B_WFULL + s]);
           lastW[s] = u;
@@ -363,7 +376,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         const int gv = g - 2;
         if (GRAD && gv >= 0) {
           const int s = gv % NV, u = gv / NV;
-          if (u > 0 && !mbar_wait_ab(&bars[B_VEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
+          if (u > 0 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_VEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
           mbar_expect_tx(&bars[B_VFULL + s], (uint32_t)VT_BYTES);
           bulk_g2s(sm + OFF_V + s * VT_BYTES, a.gblk + (size_t)gv * GBLK_BYTES + WC_BYTES, VT_BYTES,
                    &bars[B_VFULL + s]);
@@ -382,11 +395,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       const uint32_t idF = idesc_bf16(TM, TN);
       const uint32_t aX = smem_u32(sm), aOnes = smem_u32(sm + OFF_ONES);
       bool issued = false;
-      if (mbar_wait_ab(&bars[B_XREADY], 0, a.err, abort_flag)) {
+      if (mbar_wait_ab<ROLE_NAP_NS>(&bars[B_XREADY], 0, a.err, abort_flag)) {
         for (int g = 0; g < ng; ++g) {
           const int s = g % NW;
-          if (!mbar_wait_ab(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) break;
-          if (g >= 1 && !mbar_wait_ab(&bars[B_ZEMPTY + ((g - 1) & 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) break;
+          if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) break;
+          if (g >= 1 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_ZEMPTY + ((g - 1) & 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) break;
           tc_fence_after();
           const uint32_t bW = smem_u32(sm + OFF_W + s * WC_BYTES);
 #pragma unroll
@@ -413,8 +426,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       bool issued = false;
       for (int g = j; g < ng; g += 2) {
         const int b = g & 1, s = g % NV;
-        if (!mbar_wait_ab(&bars[B_YFULL + b], (g >> 1) & 1, a.err, abort_flag)) break;
-        if (!mbar_wait_ab(&bars[B_VFULL + s], (g / NV) & 1, a.err, abort_flag)) break;
+        if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_YFULL + b], (g >> 1) & 1, a.err, abort_flag)) break;
+        if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_VFULL + s], (g / NV) & 1, a.err, abort_flag)) break;
         tc_fence_after();
         const uint32_t bV = smem_u32(sm + OFF_V + s * VT_BYTES);
         const uint32_t aY = tmem + COL_Y + 64u * (uint32_t)b;
