@@ -66,10 +66,11 @@ def launches_per_step(params, tc, d):
     if not tc:
         return KERNELS_PER_STEP
     n_conv = params.n_conv or max(10, int(np.ceil(3 * np.log2(d))))
-    # cycle begin + first evaluation, per L-BFGS iteration one direction kernel and T_ls
-    # (evaluation, acceptance) pairs, freeze (3) / dedup (6) / reseed (4), HLC and anti with
-    # their scale passes, cycle end
-    return (2 + n_conv * (1 + 2 * params.T_ls) + 13 + (3 + 3 * params.n_cloud)
+    rounds = 1 + -(-(params.T_ls - 1) // 4)          # line-search rounds: 1 trial, then 4 at a time
+    # cycle begin + first evaluation, per L-BFGS iteration one direction kernel and one
+    # (evaluation, acceptance) pair per round, the history rotation, freeze (3) / dedup (6) /
+    # reseed (4), HLC and anti with their scale passes, cycle end
+    return (2 + n_conv * (1 + 2 * rounds) + 1 + 13 + (3 + 3 * params.n_cloud)
             + (2 + 2 * params.n_anti) + 1)
 
 

@@ -31,6 +31,8 @@ struct ProbHost {
   float* gather_x = nullptr;
   float* gather_f = nullptr;
   uint8_t* tc_weights = nullptr;     // tensor-core operand tiles (full-covariance mixtures)
+  float* tc_part = nullptr;          // partial results of component-split launches
+  int* tc_ticket = nullptr;          // their per-tile arrival counters (zero between launches)
   bool tc = false;                   // the cycle runs around a batched evaluator (tensor cores or external)
   ExtBuf ext{};                      // its buffers
   chisao_batch_eval_fn ext_eval = nullptr;   // CHISAO_OBJ_EXTERNAL: the caller's evaluator
@@ -271,7 +273,11 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
   P.obj.f64.p3 = n3 ? b.take<double>(n3) : nullptr;
   ph.gather_x = b.take<float>(n * d);
   ph.gather_f = b.take<float>(n);
-  if (pr.objective.kind == CHISAO_OBJ_MIXTURE_FULL) ph.tc_weights = b.take<uint8_t>(tc_weight_bytes(pr.objective.n_comp));
+  if (pr.objective.kind == CHISAO_OBJ_MIXTURE_FULL) {
+    ph.tc_weights = b.take<uint8_t>(tc_weight_bytes(pr.objective.n_comp));
+    ph.tc_part = b.take<float>(tc_split_floats());
+    ph.tc_ticket = b.take<int>(tc_split_tickets());
+  }
   ph.tc = prm.grad_mode == CHISAO_GRAD_ADJOINT_TC || pr.objective.kind == CHISAO_OBJ_EXTERNAL;
   if (ph.tc) {
     ExtBuf& E = ph.ext;
@@ -290,6 +296,7 @@ void layout_problem(Bump& b, const chisao_problem& pr, const chisao_params& prm,
     E.xp = b.take<float>(xrows * dp);
     E.gp = b.take<float>(xrows * dp);
     E.vel = b.take<float>(n * dp);
+    E.head = b.take<int>(n);
   }
 }
 
@@ -427,8 +434,8 @@ cudaError_t tc_eval_rows(const ProbHost& ph, const float* x, float* f, float* g,
     }
     return launch_zero_padding(g, rows, ph.d, ph.dp, st);   // the evaluator writes d coordinates only
   }
-  return tc_launch_mixfull(x, ph.dp, rows, ph.d, ph.K, ph.tc_weights, f, g, ph.dp, &ph.dev.cnt->err, st, idx,
-                           count);
+  return tc_launch_mixfull(x, ph.dp, rows, ph.d, ph.K, ph.tc_weights, f, g, ph.dp, &ph.dev.cnt->err, st,
+                           ph.tc_part, ph.tc_ticket, idx, count);
 }
 
 // n_iter L-BFGS iterations (Phase 1).  Per iteration: the direction kernel writes
@@ -456,7 +463,7 @@ cudaError_t enqueue_phase1_tc(const ProbHost& ph, int n_iter, bool fresh, cudaSt
       if ((e = launch_ext(EXT_ACCEPT_MULTI, P, ph.sp, E, r, st)) != cudaSuccess) return e;
     }
   }
-  return cudaSuccess;
+  return n_iter > 0 ? launch_ext(EXT_HIST_ROTATE, P, ph.sp, E, 0, st) : cudaSuccess;   // newest pair to slot 0
 }
 
 // Phase 5 (scale pass + HLC) with all M perturbations evaluated in one launch.
@@ -880,10 +887,12 @@ chisao_status chisao_create(const chisao_problem* probs, int32_t n_probs, const 
       logw.resize(ph.K);
       for (int k = 0; k < ph.K; ++k) logw[k] = std::log(pr.objective.weights[k]);
       tc_build_weights(ph.K, ph.d, linv_all.data(), pr.objective.means, logw.data(), tcw);
-      if (cudaMemcpy(ph.tc_weights, tcw.data(), tcw.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      if (cudaMemcpy(ph.tc_weights, tcw.data(), tcw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemset(ph.tc_ticket, 0, tc_split_tickets() * sizeof(int)) != cudaSuccess)
         st = cuda_fail(c, cudaGetLastError(), "tensor-core weight upload");
     }
-    if (ph.tc && launch_ext(EXT_IOTA, P, ph.sp, ph.ext, 0, c->stream) != cudaSuccess)
+    if (ph.tc && (cudaMemsetAsync(ph.ext.head, 0, sizeof(int) * (size_t)P.n, c->stream) != cudaSuccess ||
+                  launch_ext(EXT_IOTA, P, ph.sp, ph.ext, 0, c->stream) != cudaSuccess))
       st = cuda_fail(c, cudaGetLastError(), "row list of the line-search rounds");
     to32(a0, f0); to32(a1, f1); to32(a2, f2); to32(a3, f3);
     auto up = [&](const void* dst, const void* src, size_t bytes) {
@@ -1247,7 +1256,7 @@ chisao_status chisao_eval(chisao_ctx* c, int32_t prob, const float* x_dev, int64
   if (grad_mode == CHISAO_GRAD_ADJOINT_TC) {
     if (ph.kind != CHISAO_OBJ_MIXTURE_FULL) return fail(c, CHISAO_ERR_ARG, "tensor-core mode needs a full-covariance mixture");
     CK(tc_launch_mixfull(x_dev, ph.d, (int)n, ph.d, ph.K, ph.tc_weights, f_dev, g_dev, ph.d, &ph.dev.cnt->err,
-                         c->stream));
+                         c->stream, ph.tc_part, ph.tc_ticket));
     return CHISAO_OK;
   }
   EvalArgs ea{x_dev, (int)n, f_dev, g_dev};

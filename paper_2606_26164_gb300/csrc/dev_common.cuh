@@ -197,9 +197,12 @@ struct ExtBuf {
                    //   rounds' trial points (buffer b at rows b LS_BATCH n, LS_BATCH rows per sample)
   float* gp;       // the same shape: their gradients
   float* vel;      // [n][dp] anti-convergence velocity
+  int* head;       // [n] physical slot of the newest history pair during Phase 1 (the pairs form
+                   //   a ring of m slots: logical slot k at (head + k) mod m); 0 between phases,
+                   //   where slot 0 is the newest as everywhere else
 };
 enum ExtKernelId { EXT_DIR = 0, EXT_ACCEPT = 1, EXT_HLC_POINTS = 2, EXT_HLC_STEP = 3, EXT_ANTI_STEP = 4,
-                   EXT_SCALES = 5, EXT_ACCEPT_MULTI = 6, EXT_IOTA = 7 };
+                   EXT_SCALES = 5, EXT_ACCEPT_MULTI = 6, EXT_IOTA = 7, EXT_HIST_ROTATE = 8 };
 
 // Caller points for plain objective evaluation.
 struct EvalArgs {

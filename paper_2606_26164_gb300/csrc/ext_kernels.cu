@@ -16,7 +16,9 @@
 //                 the step sequential backtracking takes; a sample with none gets
 //                 the next LS_BATCH trial points, until T_ls trials are spent.
 //   Lists are filled with atomics; every result is per sample, so the order of
-//   a list changes nothing.
+//   a list changes nothing.  During Phase 1 the history of each sample is a ring
+//   of m slots with a head index, so a push writes one pair in place; after the
+//   last iteration k_ext_hist_rotate moves the newest pair back to slot 0.
 // Phase 5: k_ext_hlc_points writes x + sigma z_k for all M perturbations, the
 //   evaluator returns their gradients, k_ext_hlc_step averages and steps.
 // Phase 6: k_ext_anti_step applies the momentum step to the gradient the
@@ -25,6 +27,29 @@
 #include "obj_kernels.cuh"
 
 namespace chisao {
+
+// The history of sample i in logical order (slot 0 newest) from its ring.
+template <int DP, int V, int LPS>
+__device__ __forceinline__ void load_history_ring(const ProbDev& P, int i, int j0, int len, int head, int m,
+                                                  float (&s)[MMAX][V], float (&y)[MMAX][V], float (&rho)[MMAX],
+                                                  float& gam, const Grp<LPS>& g) {
+#pragma unroll
+  for (int k = 0; k < MMAX; ++k) {
+    if (k < len) {
+      const int ph = head + k < m ? head + k : head + k - m;
+      const size_t o = ((size_t)i * MMAX + ph) * DP + j0;
+      ld_vec<V>(P.hs + o, s[k]);
+      ld_vec<V>(P.hy + o, y[k]);
+      rho[k] = P.hrho[(size_t)i * MMAX + ph];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) s[k][v] = y[k][v] = 0.f;
+      rho[k] = 0.f;
+    }
+  }
+  gam = 1.f;
+  if (len > 0) gam = (1.0f / rho[0]) / g.sum(dotv<V>(y[0], y[0]));
+}
 
 template <int DP>
 __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, ExtBuf E, int count_start) {
@@ -45,7 +70,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
     if (gn > 0.f) {
       int len = P.hlen[i];
       float s[MMAX][V], y[MMAX][V], rho[MMAX], gam, p[V];
-      load_history<DP, V, LPS>(P, i, j0, len, s, y, rho, gam, g);
+      load_history_ring<DP, V, LPS>(P, i, j0, len, E.head[i], S.m, s, y, rho, gam, g);
       two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       if (!(g.sum(dotv<V>(G, p)) <= 0.f)) {          // ascent or not finite: restart
@@ -76,12 +101,15 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
 
 // An accepted trial point c (value -Ft, gradient -Gt of F) of sample i: the pair
 // (s, y) = (c - x, Gt - G) is pushed when curved (s^T y summed from exact products in
-// double-single, rho = 1 / s^T y finite), shifting the stored pairs one slot back
-// (slot 0 newest); then x, grad f and f take the trial's values.
+// double-single, rho = 1 / s^T y finite) into the slot before the ring's head, which
+// becomes the head (the oldest pair is overwritten once m are stored); then x, grad f
+// and f take the trial's values.
 template <int V, int LPS>
-__device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams& S, int i, int j0, int DP,
-                                              const float (&x)[V], const float (&G)[V], const float (&c)[V],
-                                              const float (&Gt)[V], float Ft, const Grp<LPS>& g) {
+__device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams& S, const ExtBuf& E, int i,
+                                              int j0, int DP, const float (&x)[V], const float (&G)[V],
+                                              const float (&c)[V], const float (&Gt)[V], float Ft,
+                                              const Grp<LPS>& g) {
+  const int head = E.head[i];                          // read by every lane before lane 0 moves it
   float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -98,21 +126,15 @@ __device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams
   yy = g.sum(yy);
   if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && 1.0f / sy <= FLT_MAX) {
     const int len = P.hlen[i];
-    for (int k = min(len, S.m - 1); k > 0; --k) {      // shift the pairs one slot back
-      const size_t o = ((size_t)i * MMAX + k) * DP + j0;
-      float a[V], b[V];
-      ld_vec<V>(P.hs + o - DP, a);
-      ld_vec<V>(P.hy + o - DP, b);
-      st_vec<V>(P.hs + o, a);
-      st_vec<V>(P.hy + o, b);
-      if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = P.hrho[(size_t)i * MMAX + k - 1];
-    }
-    const size_t o0 = (size_t)i * MMAX * DP + j0;
+    const int nh = head > 0 ? head - 1 : S.m - 1;
+    const size_t o0 = ((size_t)i * MMAX + nh) * DP + j0;
     st_vec<V>(P.hs + o0, sv);
     st_vec<V>(P.hy + o0, yv);
+    __syncwarp(g.mask);                                // the group's head reads are done
     if (g.l == 0) {
-      P.hrho[(size_t)i * MMAX] = 1.0f / sy;
+      P.hrho[(size_t)i * MMAX + nh] = 1.0f / sy;
       P.hlen[i] = min(len + 1, S.m);
+      E.head[i] = nh;
     }
   }
   float gout[V];
@@ -188,7 +210,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept(ProbDev P, StepParams S, 
     const float dec = g.sum(dl);
     if (g.l == 0) tr += 1;
     if (Ft <= F + (float)S.c1 * dec) {
-      ext_take_step<V, LPS>(P, S, i, j0, DP, x, G, c, Gt, Ft, g);
+      ext_take_step<V, LPS>(P, S, E, i, j0, DP, x, G, c, Gt, Ft, g);
     } else {
       const int f = ext_hand_on<V, LPS>(P, S, E, i, j0, DP, 1, 1, x, g);
       if (g.l == 0) fl += (unsigned long long)f;
@@ -239,7 +261,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept_multi(ProbDev P, StepPara
       const float Ft = -E.fm[base + q];
       const float dec = g.sum(dl);
       if (Ft <= F + (float)S.c1 * dec) {
-        ext_take_step<V, LPS>(P, S, i, j0, DP, x, G, c, Gt, Ft, g);
+        ext_take_step<V, LPS>(P, S, E, i, j0, DP, x, G, c, Gt, Ft, g);
         done = true;
         break;
       }
@@ -253,6 +275,44 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_accept_multi(ProbDev P, StepPara
   block_add_u64<NT_OBJ>(ev, &P.cnt->evals);
   block_add_u64<NT_OBJ>(ev, &P.cnt->grads);
   block_add_u64<NT_OBJ>(fl, &P.cnt->ls_fail);
+}
+
+// After Phase 1: each sample's ring is rotated so its newest pair is in slot 0 again
+// (all len pairs read into registers, then written back), and the head returns to 0.
+template <int DP>
+__global__ void __launch_bounds__(NT_OBJ) k_ext_hist_rotate(ProbDev P, StepParams S, ExtBuf E) {
+  constexpr int V = VL, LPS = DP / V;
+  const Grp<LPS> g;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
+  if (i >= P.n) return;
+  const int head = E.head[i], len = P.hlen[i];
+  if (head == 0) return;
+  const int j0 = V * g.l;
+  if (len > 0) {
+    float s[MMAX][V], y[MMAX][V], rho[MMAX];
+#pragma unroll
+    for (int k = 0; k < MMAX; ++k) {
+      if (k < len) {
+        const int ph = head + k < S.m ? head + k : head + k - S.m;
+        const size_t o = ((size_t)i * MMAX + ph) * DP + j0;
+        ld_vec<V>(P.hs + o, s[k]);
+        ld_vec<V>(P.hy + o, y[k]);
+        rho[k] = P.hrho[(size_t)i * MMAX + ph];
+      }
+    }
+    __syncwarp(g.mask);                                // every lane has read before any writes
+#pragma unroll
+    for (int k = 0; k < MMAX; ++k) {
+      if (k < len) {
+        const size_t o = ((size_t)i * MMAX + k) * DP + j0;
+        st_vec<V>(P.hs + o, s[k]);
+        st_vec<V>(P.hy + o, y[k]);
+        if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = rho[k];
+      }
+    }
+  }
+  __syncwarp(g.mask);
+  if (g.l == 0) E.head[i] = 0;
 }
 
 __global__ void k_ext_iota(int* __restrict__ a, long long n) {
@@ -456,6 +516,7 @@ static cudaError_t ext_launch_dp(int which, const ProbDev& P, const StepParams& 
         k_ext_accept_multi<DP><<<blocks < cap ? blocks : cap, NT_OBJ, 0, st>>>(P, S, E, arg);
       break;
     }
+    case EXT_HIST_ROTATE: k_ext_hist_rotate<DP><<<blocks, NT_OBJ, 0, st>>>(P, S, E); break;
     case EXT_IOTA: {
       const long long rows = 2ll * LS_BATCH * P.n;
       k_ext_iota<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(E.iota, rows);

@@ -80,12 +80,15 @@ cudaError_t tc_prepare_attributes();
 // A bounded wait that runs out (budget_ns of the global timer) and raises *err = 2.
 cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st);
 size_t tc_weight_bytes(int K);     // operand tiles of all component groups
+size_t tc_split_floats();          // partial results of a component-split launch
+size_t tc_split_tickets();         // its per-tile arrival counters
 void tc_build_weights(int K, int d, const double* linv, const double* mu, const double* logw,
                       std::vector<uint8_t>& out);
-// n: rows (or the capacity when count is given); idx/count: optional row list and device count
+// n: rows (or the capacity when count is given); idx/count: optional row list and device count;
+// part/ticket: the component-split scratch (null: every CTA takes a whole tile)
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights,
-                              float* f, float* g, int ldg, int* err, cudaStream_t st,
-                              const int* idx = nullptr, const int* count = nullptr);
+                              float* f, float* g, int ldg, int* err, cudaStream_t st, float* part,
+                              int* ticket, const int* idx = nullptr, const int* count = nullptr);
 int scale_blocks(const ProbDev& P);
 size_t gr_qr_smem(int d);
 

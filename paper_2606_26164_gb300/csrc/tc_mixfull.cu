@@ -32,6 +32,7 @@
 // bounded by a clock budget; on timeout the kernel raises the device error flag,
 // every role stops issuing work, waits for its copies and MMAs in flight, and the
 // tensor memory is still released.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -155,7 +156,30 @@ struct TcArgs {
   float* g;               // [n][ldg] or null
   int ldg;
   int* err;               // device error flag
+  float* part;            // [SPLIT_UNITS_MAX][PART_FIELDS][TM] partial results, or null (no split)
+  int* ticket;            // [SPLIT_UNITS_MAX] arrivals per tile, zero between launches
+  int nsm;                // multiprocessors of the device
 };
+
+// Component split: a launch of fewer tiles than half the multiprocessors (the later
+// line-search rounds, small evaluations) would leave most of them idle for a whole tile's
+// time, so the component groups of each tile are divided among nsplit CTAs, as many as
+// still fit one wave.  Each writes its partial log-sum-exp (reference m, sum relative to m)
+// and unnormalised gradient, and the last of a tile's CTAs to finish merges them.  Longer
+// launches keep whole tiles: measured on 152 multiprocessors, splitting them into more
+// waves cost more in per-CTA set-up and pipeline fill than it saved in the last wave.
+constexpr int SPLIT_MAX = 16;
+constexpr int SPLIT_UNITS_MAX = 256;       // CTAs of a split launch (one wave)
+constexpr int PART_FIELDS = 2 + 64;        // m, sum, gradient coordinates
+__host__ __device__ inline int split_of(int tiles, int ngroups, int grid, int nsm) {
+  if (tiles <= 0 || nsm <= 0) return 1;
+  int sp = nsm / tiles;
+  if (grid / tiles < sp) sp = grid / tiles;
+  if (SPLIT_UNITS_MAX / tiles < sp) sp = SPLIT_UNITS_MAX / tiles;
+  if (ngroups < sp) sp = ngroups;
+  if (SPLIT_MAX < sp) sp = SPLIT_MAX;
+  return sp < 2 ? 1 : sp;
+}
 
 constexpr int NW = 4;                      // stages of the factor-tile ring (W, bias tile, constants)
 constexpr int NV = 3;                      // stages of the V-tile ring
@@ -184,7 +208,7 @@ constexpr int OFF_V = OFF_W + NW * WC_BYTES;              // [NV] V tiles
 constexpr int OFF_XCH = OFF_V + NV * VT_BYTES;            // exchange of the two warpgroups at the end
 constexpr int XCH_BYTES = TM * 64 * 4 + 8 * TM * 4;       // [64][TM] gradient half, [2][2][TM] max, [2][2][TM] sum
 constexpr int OFF_BAR = OFF_XCH + XCH_BYTES;
-constexpr int SMEM2_BYTES = OFF_BAR + NBARS * 8 + 8;      // + TMEM address, abort flag
+constexpr int SMEM2_BYTES = OFF_BAR + NBARS * 8 + 16;     // + TMEM address, abort flag, merge flag
 static_assert(WC_BYTES % 1024 == 0 && VT_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned tiles");
 static_assert(SMEM2_BYTES <= 232448, "shared memory per block");
 // TMEM columns: Z, the gradient accumulator of component h for the groups of parity b
@@ -325,8 +349,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   volatile int* abort_flag = &s_abort;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nrows = a.count ? *a.count : a.n;
-  if ((int)blockIdx.x * TM >= nrows) return;          // whole CTA past the rows: nothing to do
-  const int ng = a.ngroups;
+  const int tiles = (nrows + TM - 1) / TM;
+  const int nsplit = a.part ? split_of(tiles, a.ngroups, (int)gridDim.x, a.nsm) : 1;
+  const int tile = (int)blockIdx.x / nsplit;
+  if (tile >= tiles) return;                            // whole CTA past the rows: nothing to do
+  // this CTA's component groups [g0, g0 + ng)
+  const int sp = (int)blockIdx.x - tile * nsplit;
+  const int g0 = (int)((long long)sp * a.ngroups / nsplit);
+  const int ng = (int)((long long)(sp + 1) * a.ngroups / nsplit) - g0;
+  const uint8_t* gblk = a.gblk + (size_t)g0 * GBLK_BYTES;
 
   if (t == 0) {
     for (int i = 0; i < NW; ++i) {
@@ -370,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
           const int s = g % NW, u = g / NW;
           if (u > 0 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_WEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
           mbar_expect_tx(&bars[B_WFULL + s], (uint32_t)WC_BYTES);
-          bulk_g2s(sm + OFF_W + s * WC_BYTES, a.gblk + (size_t)g * GBLK_BYTES, WC_BYTES, &bars[B_WFULL + s]);
+          bulk_g2s(sm + OFF_W + s * WC_BYTES, gblk + (size_t)g * GBLK_BYTES, WC_BYTES, &bars[B_WFULL + s]);
           lastW[s] = u;
         }
         const int gv = g - 2;
@@ -378,7 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
           const int s = gv % NV, u = gv / NV;
           if (u > 0 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_VEMPTY + s], (u - 1) & 1, a.err, abort_flag)) break;
           mbar_expect_tx(&bars[B_VFULL + s], (uint32_t)VT_BYTES);
-          bulk_g2s(sm + OFF_V + s * VT_BYTES, a.gblk + (size_t)gv * GBLK_BYTES + WC_BYTES, VT_BYTES,
+          bulk_g2s(sm + OFF_V + s * VT_BYTES, gblk + (size_t)gv * GBLK_BYTES + WC_BYTES, VT_BYTES,
                    &bars[B_VFULL + s]);
           lastV[s] = u;
         }
@@ -452,7 +483,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
     const int h = (warp - 4) >> 2;                      // component of the group
     const int quad = warp & 3;                          // TMEM lane quadrant of this warp
     const int p = quad * 32 + lane;                     // point of the tile
-    const int lrow = blockIdx.x * TM + p;
+    const int lrow = tile * TM + p;
     const bool live = lrow < nrows;
     const int row = live ? (a.idx ? a.idx[lrow] : lrow) : 0;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
@@ -488,7 +519,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       if (lane == 0) mbar_arrive(&bars[B_XREADY]);
     }
 
-    const float* cst_ptr = reinterpret_cast<const float*>(a.gblk + W_BYTES + BT_BYTES) + h;
+    const float* cst_ptr = reinterpret_cast<const float*>(gblk + W_BYTES + BT_BYTES) + h;
     float cst_next = __ldg(cst_ptr);
     float mref0 = -CUDART_INF_F, mref1 = -CUDART_INF_F, ssum0 = 0.f, ssum1 = 0.f;   // per group parity
     bool ok = true;
@@ -605,13 +636,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       if (i == 2 * h + 1) eb1 = ei;
     }
     const bool fine = ok && !*abort_flag;
-    if (h == 0 && live && fine && a.f) a.f[row] = m + logf(stot);
+    // a split CTA's partial, field-major: [0] m, [1] the sum relative to m, [2 + e] the
+    // unnormalised gradient sum_b e^(m_b - m) G_b
+    float* part = nsplit > 1 ? a.part + (size_t)blockIdx.x * PART_FIELDS * TM : nullptr;
+    if (h == 0 && part) {
+      part[p] = m;
+      part[TM + p] = stot;
+    }
+    if (h == 0 && !part && live && fine && a.f) a.f[row] = m + logf(stot);
     if (GRAD) {
       if (fine) {
         tc_fence_after();
 #pragma unroll
         for (int b = 0; b < 2; ++b) {                    // parity 0, then parity 1 (fixed order)
-          const float sc = -(b ? eb1 : eb0) / stot;
+          const float sc = part ? (b ? eb1 : eb0) : -(b ? eb1 : eb0) / stot;
           uint32_t r0[32], r1[32];
           const uint32_t c0 = tl + COL_G + 128u * b + 64u * h;
           tmem_ld32_async(c0, r0);
@@ -631,11 +669,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         }
       }
       epi_sync();
-      if (h == 0 && live && fine) {
+      if (h == 0 && part && fine) {
+#pragma unroll
+        for (int e = 0; e < 64; ++e) part[(2 + e) * TM + p] = gacc[e] + xch[e * TM + p];
+      } else if (h == 0 && live && fine) {
         float* gr = a.g + (size_t)row * a.ldg;
 #pragma unroll
         for (int e = 0; e < 64; ++e)                    // the row's padding (d <= e < ldg) gets zeros
           if (e < a.ldg) gr[e] = e < a.d ? gacc[e] + xch[e * TM + p] : 0.f;
+      }
+    }
+    if (part) {
+      // the last of the tile's nsplit CTAs to arrive merges their partials (every CTA arrives,
+      // also after an abort, so the tickets return to zero)
+      int* s_last = reinterpret_cast<int*>(sm + OFF_BAR + NBARS * 8 + 8);
+      __threadfence();
+      epi_sync();
+      if (t == 128) {
+        const int prev = atomicAdd(&a.ticket[tile], 1);
+        const int last = prev == nsplit - 1;
+        if (last) a.ticket[tile] = 0;
+        __threadfence();
+        *s_last = last;
+      }
+      epi_sync();
+      if (*s_last && live && fine) {
+        const float* pt = a.part + (size_t)tile * nsplit * PART_FIELDS * TM + p;
+        float mm = -CUDART_INF_F;
+        for (int q = 0; q < nsplit; ++q) mm = fmaxf(mm, __ldcg(pt + (size_t)q * PART_FIELDS * TM));
+        float st = 0.f;
+        for (int q = 0; q < nsplit; ++q) {
+          const float mq = __ldcg(pt + (size_t)q * PART_FIELDS * TM);
+          if (mq > -CUDART_INF_F) st += __ldcg(pt + (size_t)q * PART_FIELDS * TM + TM) * expf(mq - mm);
+        }
+        if (h == 0 && a.f) a.f[row] = mm + logf(st);
+        if (GRAD) {
+          float acc[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+          for (int q = 0; q < nsplit; ++q) {
+            const float* pq = pt + (size_t)q * PART_FIELDS * TM;
+            const float mq = __ldcg(pq);
+            const float wq = mq > -CUDART_INF_F ? expf(mq - mm) : 0.f;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc[e] = fmaf(__ldcg(pq + (size_t)(2 + 32 * h + e) * TM), wq, acc[e]);
+          }
+          float* gr = a.g + (size_t)row * a.ldg;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int j = 32 * h + e;
+            if (j < a.ldg) gr[j] = j < a.d ? -acc[e] / st : 0.f;
+          }
+        }
       }
     }
   }
@@ -676,14 +761,21 @@ __global__ void k_wait_selftest(long long budget_ns, int* err) {
 }  // namespace tc
 
 // ------------------------------------------------------------------ host side
+static int g_tc_nsm = 0;   // multiprocessors of the device, read once with the attributes
 cudaError_t tc_prepare_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_mixfull<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_tc_nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc::k_tc_mixfull<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        tc::SMEM2_BYTES);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(tc::k_tc_mixfull<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM2_BYTES);
 }
 
 size_t tc_weight_bytes(int K) { return (size_t)((K + tc::CG - 1) / tc::CG) * tc::GBLK_BYTES; }
+size_t tc_split_floats() { return (size_t)tc::SPLIT_UNITS_MAX * tc::PART_FIELDS * tc::TM; }
+size_t tc_split_tickets() { return (size_t)tc::SPLIT_UNITS_MAX; }
 
 static uint16_t host_f2bf(float f) {
   uint32_t u;
@@ -750,14 +842,23 @@ cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st) {
 }
 
 cudaError_t tc_launch_mixfull(const float* x, int ldx, int n, int d, int K, const uint8_t* weights, float* f,
-                              float* g, int ldg, int* err, cudaStream_t st, const int* idx, const int* count) {
+                              float* g, int ldg, int* err, cudaStream_t st, float* part, int* ticket,
+                              const int* idx, const int* count) {
   if (n <= 0) return cudaSuccess;
-  tc::TcArgs a{x, ldx, n, idx, count, d, (K + tc::CG - 1) / tc::CG, weights, f, g, ldg, err};
-  const unsigned grid = (unsigned)((n + tc::TM - 1) / tc::TM);
+  const bool split = part && ticket && g_tc_nsm > 0;
+  tc::TcArgs a{x,    ldx, n,    idx, count, d, (K + tc::CG - 1) / tc::CG, weights, f, g, ldg, err,
+               split ? part : nullptr, split ? ticket : nullptr, g_tc_nsm};
+  // a row count known here gets exactly its CTAs; one known only on the device (count) gets
+  // the tiles of the capacity, or the one wave a split of fewer tiles may fill
+  const long long tiles = (n + tc::TM - 1) / tc::TM;
+  const int ngroups = (K + tc::CG - 1) / tc::CG;
+  long long grid = tiles;
+  if (split && !count) grid = tiles * tc::split_of((int)std::min<long long>(tiles, 1 << 30), ngroups, 1 << 30, g_tc_nsm);
+  else if (split) grid = std::max<long long>(tiles, std::min<long long>(tc::SPLIT_MAX * tiles, g_tc_nsm));
   if (g)
-    tc::k_tc_mixfull<true><<<grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
+    tc::k_tc_mixfull<true><<<(unsigned)grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
   else
-    tc::k_tc_mixfull<false><<<grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
+    tc::k_tc_mixfull<false><<<(unsigned)grid, tc::NTHREADS, tc::SMEM2_BYTES, st>>>(a);
   return cudaGetLastError();
 }
 

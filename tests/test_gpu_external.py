@@ -105,6 +105,40 @@ def test_external_objective_lbfgs_iteration(name):
     model.close()
 
 
+def test_external_objective_history_ring():
+    """Several Phase-1 iterations in one call with a short memory (m = 3, five pushes
+    onto two stored pairs): the pairs are kept in a ring during the phase and rotated
+    back after it, so the history read back is the oracle's, newest first, slot by slot
+    (s, y and rho of every sample whose path matched)."""
+    prob = I.small_quadratic(7, 700, seed=8)
+    P = M.Params(m=3, grad_mode=M.GRAD_ADJOINT)
+    st = M.new_state(prob.x0, P.m)
+    M.lbfgs_iterations(prob, st, P, 2)
+    st = U.rounded(st)
+    st.f = M.evaluate(prob, st.x)
+    st.g = M.gradient(prob, st.x, P)
+    st = U.rounded(st)
+    model = U.open_ctx(_external(prob), P)
+    U.write_state(model, prob, st)
+    model.run_phase(0, CH.PHASE_LBFGS, -5)
+    got = U.read_state(model, prob, P.m)
+    ref = _copy(st)
+    M.lbfgs_iterations(prob, ref, P, 5, fresh_gradient=False)
+    step = np.abs(ref.x - st.x).max(axis=1)
+    err = np.abs(got.x - ref.x).max(axis=1)
+    ok = (err <= 1e-4 * step + 1e-6 * np.abs(st.x).max(axis=1)) & (got.hlen == ref.hlen)
+    assert ok.sum() >= 0.9 * prob.n, ok.sum()
+    assert np.all(ref.hlen[ok] == P.m)
+    for k in range(P.m):
+        for a, b in ((got.S[:, k], ref.S[:, k]), (got.Y[:, k], ref.Y[:, k])):
+            scale = np.abs(b).max(axis=1) + 1e-30
+            e = np.abs(a - b).max(axis=1) / scale
+            assert np.all(e[ok] <= 1e-3), (k, np.sort(e[ok])[-5:])
+        r = np.abs(got.rho[:, k] - ref.rho[:, k]) / np.abs(ref.rho[:, k])
+        assert np.all(r[ok] <= 1e-3), (k, np.sort(r[ok])[-5:])
+    model.close()
+
+
 def test_external_objective_hlc_and_anti_single_steps():
     prob = PROBS["mix_d5"](901)
     rng = np.random.default_rng(5)

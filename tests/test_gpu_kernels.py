@@ -523,3 +523,46 @@ def test_tensor_core_mixture_objective(which):
     fv, _ = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT_TC, want_grad=False)
     np.testing.assert_array_equal(fv.cpu().numpy(), f.astype(np.float32))
     model.close()
+
+
+def _tc_split(tiles, ngroups, grid, nsm, split_max=16, units_max=256):
+    """The component split the tensor-core kernel chooses for a launch of `tiles`
+    128-point tiles: as many CTAs per tile as still fit one wave (none past it)."""
+    sp = min(nsm // tiles, grid // tiles, units_max // tiles, ngroups, split_max)
+    return sp if sp >= 2 else 1
+
+
+def test_tensor_core_component_split():
+    """A tile's component groups divided among several CTAs and merged (a launch of a few
+    tiles) gives the objective within the same bounds as whole tiles (a launch of one tile
+    per multiprocessor): both against the FP64 evaluation of the rounded objective, and
+    against each other within the sum of their bounds."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n_big = 128 * nsm
+    prob = I.mixture256_d64(n=n_big)
+    ng = (prob.objective.arrays["means"].shape[0] + 1) // 2
+    assert _tc_split(nsm, ng, 1 << 30, nsm) == 1
+    assert _tc_split(8, ng, 1 << 30, nsm) > 1
+    model = U.open_ctx(prob, M.Params(grad_mode=M.GRAD_ADJOINT))
+    rng = np.random.default_rng(12)
+    mu = prob.objective.arrays["means"]
+    x = (prob.x0 * np.float32(0.7)).astype(np.float32)
+    sel = rng.choice(n_big, 1000, replace=False)
+    x[sel[:500]] = (mu[rng.integers(0, mu.shape[0], 500)] + rng.normal(0, 0.05, (500, prob.d))).astype(np.float32)
+    f1, g1 = model.eval(0, _torch_x(x), CH.GRAD_ADJOINT_TC)          # whole tiles
+    xs = x[sel]
+    f2, g2 = model.eval(0, _torch_x(xs), CH.GRAD_ADJOINT_TC)         # 8 tiles, split
+    f1 = f1.cpu().numpy().astype(np.float64)[sel]
+    g1 = g1.cpu().numpy().astype(np.float64)[sel]
+    f2, g2 = f2.cpu().numpy().astype(np.float64), g2.cpu().numpy().astype(np.float64)
+    tco = OB.tensor_core_objective(prob.objective)
+    f_ref, g_ref = OB.value(tco, xs.astype(np.float64)), OB.grad(tco, xs.astype(np.float64))
+    tol_f, tol_g = tc_error_bounds(tco, OB.bf16_split(xs))
+    for f, g in ((f1, g1), (f2, g2)):
+        assert np.all(np.abs(f - f_ref) <= tol_f), (np.abs(f - f_ref) / tol_f).max()
+        assert np.all(np.abs(g - g_ref) <= tol_g), (np.abs(g - g_ref) / tol_g).max()
+    assert np.all(np.abs(f1 - f2) <= 2 * tol_f) and np.all(np.abs(g1 - g2) <= 2 * tol_g)
+    fv, _ = model.eval(0, _torch_x(xs), CH.GRAD_ADJOINT_TC, want_grad=False)
+    np.testing.assert_array_equal(fv.cpu().numpy(), f2.astype(np.float32))
+    model.close()
