@@ -188,18 +188,18 @@ enum : int {
   B_WFULL = 0,                 // [NW] factor tile, bias tile and constants of a group landed
   B_WEMPTY = B_WFULL + NW,     // [NW] read by the Z MMAs
   B_VFULL = B_WEMPTY + NW,     // [NV] V tile of a group landed
-  B_VEMPTY = B_VFULL + NV,     // [NV] read by the gradient MMAs
-  B_ZFULL = B_VEMPTY + NV,     // Z of the current group in TMEM
-  B_ZEMPTY = B_ZFULL + 1,      // [2] Z of a group of parity b read into registers by all eight epilogue
-                               //     warps (one barrier per parity: each Z issuer then waits at most one
-                               //     phase past one it has seen, so a parity wait cannot alias)
-  B_YFULL = B_ZEMPTY + 2,      // [2] Y buffer b written (eight warps)
-  B_G2DONE = B_YFULL + 2,      // [2] gradient MMAs reading Y buffer b finished
-  B_XREADY = B_G2DONE + 2,     // split input tile written (eight warps)
-  B_DRAIN = B_XREADY + 1,      // [3] every MMA of issuer i finished
-  NBARS = B_DRAIN + 3
+  B_VEMPTY = B_VFULL + NV,     // [NV] read by the gradient MMAs of both components (two commits)
+  B_ZFULL = B_VEMPTY + NV,     // [2] Z buffer b holds its group (groups of parity b)
+  B_ZEMPTY = B_ZFULL + 2,      // [2] Z buffer b read into registers by all eight epilogue warps
+  B_YFULL = B_ZEMPTY + 2,      // [2 h + b] component h's half of Y buffer b written (warpgroup h)
+  B_GDONE = B_YFULL + 4,       // [2 h + b] gradient MMAs of component h for a group of parity b finished
+  B_XREADY = B_GDONE + 4,      // split input tile written (eight warps)
+  B_DRAIN = B_XREADY + 1,      // [4] every MMA of issuer i finished
+  NBARS = B_DRAIN + 4
 };
-constexpr int NTHREADS = 384;              // warp 0 copies, warps 1-3 issue MMAs, warps 4-11 epilogue
+// warp 0 copies, warps 1-2 issue Z (groups of parity 0 / 1), warps 3 and 12 issue the
+// gradient MMAs of component 0 / 1, warps 4-11 are the epilogue
+constexpr int NTHREADS = 416;
 constexpr int A_BYTES = TM * DK * 2;                      // 16 KB per BF16 input half
 constexpr int ONES_BYTES = TM * 16 * 2;                   // 4 KB: the K block [1, 1, 1, 0 ...] of every point
 constexpr int OFF_ONES = 2 * A_BYTES;
@@ -211,9 +211,10 @@ constexpr int OFF_BAR = OFF_XCH + XCH_BYTES;
 constexpr int SMEM2_BYTES = OFF_BAR + NBARS * 8 + 16;     // + TMEM address, abort flag, merge flag
 static_assert(WC_BYTES % 1024 == 0 && VT_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned tiles");
 static_assert(SMEM2_BYTES <= 232448, "shared memory per block");
-// TMEM columns: Z, the gradient accumulator of component h for the groups of parity b
-// at COL_G + 64 (2b + h), and Y buffer b (BF16 weights, two K-elements per column)
-constexpr uint32_t COL_Z = 0, COL_G = TN, COL_Y = TN + 256;
+// TMEM columns: Z buffer b at COL_Z + 128 b, the gradient accumulator of component h at
+// COL_G + 64 h, and Y buffer b (BF16 weights, two K-elements per column) at COL_Y + 64 b,
+// component h's half at + 32 h
+constexpr uint32_t COL_Z = 0, COL_G = 2 * TN, COL_Y = 2 * TN + 128;
 static_assert(COL_Y + 2 * 64 <= TMEM_COLS, "tensor memory columns");
 // Z column of component h's slab s of z
 __host__ __device__ constexpr uint32_t zcol(int h, int s) { return (uint32_t)zrow(h, 16 * s); }
@@ -321,25 +322,25 @@ __device__ __forceinline__ void tmem_scale64(uint32_t taddr, float s) {
 // One CTA = one tile of 128 points; the components go in groups of two (parity b = g & 1):
 //   warp 0 (one thread) bulk-copies each group's factor tile, bias tile and constants
 //   into a ring of NW stages and its V tile into a ring of NV stages;
-//   warp 1 (one thread) issues Z = [x_hi|x_lo|1] [W|W|-b]^T into TMEM, only the nonzero
-//   triangle of each K-chunk (the bias enters the contraction through a K block of ones
-//   against the exact three-term BF16 split of -b, so z leaves the tensor cores centred);
-//   warps 2 and 3 (one thread each, groups of parity 0 and 1) issue
-//   G_{h,b} += Y_h V_h (h = the group's first or second component), Y read from TMEM
-//   buffer b.  Spreading the issue over three threads matters: a thread that issued
-//   MMAs finds its next barrier operation held until they ran, so each gradient issuer
-//   only waits on barriers whose MMAs finished long ago, and the gradient MMAs fill the
-//   tensor pipe while the next Z waits for its buffer.  Within a parity the gradient
-//   MMAs stay in group order (group g's weights are written only after those of g - 2
-//   were consumed), so the sums are deterministic;
+//   warps 1 and 2 (one thread each, the groups of parity 0 and 1) issue
+//   Z = [x_hi|x_lo|1] [W|W|-b]^T into Z buffer b, only the nonzero triangle of each
+//   K-chunk (the bias enters the contraction through a K block of ones against the
+//   exact three-term BF16 split of -b, so z leaves the tensor cores centred);
+//   warps 3 and 12 (one thread each, components 0 and 1 of every group) issue
+//   G_h += Y_h V_h, Y read from TMEM buffer b.
+//   A thread's tcgen05.mma issues are serial: each takes about 117 clocks whatever N
+//   (measured for N = 16 ... 128, A from shared or tensor memory), while MMAs issued by
+//   different threads into different accumulators overlap.  The nine dependent MMAs of
+//   a group's Z therefore run about 1050 clocks: two Z buffers with one issuer each let
+//   the next group's Z run while the epilogue reads this one, and one gradient issuer per
+//   component keeps each accumulator's MMAs in group order (deterministic sums);
 //   warps 4-11 are two warpgroups, one per component of the group, each covering the
 //   four TMEM lane quadrants (one point per thread): they read z, fold the component
 //   into a log-sum-exp and write the gradient weights e^(lc - m_ref) z as BF16 into
-//   TMEM.  Each warpgroup keeps one reference m_ref, sum and pair of accumulators per
-//   group parity: m_ref is raised only when a component exceeds it by TAU, the rows of
-//   that parity's accumulator then being rescaled in place, which needs only the
-//   gradient MMAs of the same parity two groups back (also what frees the Y buffer).
-//   The four partial results are combined at the end.
+//   TMEM.  Each warpgroup keeps one reference m_ref and sum per point: m_ref is raised
+//   only when a component exceeds it by TAU, its accumulator's rows then being rescaled
+//   in place once the gradient MMAs of the previous group have finished with it.  The
+//   two partial results are combined at the end.
 template <bool GRAD>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -366,15 +367,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
     }
     for (int i = 0; i < NV; ++i) {
       mbar_init(&bars[B_VFULL + i], 1);
-      mbar_init(&bars[B_VEMPTY + i], 1);
+      mbar_init(&bars[B_VEMPTY + i], 2);
     }
-    mbar_init(&bars[B_ZFULL], 1);
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars[B_ZFULL + b], 1);
       mbar_init(&bars[B_ZEMPTY + b], 8);
-      mbar_init(&bars[B_YFULL + b], 8);
-      mbar_init(&bars[B_G2DONE + b], 1);
     }
-    for (int i = 0; i < 3; ++i) mbar_init(&bars[B_DRAIN + i], 1);
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&bars[B_YFULL + i], 4);
+      mbar_init(&bars[B_GDONE + i], 1);
+      mbar_init(&bars[B_DRAIN + i], 1);
+    }
     mbar_init(&bars[B_XREADY], 8);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -420,65 +423,65 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       for (int s = 0; s < NV; ++s)
         if (lastV[s] >= 0) mbar_wait(&bars[B_VFULL + s], lastV[s] & 1, a.err);
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ Z issuer
+  } else if (warp == 1 || warp == 2) {
+    // ------------------------------------------------------------ Z issuer of the groups of parity j
     if (lane == 0) {
+      const int j = warp - 1;
       const uint32_t idF = idesc_bf16(TM, TN);
       const uint32_t aX = smem_u32(sm), aOnes = smem_u32(sm + OFF_ONES);
+      const uint32_t dz = tmem + COL_Z + (uint32_t)(TN * j);
       bool issued = false;
       if (mbar_wait_ab<ROLE_NAP_NS>(&bars[B_XREADY], 0, a.err, abort_flag)) {
-        for (int g = 0; g < ng; ++g) {
-          const int s = g % NW;
+        for (int g = j; g < ng; g += 2) {
+          const int s = g % NW;                        // NW is even: stage s always holds groups of parity j
           if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_WFULL + s], (g / NW) & 1, a.err, abort_flag)) break;
-          if (g >= 1 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_ZEMPTY + ((g - 1) & 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) break;
+          if (g >= 2 && !mbar_wait_ab<ROLE_NAP_NS>(&bars[B_ZEMPTY + j], ((g - 2) >> 1) & 1, a.err, abort_flag)) break;
           tc_fence_after();
           const uint32_t bW = smem_u32(sm + OFF_W + s * WC_BYTES);
 #pragma unroll
           for (int hl = 0; hl < 2; ++hl)               // x_hi then x_lo against the same factor tile
 #pragma unroll
             for (int c = 0; c < NSLAB; ++c)            // K-chunk c meets the rows of slabs >= c
-              mma_bf16(tmem + COL_Z, sdesc(aX + hl * A_BYTES + c * 256, 128, 1024), sdesc(bW + c * 256, 128, 1024),
+              mma_bf16(dz, sdesc(aX + hl * A_BYTES + c * 256, 128, 1024), sdesc(bW + c * 256, 128, 1024),
                        idesc_bf16(TM, zn_of_chunk(c)), (hl | c) ? 1u : 0u);
-          mma_bf16(tmem + COL_Z, sdesc(aOnes, 128, 256), sdesc(bW + W_BYTES, 128, 256), idF, 1u);   // - b
-          mma_commit(&bars[B_ZFULL]);
+          mma_bf16(dz, sdesc(aOnes, 128, 256), sdesc(bW + W_BYTES, 128, 256), idF, 1u);   // - b
+          mma_commit(&bars[B_ZFULL + j]);
           mma_commit(&bars[B_WEMPTY + s]);
           issued = true;
         }
       }
       if (issued) {                                     // every issued MMA completes before exit
-        mma_commit(&bars[B_DRAIN]);
-        mbar_wait(&bars[B_DRAIN], 0, a.err);
+        mma_commit(&bars[B_DRAIN + j]);
+        mbar_wait(&bars[B_DRAIN + j], 0, a.err);
       }
     }
-  } else if (warp <= 3) {
-    // ------------------------------------------------------------ gradient issuers (groups of parity j)
+  } else if (warp == 3 || warp == 12) {
+    // ------------------------------------------------------------ gradient issuer of component h
     if (GRAD && lane == 0) {
-      const int j = warp - 2;
+      const int h = warp == 3 ? 0 : 1;
+      const uint32_t dg = tmem + COL_G + 64u * (uint32_t)h;
       bool issued = false;
-      for (int g = j; g < ng; g += 2) {
+      for (int g = 0; g < ng; ++g) {
         const int b = g & 1, s = g % NV;
-        if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_YFULL + b], (g >> 1) & 1, a.err, abort_flag)) break;
+        if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_YFULL + 2 * h + b], (g >> 1) & 1, a.err, abort_flag)) break;
         if (!mbar_wait_ab<ROLE_NAP_NS>(&bars[B_VFULL + s], (g / NV) & 1, a.err, abort_flag)) break;
         tc_fence_after();
         const uint32_t bV = smem_u32(sm + OFF_V + s * VT_BYTES);
-        const uint32_t aY = tmem + COL_Y + 64u * (uint32_t)b;
-        const uint32_t dg = tmem + COL_G + 128u * (uint32_t)b;
+        const uint32_t aY = tmem + COL_Y + 64u * (uint32_t)b + 32u * (uint32_t)h;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int c = NSLAB - 1; c >= 0; --c)         // y K-chunk c meets outputs j <= 16 c + 15
-            mma_bf16_ts(dg + 64u * h, aY + 32u * h + 8u * c, sdesc(bV + (h * NSLAB + c) * 256, 128, 2048),
-                        idesc_bf16(TM, gn_of_chunk(c)), (g >= 2 || c < NSLAB - 1) ? 1u : 0u);
-        mma_commit(&bars[B_G2DONE + b]);
+        for (int c = NSLAB - 1; c >= 0; --c)           // y K-chunk c meets outputs j <= 16 c + 15
+          mma_bf16_ts(dg, aY + 8u * c, sdesc(bV + (h * NSLAB + c) * 256, 128, 2048), idesc_bf16(TM, gn_of_chunk(c)),
+                      (g > 0 || c < NSLAB - 1) ? 1u : 0u);
+        mma_commit(&bars[B_GDONE + 2 * h + b]);
         mma_commit(&bars[B_VEMPTY + s]);
         issued = true;
       }
       if (issued) {
-        mma_commit(&bars[B_DRAIN + 1 + j]);
-        mbar_wait(&bars[B_DRAIN + 1 + j], 0, a.err);
+        mma_commit(&bars[B_DRAIN + 2 + h]);
+        mbar_wait(&bars[B_DRAIN + 2 + h], 0, a.err);
       }
     }
-  } else if (warp >= 4) {
+  } else {
     // ------------------------------------------------------------ epilogue (warps 4-11)
     const int h = (warp - 4) >> 2;                      // component of the group
     const int quad = warp & 3;                          // TMEM lane quadrant of this warp
@@ -487,6 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
     const bool live = lrow < nrows;
     const int row = live ? (a.idx ? a.idx[lrow] : lrow) : 0;
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t gcol = tl + COL_G + 64u * (uint32_t)h;
 
     // split input: this thread converts columns [32h, 32h + 32) of its point; the first
     // warpgroup also writes the point's ones block
@@ -521,17 +525,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
 
     const float* cst_ptr = reinterpret_cast<const float*>(gblk + W_BYTES + BT_BYTES) + h;
     float cst_next = __ldg(cst_ptr);
-    float mref0 = -CUDART_INF_F, mref1 = -CUDART_INF_F, ssum0 = 0.f, ssum1 = 0.f;   // per group parity
+    float mref = -CUDART_INF_F, ssum = 0.f;
     bool ok = true;
     for (int g = 0; g < ng; ++g) {
-      const int b = g & 1, s = g % NW;
-      if (!warp_wait(&bars[B_ZFULL], g & 1, a.err, abort_flag)) { ok = false; break; }
+      const int b = g & 1;
+      if (!warp_wait(&bars[B_ZFULL + b], (g >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
       float z[64];
       {
         uint32_t r[NSLAB][16];
 #pragma unroll
-        for (int c = 0; c < NSLAB; ++c) tmem_ld16_async(tl + COL_Z + zcol(h, c), r[c]);
+        for (int c = 0; c < NSLAB; ++c) tmem_ld16_async(tl + COL_Z + (uint32_t)(TN * b) + zcol(h, c), r[c]);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < NSLAB; ++c) {
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars[B_ZEMPTY + b]);   // Z may take the next group
+      if (lane == 0) mbar_arrive(&bars[B_ZEMPTY + b]);   // Z buffer b may take group g + 2
 
       // the log-constant of this group, read from global memory one group ahead (the factor
       // ring then depends on the Z MMAs alone)
@@ -561,39 +565,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
       const float lc = cst - 0.5f * (((qa.x + qa.y) + (qb.x + qb.y)) + ((qc.x + qc.y) + (qd.x + qd.y)));
 
       if (!GRAD) {
-        if (lc > mref0) {
-          ssum0 = ssum0 * expf(mref0 - lc) + 1.f;
-          mref0 = lc;
+        if (lc > mref) {
+          ssum = ssum * expf(mref - lc) + 1.f;
+          mref = lc;
         } else if (lc > -CUDART_INF_F) {
-          ssum0 += expf(lc - mref0);
+          ssum += expf(lc - mref);
         }
         continue;
       }
-      float mr = b ? mref1 : mref0, ss = b ? ssum1 : ssum0;
       float scale = 1.f;
       bool resc = false;
-      if (lc > mr + TAU) {
-        if (mr > -CUDART_INF_F) {
-          scale = expf(mr - lc);
+      if (lc > mref + TAU) {
+        if (mref > -CUDART_INF_F) {
+          scale = expf(mref - lc);
           resc = true;
-          ss *= scale;
+          ssum *= scale;
         }
-        mr = lc;
+        mref = lc;
       }
-      // Y buffer b and the parity-b accumulators are free once the gradient MMAs of group
-      // g - 2 finished
-      if (g >= 2 && !warp_wait(&bars[B_G2DONE + b], ((g - 2) >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
+      // this component's half of Y buffer b is free once its gradient MMAs of group g - 2
+      // finished
+      if (g >= 2 && !warp_wait(&bars[B_GDONE + 2 * h + b], ((g - 2) >> 1) & 1, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      if (__any_sync(0xffffffffu, resc)) tmem_scale64(tl + COL_G + 128u * b + 64u * h, scale);
-      const float r = lc > -CUDART_INF_F ? expf(lc - mr) : 0.f;
-      ss += r;
-      if (b) {
-        mref1 = mr;
-        ssum1 = ss;
-      } else {
-        mref0 = mr;
-        ssum0 = ss;
-      }
+      const float r = lc > -CUDART_INF_F ? expf(lc - mref) : 0.f;
+      ssum += r;
       {
         uint32_t y[32];
 #pragma unroll
@@ -603,41 +598,49 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
         }
         tmem_st32(tl + COL_Y + 64u * (uint32_t)b + 32u * h, y);
       }
+      // a raised reference rescales the accumulator, once the gradient MMAs of group g - 1
+      // have finished with it (waited for last: they ran while this group's weights were
+      // formed); group g's MMAs are issued only after the arrival below
+      if (__any_sync(0xffffffffu, resc)) {
+        if (g >= 1 && !warp_wait(&bars[B_GDONE + 2 * h + (b ^ 1)], ((g - 1) >> 1) & 1, a.err, abort_flag)) {
+          tmem_wait_st();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        tmem_scale64(gcol, scale);
+      }
       tmem_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars[B_YFULL + b]);
+      if (lane == 0) mbar_arrive(&bars[B_YFULL + 2 * h + b]);
     }
 
-    // ---- combine the two warpgroups and the two parities, write f and g
+    // ---- combine the two warpgroups, write f and g
     float gacc[64];
     if (GRAD && ok) {
-      // the last group of each parity completes that parity's accumulators
-      if (ng >= 2) ok = warp_wait(&bars[B_G2DONE + ((ng - 2) & 1)], ((ng - 2) >> 1) & 1, a.err, abort_flag);
-      if (ok) ok = warp_wait(&bars[B_G2DONE + ((ng - 1) & 1)], ((ng - 1) >> 1) & 1, a.err, abort_flag);
+      // the gradient MMAs of the last group complete this component's accumulator (the
+      // issuer's earlier MMAs were issued before them)
+      ok = warp_wait(&bars[B_GDONE + 2 * h + ((ng - 1) & 1)], ((ng - 1) >> 1) & 1, a.err, abort_flag);
     }
     float* xch = reinterpret_cast<float*>(sm + OFF_XCH);            // [64][TM]
-    float* s_m = xch + 64 * TM;                                     // [h][b][TM]
-    float* s_s = s_m + 4 * TM;                                      // [h][b][TM]
-    s_m[(2 * h) * TM + p] = mref0;
-    s_m[(2 * h + 1) * TM + p] = mref1;
-    s_s[(2 * h) * TM + p] = ssum0;
-    s_s[(2 * h + 1) * TM + p] = ssum1;
+    float* s_m = xch + 64 * TM;                                     // [h][TM]
+    float* s_s = s_m + 2 * TM;                                      // [h][TM]
+    s_m[h * TM + p] = mref;
+    s_s[h * TM + p] = ssum;
     epi_sync();
-    float m = -CUDART_INF_F;
-    for (int i = 0; i < 4; ++i) m = fmaxf(m, s_m[i * TM + p]);
-    float stot = 0.f, eb0 = 0.f, eb1 = 0.f;            // eb: weights of this warpgroup's two parities
+    const float m = fmaxf(s_m[p], s_m[TM + p]);
+    float stot = 0.f, eb = 0.f;                         // eb: weight of this warpgroup's partial
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
       const float mi = s_m[i * TM + p];
       const float ei = mi > -CUDART_INF_F ? expf(mi - m) : 0.f;
       stot += s_s[i * TM + p] * ei;
-      if (i == 2 * h) eb0 = ei;
-      if (i == 2 * h + 1) eb1 = ei;
+      if (i == h) eb = ei;
     }
     const bool fine = ok && !*abort_flag;
     // a split CTA's partial, field-major: [0] m, [1] the sum relative to m, [2 + e] the
-    // unnormalised gradient sum_b e^(m_b - m) G_b
+    // unnormalised gradient sum_h e^(m_h - m) G_h
     float* part = nsplit > 1 ? a.part + (size_t)blockIdx.x * PART_FIELDS * TM : nullptr;
     if (h == 0 && part) {
       part[p] = m;
@@ -647,21 +650,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_mixfull(TcArgs a) {
     if (GRAD) {
       if (fine) {
         tc_fence_after();
+        const float sc = part ? eb : -eb / stot;
+        uint32_t r0[32], r1[32];
+        tmem_ld32_async(gcol, r0);
+        tmem_ld32_async(gcol + 32, r1);
+        tmem_wait_ld();
+        tmem_pin32(r0);
+        tmem_pin32(r1);
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {                    // parity 0, then parity 1 (fixed order)
-          const float sc = part ? (b ? eb1 : eb0) : -(b ? eb1 : eb0) / stot;
-          uint32_t r0[32], r1[32];
-          const uint32_t c0 = tl + COL_G + 128u * b + 64u * h;
-          tmem_ld32_async(c0, r0);
-          tmem_ld32_async(c0 + 32, r1);
-          tmem_wait_ld();
-          tmem_pin32(r0);
-          tmem_pin32(r1);
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            gacc[e] = b ? fmaf(__uint_as_float(r0[e]), sc, gacc[e]) : __uint_as_float(r0[e]) * sc;
-            gacc[32 + e] = b ? fmaf(__uint_as_float(r1[e]), sc, gacc[32 + e]) : __uint_as_float(r1[e]) * sc;
-          }
+        for (int e = 0; e < 32; ++e) {
+          gacc[e] = __uint_as_float(r0[e]) * sc;
+          gacc[32 + e] = __uint_as_float(r1[e]) * sc;
         }
         if (h == 1) {
 #pragma unroll
