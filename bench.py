@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 KERNELS_PER_STEP = 22   # kernel launches in one non-final cycle of one problem
 FP32_LANES_PER_SM = 128
 N_SM = 152
+SM_MHZ_NOMINAL = 2070.0
 
 
 def parse():
@@ -421,6 +422,18 @@ def full_covariance_leg(CH, steps, n_osc, fp32_peak_tf):
                                   "executed_tflops": executed / tk / 1e12,
                                   "peak_source": f"{src} bf16 dense (MEASURED_PEAKS.json burst)",
                                   "launch_ms": 1e3 * tk, "points_per_launch": N}
+            # the instruction-rate floor: a group of two components issues 17 small MMAs
+            # (M = 128, K = 16: nine for Z, eight for the gradient), which the tensor core takes
+            # at a measured rate whatever their width; one CTA per SM, waves of whole tiles
+            clk4 = CH.measure_mma_rate(64, 4, 2)
+            clk1 = CH.measure_mma_rate(64, 1, 0)
+            waves = -(-(-(-N // 128)) // N_SM)
+            floor_ms = waves * ((K + 1) // 2) * 17 * clk4 / (SM_MHZ_NOMINAL * 1e3)
+            res["roofline_tc"]["mma_rate_floor"] = {
+                "clk_per_mma_4_issuers": clk4, "clk_per_mma_1_issuer": clk1, "mmas_per_group": 17,
+                "waves": waves, "floor_ms": floor_ms, "frac": floor_ms / (1e3 * tk),
+                "basis": "measured clocks per tcgen05.mma (N = 64, four issuers, two reading A from TMEM) "
+                         "x 17 per group x groups x waves at the nominal 2070 MHz"}
             res["tc_error_vs_exact"] = tc_error_vs_exact(CH, m4)
         m4.close()
     res["matched_error"] = matched_error_forms(CH)

@@ -285,6 +285,18 @@ chisao_status chisao_modes(chisao_ctx *c, int32_t prob, float *x_out,
  * the default stream) and synchronizes it; a few milliseconds. */
 chisao_status chisao_measure_fma_peak(int32_t precision, void *cuda_stream, double *flops);
 
+/* Measured instruction rate of the tensor core for the small MMAs the full-covariance
+ * objective issues (tcgen05.mma kind::f16, M = 128, K = 16, width n a multiple of 16 up
+ * to 256 with one issuer, 128 with two, 64 with three or four): `threads` issuing
+ * threads (1 .. 4, in different warps) each run 2048 MMAs into their own accumulator,
+ * the last tmem_a (0 .. threads) of them reading A from tensor memory;
+ * *clk_per_mma receives SM clocks per MMA with all of them together.  One CTA, zero
+ * operands; runs on the given stream (NULL: the default stream) and synchronizes it.
+ * CHISAO_ERR_ARG for other arguments; CHISAO_ERR_CUDA if the kernel fails or its
+ * bounded completion wait runs out. */
+chisao_status chisao_measure_mma_rate(int32_t n, int32_t threads, int32_t tmem_a, void *cuda_stream,
+                                      double *clk_per_mma);
+
 /* Result of chisao_autotune. */
 typedef struct {
   int32_t n_branch;        /* branch streams chosen (contexts of several problems)  */

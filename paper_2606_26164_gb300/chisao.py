@@ -30,7 +30,7 @@ EXPORTS = ["chisao_default_params", "chisao_arena_bytes", "chisao_create", "chis
            "chisao_load_population", "chisao_modes", "chisao_get_counters", "chisao_eval",
            "chisao_last_error", "chisao_destroy", "chisao_layout", "chisao_state_get",
            "chisao_state_set", "chisao_run_phase", "chisao_set_gr_state", "chisao_dedup_noalloc", "chisao_seed",
-           "chisao_widths", "chisao_selftest_wait", "chisao_autotune", "chisao_measure_fma_peak", "chisao_init",
+           "chisao_widths", "chisao_selftest_wait", "chisao_autotune", "chisao_measure_fma_peak", "chisao_measure_mma_rate", "chisao_init",
            "chisao_stats", "chisao_set_tile"]
 
 
@@ -165,6 +165,7 @@ def library() -> C.CDLL:
         lib.chisao_selftest_wait.argtypes = [vp, C.c_int32, C.c_int64]
         lib.chisao_autotune.argtypes = [vp, C.c_int32, C.POINTER(CTuning)]
         lib.chisao_measure_fma_peak.argtypes = [C.c_int32, vp, C.POINTER(C.c_double)]
+        lib.chisao_measure_mma_rate.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, C.POINTER(C.c_double)]
         lib.chisao_widths.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
                                       C.POINTER(C.c_int64)]
         lib.chisao_modes.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
@@ -187,6 +188,16 @@ def library() -> C.CDLL:
                 getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
+
+
+def measure_mma_rate(n: int, threads: int, tmem_a: int = 0, stream=None) -> float:
+    """SM clocks per tcgen05.mma (M = 128, K = 16, width n) with `threads` issuers together."""
+    out = C.c_double(0.0)
+    ptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = library().chisao_measure_mma_rate(n, threads, tmem_a, ptr, C.byref(out))
+    if st != OK:
+        raise ChisaoError(f"chisao_measure_mma_rate failed ({st})")
+    return out.value
 
 
 def measure_fma_peak(f64: bool = False, stream=None) -> float:

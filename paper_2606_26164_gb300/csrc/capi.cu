@@ -1038,6 +1038,18 @@ chisao_status chisao_measure_fma_peak(int32_t precision, void* cuda_stream, doub
              : CHISAO_ERR_CUDA;
 }
 
+chisao_status chisao_measure_mma_rate(int32_t n, int32_t threads, int32_t tmem_a, void* cuda_stream,
+                                      double* clk_per_mma) {
+  const int nmax = threads == 1 ? 256 : threads == 2 ? 128 : 64;   // each issuer's accumulator width
+  if (!clk_per_mma || n < 16 || n > nmax || n % 16 || threads < 1 || threads > 4 || tmem_a < 0 ||
+      tmem_a > threads)
+    return CHISAO_ERR_ARG;
+  return tc_measure_mma_rate(n, threads, tmem_a, clk_per_mma, reinterpret_cast<cudaStream_t>(cuda_stream)) ==
+                 cudaSuccess
+             ? CHISAO_OK
+             : CHISAO_ERR_CUDA;
+}
+
 chisao_status chisao_autotune(chisao_ctx* c, int32_t cycles_per_trial, chisao_tuning* out) {
   if (!c) return CHISAO_ERR_ARG;
   if (!out || cycles_per_trial < 1 || cycles_per_trial > 100) return fail(c, CHISAO_ERR_ARG, "bad arguments");

@@ -79,6 +79,8 @@ cudaError_t launch_ext(int which, const ProbDev& P, const StepParams& S, const E
 cudaError_t tc_prepare_attributes();
 // A bounded wait that runs out (budget_ns of the global timer) and raises *err = 2.
 cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st);
+// Clocks per tcgen05.mma (M = 128, K = 16, width n) with `threads` issuers together.
+cudaError_t tc_measure_mma_rate(int n, int threads, int tmem_a, double* clk_per_mma, cudaStream_t st);
 size_t tc_weight_bytes(int K);     // operand tiles of all component groups
 size_t tc_split_floats();          // partial results of a component-split launch
 size_t tc_split_tickets();         // its per-tile arrival counters

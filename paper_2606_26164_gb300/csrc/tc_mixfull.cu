@@ -757,6 +757,61 @@ __global__ void k_wait_selftest(long long budget_ns, int* err) {
   __syncthreads();
 }
 
+// Instruction rate of the tensor core for the MMA shape this kernel issues: lane 0 of
+// warps 0 .. threads - 1 each issues `reps` MMAs (kind::f16, M = 128, K = 16, width n)
+// into its own accumulator (columns 128 i for up to two issuers, 64 i for more; n fits
+// that width), the last tmem_a of them with A read from tensor memory (columns 256 ..),
+// the others from shared memory (zero operands: the rate, not the values, is measured).  clk[i] receives issuer i's clocks from its first issue until
+// its MMAs completed (a bounded wait; *err = 2 when it runs out).
+constexpr int RATE_SMEM = 65536 + 128;
+__global__ void __launch_bounds__(128, 1) k_mma_rate(int n, int reps, int threads, int tmem_a, long long* clk,
+                                                     int* err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 65536);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + 65536 + 64);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int i = t; i < 65536 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
+  if (t == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  if (lane == 0 && warp < threads) {
+    const uint32_t wide = threads <= 2 ? 2u : 1u;      // accumulator and B stride in units of 64 rows
+    const uint32_t d = tmem + 64u * wide * (uint32_t)warp;
+    const uint64_t ad = sdesc(smem_u32(sm), 128, 1024);
+    const uint64_t bd = sdesc(smem_u32(sm + 16384 + (int)(8192u * wide) * warp), 128, 1024);
+    const uint32_t aT = tmem + 256u + 32u * (uint32_t)(warp & 1);
+    const uint32_t id = idesc_bf16(TM, n);
+    const bool ts = warp >= threads - tmem_a;
+    const long long t0 = clock64();
+    for (int r = 0; r < reps; ++r) {
+      if (ts)
+        mma_bf16_ts(d, aT, bd, id, r > 0 ? 1u : 0u);
+      else
+        mma_bf16(d, ad, bd, id, r > 0 ? 1u : 0u);
+    }
+    mma_commit(&bars[warp]);
+    mbar_wait(&bars[warp], 0, err);
+    clk[warp] = clock64() - t0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------ host side
@@ -833,6 +888,35 @@ void tc_build_weights(int K, int d, const double* linv, const double* mu, const 
       cst[kl] = (float)(logw[k] + ldet - d * half_log2pi);
     }
   }
+}
+
+// Clocks per MMA of the tensor core, all issuers together (the slowest issuer's clocks
+// over all MMAs), after one untimed run; synchronizes the stream.
+cudaError_t tc_measure_mma_rate(int n, int threads, int tmem_a, double* clk_per_mma, cudaStream_t st) {
+  constexpr int reps = 2048;
+  long long* clk = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaFuncSetAttribute(tc::k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::RATE_SMEM);
+  if (e == cudaSuccess) e = cudaMalloc(&clk, 4 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+    tc::k_mma_rate<<<1, 128, tc::RATE_SMEM, st>>>(n, reps, threads, tmem_a, clk, err);
+    e = cudaGetLastError();
+  }
+  long long h[4] = {0, 0, 0, 0};
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, clk, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(clk);
+  cudaFree(err);
+  if (e != cudaSuccess) return e;
+  if (herr) return cudaErrorTimeout;
+  long long mx = 0;
+  for (int i = 0; i < threads; ++i) mx = h[i] > mx ? h[i] : mx;
+  *clk_per_mma = (double)mx / ((double)reps * threads);
+  return cudaSuccess;
 }
 
 cudaError_t tc_wait_selftest(long long budget_ns, int* err, cudaStream_t st) {

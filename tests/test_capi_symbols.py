@@ -178,3 +178,13 @@ def test_eval_rejects_bad_points_before_any_launch(lib):
         CH.library = orig
     assert calls == []
     model.ctx = None
+
+
+def test_mma_rate_rejects_bad_arguments_before_any_launch(lib):
+    """The tensor-core rate measurement checks its shape arguments on the host (no GPU
+    needed to get CHISAO_ERR_ARG)."""
+    out = C.c_double(0.0)
+    for n, thr, ta in ((8, 1, 0), (272, 1, 0), (144, 2, 0), (80, 3, 0), (24, 1, 0), (16, 0, 0), (16, 5, 0),
+                      (16, 2, 3), (16, 2, -1)):
+        assert lib.chisao_measure_mma_rate(n, thr, ta, None, C.byref(out)) == CH.ERR_ARG, (n, thr, ta)
+    assert lib.chisao_measure_mma_rate(16, 1, 0, None, None) == CH.ERR_ARG

@@ -566,3 +566,11 @@ def test_tensor_core_component_split():
     fv, _ = model.eval(0, _torch_x(xs), CH.GRAD_ADJOINT_TC, want_grad=False)
     np.testing.assert_array_equal(fv.cpu().numpy(), f2.astype(np.float32))
     model.close()
+
+
+def test_mma_rate_measurement():
+    """The tensor core's rate for the objective's MMA shape (M = 128, K = 16): one issuer
+    is slower per MMA than four together, and every figure is a plausible clock count."""
+    one = CH.measure_mma_rate(64, 1, 0)
+    four = CH.measure_mma_rate(64, 4, 2)
+    assert 8.0 < four < one < 2000.0, (one, four)
