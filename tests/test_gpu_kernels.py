@@ -251,7 +251,7 @@ def _armijo_margin(prob, st, P, Pd, alpha):
 
 
 @pytest.mark.parametrize("mode", [M.GRAD_ADJOINT, M.GRAD_FD64, M.GRAD_FD32])
-@pytest.mark.parametrize("name", ["mix_d5", "mix_d16", "quad_d7", "quad_d12", "full_d3"])
+@pytest.mark.parametrize("name", ["mix_d5", "mix_d16", "mix_d64", "quad_d7", "quad_d12", "quad_d64", "full_d3"])
 def test_lbfgs_iteration(name, mode):
     """One Phase-1 iteration (direction, Armijo search, new gradient, history
     push) from the same binary32 state on both sides."""
