@@ -94,34 +94,49 @@ __global__ void __launch_bounds__(NT_LIN) k_freeze(ProbDev P, StepParams S) { fr
 CHISAO_ALL_KERNEL(k_freeze, NT_LIN, freeze_body(P, S, pos.b))
 
 // ------------------------------------------------------------ ordered compaction
-// One block; thread t owns a contiguous run of mask words; a block scan of the
-// per-thread counts gives each run its output offset, so the list comes out
-// in increasing sample index.
+// One block; warp w owns a contiguous run of mask words; a block scan of the per-warp
+// counts gives each run its output offset, so the list comes out in increasing sample
+// index.  Within a run the warp takes 32 words at a time and writes them one word after
+// another, lane j storing bit j: consecutive set bits go to consecutive positions, so
+// each store is coalesced.
 template <class WordFn>
 __device__ int block_compact(int nwords, WordFn word_of, int* out) {
-  __shared__ int scan[NT_ONE];
-  const int t = threadIdx.x;
-  const int per = (nwords + NT_ONE - 1) / NT_ONE;
-  const int w0 = min(nwords, t * per), w1 = min(nwords, w0 + per);
+  constexpr int NWARP = NT_ONE / 32;
+  __shared__ int scan[NWARP];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (nwords + NWARP - 1) / NWARP;
+  const int w0 = min(nwords, warp * per), w1 = min(nwords, w0 + per);
   int c = 0;
-  for (int w = w0; w < w1; ++w) c += __popc(word_of(w));
-  scan[t] = c;
+  for (int w = w0 + lane; w < w1; w += 32) c += __popc(word_of(w));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) scan[warp] = c;
   __syncthreads();
-  for (int off = 1; off < NT_ONE; off <<= 1) {
-    const int v = t >= off ? scan[t - off] : 0;
-    __syncthreads();
-    scan[t] += v;
-    __syncthreads();
+  int base = 0, total = 0;
+  for (int k = 0; k < NWARP; ++k) {                 // every thread scans the 32 counts itself
+    const int v = scan[k];
+    if (k < warp) base += v;
+    total += v;
   }
-  int base = scan[t] - c;
-  const int total = scan[NT_ONE - 1];
-  for (int w = w0; w < w1; ++w) {
-    unsigned m = word_of(w);
-    while (m) {
-      const int b = __ffs(m) - 1;
-      out[base++] = w * 32 + b;
-      m &= m - 1u;
+  const unsigned below = (1u << lane) - 1u;
+  for (int r0 = w0; r0 < w1; r0 += 32) {
+    const unsigned m = r0 + lane < w1 ? word_of(r0 + lane) : 0u;
+    const int pc = __popc(m);
+    int ex = pc;                                     // inclusive scan of the round's counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, ex, o);
+      if (lane >= o) ex += u;
     }
+    const int round_total = __shfl_sync(0xffffffffu, ex, 31);
+    ex -= pc;
+    const int nk = min(32, w1 - r0);
+    for (int k = 0; k < nk; ++k) {
+      const unsigned mk = __shfl_sync(0xffffffffu, m, k);
+      const int ok = __shfl_sync(0xffffffffu, ex, k);
+      if ((mk >> lane) & 1u) out[base + ok + __popc(mk & below)] = (r0 + k) * 32 + lane;
+    }
+    base += round_total;
   }
   __syncthreads();
   return total;
@@ -623,10 +638,19 @@ __device__ __forceinline__ void finalize_body(const ProbDev& P, const StepParams
     const int col = c0 + cl;
     float h = 0.f, l = 0.f;
     if (col < W) {
-#pragma unroll 4
-      for (int b = q; b < nblocks; b += FIN_RG) {
-        const float2 v = P.partials[(size_t)b * W + col];
-        ff_add(h, l, v.x, v.y);
+      // FIN_PF partials in flight per thread (the single block is bound by load latency),
+      // added in the same order b = q, q + FIN_RG, ...
+      constexpr int FIN_PF = 16;
+      for (int b0 = q; b0 < nblocks; b0 += FIN_PF * FIN_RG) {
+        float2 v[FIN_PF];
+#pragma unroll
+        for (int u = 0; u < FIN_PF; ++u) {
+          const int b = b0 + u * FIN_RG;
+          v[u] = b < nblocks ? P.partials[(size_t)b * W + col] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < FIN_PF; ++u)
+          if (b0 + u * FIN_RG < nblocks) ff_add(h, l, v[u].x, v[u].y);
       }
     }
     part[q][cl] = make_float2(h, l);
