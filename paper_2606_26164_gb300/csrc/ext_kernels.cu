@@ -52,7 +52,7 @@ __device__ __forceinline__ void load_history_ring(const ProbDev& P, int i, int j
 }
 
 template <int DP>
-__global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, ExtBuf E, int count_start) {
+__global__ void __launch_bounds__(NT_OBJ, 4) k_ext_dir(ProbDev P, StepParams S, ExtBuf E, int count_start) {
   constexpr int V = VL, LPS = DP / V;
   const Grp<LPS> g;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / LPS);
@@ -60,7 +60,12 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
   if (i < P.n) {
     const int j0 = V * g.l;
     float G[V], x[V], lo[V], hi[V];
+    // the sample's loads that do not depend on another are issued first (one memory
+    // round trip for these, one more for the history rows they locate)
     ld_vec<V>(P.g + (size_t)i * DP + j0, G);
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    int len = P.hlen[i];
+    const int head = E.head[i];
 #pragma unroll
     for (int v = 0; v < V; ++v) G[v] = -G[v];
     float gl = 0.f;
@@ -68,9 +73,8 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
     for (int v = 0; v < V; ++v) gl = fmaxf(gl, fabsf(G[v]));
     const float gn = g.maxf(gl);
     if (gn > 0.f) {
-      int len = P.hlen[i];
       float s[MMAX][V], y[MMAX][V], rho[MMAX], gam, p[V];
-      load_history_ring<DP, V, LPS>(P, i, j0, len, E.head[i], S.m, s, y, rho, gam, g);
+      load_history_ring<DP, V, LPS>(P, i, j0, len, head, S.m, s, y, rho, gam, g);
       two_loop<V, LPS>(s, y, rho, len, gam, G, p, g);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       if (!(g.sum(dotv<V>(G, p)) <= 0.f)) {          // ascent or not finite: restart
@@ -80,8 +84,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_ext_dir(ProbDev P, StepParams S, Ext
         a0 = fminf(1.f, 1.f / gn);
         if (g.l == 0) P.hlen[i] = 0;
       }
-      ld_vec<V>(P.x + (size_t)i * DP + j0, x);
-      ld_vec<V>(P.lo + j0, lo);
+      ld_vec<V>(P.lo + j0, lo);                      // the box: cache-resident, shared by all samples
       ld_vec<V>(P.hi + j0, hi);
       float c[V];
 #pragma unroll
@@ -110,6 +113,7 @@ __device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams
                                               const float (&c)[V], const float (&Gt)[V], float Ft,
                                               const Grp<LPS>& g) {
   const int head = E.head[i];                          // read by every lane before lane 0 moves it
+  const int len = P.hlen[i];
   float sv[V], yv[V], syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -125,7 +129,6 @@ __device__ __forceinline__ void ext_take_step(const ProbDev& P, const StepParams
   ss = g.sum(ss);
   yy = g.sum(yy);
   if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && 1.0f / sy <= FLT_MAX) {
-    const int len = P.hlen[i];
     const int nh = head > 0 ? head - 1 : S.m - 1;
     const size_t o0 = ((size_t)i * MMAX + nh) * DP + j0;
     st_vec<V>(P.hs + o0, sv);
