@@ -267,6 +267,28 @@ def test_tensor_core_cycle_with_fp32_refinement():
     model.close()
 
 
+def test_tensor_core_cycle_graph_equivalence():
+    """The tensor-core cycle captured in a CUDA graph and launched eagerly leave the same
+    state bit for bit (the line-search rounds fill their lists with atomics, in any order,
+    and every result is per sample) and count the same evaluations, trials and failed
+    searches."""
+    prob = I.mixture256_d64(n=4096)
+    P = M.Params(n_osc=3, n_conv=12, m=10, eps_grad=1e-2, grad_mode=M.GRAD_ADJOINT, seed=7)
+    fields = (CH.FIELD_X, CH.FIELD_G, CH.FIELD_F, CH.FIELD_HS, CH.FIELD_HY, CH.FIELD_HLEN, CH.FIELD_STUCK)
+    keys = ("evals", "grads", "ls_trials", "ls_fail")
+    runs = []
+    for use_graph in (1, 0):
+        model = U.open_ctx(prob, P, grad_mode=CH.GRAD_ADJOINT_TC, use_graph=use_graph)
+        for _ in range(2):
+            model.step()
+        c = model.counters(0)
+        runs.append(({f: model.get(0, f).copy() for f in fields}, {k: c[k] for k in keys}))
+        model.close()
+    for f in fields:
+        np.testing.assert_array_equal(runs[0][0][f], runs[1][0][f])
+    assert runs[0][1] == runs[1][1], runs
+
+
 @pytest.mark.parametrize("d", [8, 16])
 def test_carry_tiger_seeding_on_ackley(d):
     """Sec. 5.3: on Ackley's flat outer region uniform samples see almost no
