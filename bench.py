@@ -724,9 +724,12 @@ def main():
                                                   "(sampled clock)",
                            "fp64_peak_measured": CH.measure_fma_peak(True, model._stream) / 1e12,
                            "launch_ms": 1e3 * t_k, "evals_per_launch": ev_k,
-                           "limiter": "the L1 / shared-memory data path (about 76 % busy under ncu, 486 wavefronts "
-                                      "per warp-iteration: matrix blocks, the history ring, group-reduction "
-                                      "shuffles), not the FMA pipe; profiles/k_phase1_quadratic_d64.md"}
+                           "limiter": "the latency of each warp's serial chain (20 dependent group reductions per "
+                                      "two-loop recursion, the line search's reductions) at the 20 warps per SM "
+                                      "that 96 registers and the 45 KB shared-memory history ring allow: issue "
+                                      "54 %, the L1 / shared-memory path 74 % busy under ncu; moving the history "
+                                      "into tensor memory took that path to 46 % but the launch got slower (16 "
+                                      "warps per SM); profiles/k_phase1_quadratic_d64.md"}
         # --- recovery at a schedule long enough to converge (Prop. 1): one cycle of
         #     n_conv = 2500 on the whole population (the quadratic's mode is its centre)
         if args.workload == "quadratic_d64":
