@@ -42,10 +42,15 @@ def _reseed_case(case, d, N, rng):
 
 
 @pytest.mark.parametrize("case,d", [("rm", 5), ("rm", 64), ("gr", 5), ("gr", 64), ("gr_off", 8),
-                                    ("none", 5), ("no_surv", 3)])
+                                    ("none", 5), ("no_surv", 3), ("rm_large", 7), ("gr_large", 3)])
 def test_reseed(case, d):
+    """The _large cases (N = 70001, 2188 mask words) run the ordered compactions over
+    several 32-word rounds per warp with a ragged last word: the parents Repulse Monkey
+    draws by position in the unfrozen list, and the peaks Golden Rooster takes by rank
+    from the survivor list, come out right only if the lists are in index order."""
     rng = np.random.default_rng(zlib.crc32(f"{case}{d}".encode()))
-    N = 777
+    N = 70001 if case.endswith("_large") else 777
+    case = case.replace("_large", "")
     prob = I.small_mixture(d, 3, N, seed=12)
     P = M.Params(seed=21)
     stuck, removed, gr = _reseed_case(case, d, N, rng)
@@ -148,6 +153,9 @@ HLC_CASES = ([(nm, mode, nc, 8) for nm in ("mix_d3", "mix_d16") for mode in (M.G
              + [(nm, M.GRAD_ADJOINT, nc, Mk) for nm in ("quad_d3", "quad_d12", "quad_d27", "quad_d64")
                 for nc in (1, 3) for Mk in (7, 8)]
              + [(nm, M.GRAD_FD64, 1, 8) for nm in ("quad_d12", "quad_d64")]
+             # d <= 4 with finite differences: the perturbations run on separate lanes (k_hlc_wide),
+             # M = 7 leaving one lane of each sample idle
+             + [("quad_d3", M.GRAD_FD64, nc, Mk) for nc in (1, 3) for Mk in (7, 8)]
              + [(nm, mode, nc, 8) for nm in ("full_d8", "full_d33") for mode in (M.GRAD_ADJOINT, M.GRAD_FD64)
                 for nc in (1, 3)])
 
