@@ -60,13 +60,12 @@ __device__ __forceinline__ void two_loop(const float (&s)[MMAX][V], const float 
 }
 
 // The same recursion over a history held in shared memory as a ring: logical slot
-// k (0 newest) of this lane is row (head + k) mod MMAX of hs / hy (one float4 per
-// lane and slot); rho stays in registers in logical order.
-template <int LPS>
-__device__ __forceinline__ void two_loop_ring(const float4 (*hs)[NT_OBJ], const float4 (*hy)[NT_OBJ], int head,
+// k (0 newest) of this lane is row (head + k) mod MMAX of hs / hy, column t (one float4
+// per lane and slot); rho stays in registers in logical order.
+template <int LPS, int NC = NT_OBJ>
+__device__ __forceinline__ void two_loop_ring(const float4 (*hs)[NC], const float4 (*hy)[NC], int head,
                                               const float (&rho)[MMAX], int len, float gam, const float (&G)[4],
-                                              float (&p)[4], const Grp<LPS>& g) {
-  const int t = threadIdx.x;
+                                              float (&p)[4], const Grp<LPS>& g, int t) {
   float q[4], al[MMAX];
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = G[v];
@@ -207,7 +206,7 @@ __device__ __forceinline__ void phase1_body(const ProbDev& P, const StepParams& 
       const float gn = g.maxf(gl);
       if (!(gn > 0.f)) break;                      // exactly stationary (or invalid): stays put
       float p[V];
-      two_loop_ring<LPS>(hist_s, hist_y, head, rho, len, gam, G, p, g);
+      two_loop_ring<LPS>(hist_s, hist_y, head, rho, len, gam, G, p, g, (int)threadIdx.x);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       const float gp = g.sum(dotv<V>(G, p));
       // restart when p is an ascent direction or not finite; g^T p = 0 (the product
@@ -333,6 +332,246 @@ template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1(ProbDev P, StepParams S, int n_iter, int fresh,
                                                    const int* __restrict__ rows, const int* __restrict__ nrows) {
   phase1_body<KIND, DP, GM>(P, S, n_iter, fresh, rows, nrows, blockIdx.x);
+}
+
+// Phase 1 for samples of at most four coordinates (one lane each) with finite-difference
+// gradients.  There a sample's iteration is a serial chain of scalar evaluations: up to T_ls
+// Armijo trials (all of them at a mode, where no step decreases F) and the 2d stencil points
+// of the new gradient.  Here P1_W lanes share a sample and keep identical copies of its
+// state: a batch of P1_W trials is evaluated side by side (lane j trial t0 + j) and the
+// first that passes is taken, which is the step sequential backtracking takes, and the
+// stencil points are spread over the lanes (lane 2v: x + h e_v, lane 2v + 1: x - h e_v).
+// Every value is the one phase1_body computes, so the results (and the counters, which
+// count the trials and evaluations of the sequential search) are the same bit for bit.
+constexpr int P1_W = 8;
+
+// Central differences with the 2d stencil values evaluated on the lanes of the group
+// (d <= 4), combined on every lane exactly as fd_gradient combines them.
+template <int KIND, int GM>
+__device__ __forceinline__ void fd_gradient_wide(const ObjDev& O, const StepParams& S, int d, const float (&xf)[4],
+                                                 float (&gr)[4], const Grp<1>& g, int j, unsigned wmask) {
+  using TE = EvalT<GM>;
+  const auto& o = params_of<GM>(O);
+  TE x[4], xs[4], hs[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    x[v] = (TE)xf[v];
+    gr[v] = 0.f;
+    hs[v] = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(x[v])) : (TE)S.h;
+  }
+  // this lane's stencil point: coordinate j / 2, plus for even j, minus for odd j
+  const int v0 = j >> 1;
+  TE fv = TE(0);
+  if (v0 < d) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) xs[v] = x[v];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if (v == v0) xs[v] = (j & 1) ? stencil_sub(x[v], hs[v]) : stencil_add(x[v], hs[v]);
+    fv = value_noisy<KIND, TE, 4, 1>(O, o, S, xs, g);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const TE fp = __shfl_sync(wmask, fv, 2 * v, P1_W), fm = __shfl_sync(wmask, fv, 2 * v + 1, P1_W);
+    if (v < d) {
+      const TE xp = stencil_add(x[v], hs[v]), xm = stencil_sub(x[v], hs[v]);
+      gr[v] = (float)((fp - fm) / (xp - xm));
+    }
+  }
+}
+
+template <int KIND, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S, int n_iter, int fresh,
+                                                        const int* __restrict__ rows, const int* __restrict__ nrows) {
+  constexpr int DP = 4, V = VL, LPS = 1, NS = NT_OBJ / P1_W;    // samples per block
+  static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
+  using TE = EvalT<GM>;
+  __shared__ float4 hist_s[MMAX][NS], hist_y[MMAX][NS];        // one ring per sample
+  const Grp<LPS> g;
+  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1), col = (int)threadIdx.x / P1_W;
+  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
+  const int gi = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  const bool act = rows ? gi < *nrows : gi < P.n;
+  const int i = rows ? (act ? rows[gi] : 0) : gi;
+  unsigned long long evals = 0, grads = 0, trials = 0, fails = 0;
+  if (act) {
+    float x[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP, x);
+    ld_vec<V>(P.lo, lo);
+    ld_vec<V>(P.hi, hi);
+    int len = P.hlen[i];
+    float rho[MMAX], gam = 1.f;
+    int head = 0;
+#pragma unroll
+    for (int k = 0; k < MMAX; ++k) {
+      rho[k] = 0.f;
+      if (k < len) {
+        const size_t o = ((size_t)i * MMAX + k) * DP;
+        if (j == 0) {
+          hist_s[k][col] = *reinterpret_cast<const float4*>(P.hs + o);
+          hist_y[k][col] = *reinterpret_cast<const float4*>(P.hy + o);
+        }
+        rho[k] = P.hrho[(size_t)i * MMAX + k];
+      }
+    }
+    __syncwarp(wmask);
+    if (len > 0) {
+      const float4 y4 = hist_y[0][col];
+      const float y0[V] = {y4.x, y4.y, y4.z, y4.w};
+      gam = (1.0f / rho[0]) / g.sum(dotv<V>(y0, y0));
+    }
+    TE F;
+    float G[V];
+    if (fresh) {
+      TE xe[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) xe[v] = (TE)x[v];
+      F = -value_noisy<KIND, TE, V, LPS>(P.obj, params_of<GM>(P.obj), S, xe, g);
+      float a[V];
+      fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, a, g, j, wmask);
+      evals += 1 + 2ull * P.d;
+      grads += 1;
+#pragma unroll
+      for (int v = 0; v < V; ++v) G[v] = -a[v];
+    } else {
+      F = -(TE)P.f[i];
+      ld_vec<V>(P.g + (size_t)i * DP, G);
+#pragma unroll
+      for (int v = 0; v < V; ++v) G[v] = -G[v];
+    }
+    for (int it = 0; it < n_iter; ++it) {
+      float gl = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) gl = fmaxf(gl, fabsf(G[v]));
+      const float gn = g.maxf(gl);
+      if (!(gn > 0.f)) break;                        // exactly stationary (or invalid): stays put
+      float p[V];
+      two_loop_ring<LPS, NS>(hist_s, hist_y, head, rho, len, gam, G, p, g, col);
+      float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
+      const float gp = g.sum(dotv<V>(G, p));
+      if (!(gp <= 0.f)) {
+        len = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = -G[v];
+        a0 = fminf(1.f, 1.f / gn);
+      }
+      // the trials in batches of P1_W: the first that passes wins
+      int tacc = -1;
+      TE Ft = F;
+      for (int t0 = 0; t0 < S.T_ls && tacc < 0; t0 += P1_W) {
+        const int t = t0 + j;
+        bool pass = false;
+        TE ft = TE(0);
+        if (t < S.T_ls) {
+          const float a = ldexpf(a0, -t);
+          float c[V];
+          TE ce[V];
+          TE dl = TE(0);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            c[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
+            dl += (TE)G[v] * ((TE)c[v] - (TE)x[v]);
+            ce[v] = (TE)c[v];
+          }
+          ft = value_noisy<KIND, TE, V, LPS>(P.obj, params_of<GM>(P.obj), S, ce, g);
+          const TE dec = g.sum(dl);
+          pass = -ft <= F + (TE)S.c1 * dec;
+        }
+        const unsigned b = (__ballot_sync(wmask, pass) & wmask) >> (lane & ~(P1_W - 1));
+        const int nt = min(P1_W, S.T_ls - t0);
+        if (b) {
+          const int q = __ffs(b) - 1;
+          tacc = t0 + q;
+          Ft = -__shfl_sync(wmask, ft, q, P1_W);
+          trials += q + 1;
+          evals += q + 1;
+        } else {
+          trials += nt;
+          evals += nt;
+        }
+      }
+      if (tacc < 0) {
+        len = 0;
+        ++fails;
+        continue;
+      }
+      float xt[V], Gt[V];
+      {
+        const float a = ldexpf(a0, -tacc);
+#pragma unroll
+        for (int v = 0; v < V; ++v) xt[v] = clampf(fmaf(a, p[v], x[v]), lo[v], hi[v]);
+      }
+      {
+        float ag[V];
+        fd_gradient_wide<KIND, GM>(P.obj, S, P.d, xt, ag, g, j, wmask);
+        evals += 2ull * P.d;
+        grads += 1;
+#pragma unroll
+        for (int v = 0; v < V; ++v) Gt[v] = -ag[v];
+      }
+      float sv[V], yv[V];
+      float syh = 0.f, syl = 0.f, ss = 0.f, yy = 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sv[v] = xt[v] - x[v];
+        yv[v] = Gt[v] - G[v];
+        const float pr = sv[v] * yv[v];
+        ff_add(syh, syl, pr, fmaf(sv[v], yv[v], -pr));
+        ss = fmaf(sv[v], sv[v], ss);
+        yy = fmaf(yv[v], yv[v], yy);
+      }
+      g.ff_sum(syh, syl);
+      const float sy = syh + syl;
+      ss = g.sum(ss);
+      yy = g.sum(yy);
+      const float rsy = 1.0f / sy;
+      if (sy > (float)S.curv_eps * sqrtf(ss) * sqrtf(yy) && rsy <= FLT_MAX) {
+#pragma unroll
+        for (int k = MMAX - 1; k > 0; --k) rho[k] = rho[k - 1];
+        head = head == 0 ? MMAX - 1 : head - 1;
+        __syncwarp(wmask);                           // every lane has read the row it replaces
+        if (j == 0) {
+          hist_s[head][col] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+          hist_y[head][col] = make_float4(yv[0], yv[1], yv[2], yv[3]);
+        }
+        __syncwarp(wmask);
+        rho[0] = rsy;
+        len = min(len + 1, S.m);
+        gam = sy / yy;
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        x[v] = xt[v];
+        G[v] = Gt[v];
+      }
+      F = Ft;
+    }
+    if (j == 0) {
+      float gout[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) gout[v] = -G[v];
+      st_vec<V>(P.x + (size_t)i * DP, x);
+      st_vec<V>(P.g + (size_t)i * DP, gout);
+#pragma unroll
+      for (int k = 0; k < MMAX; ++k) {
+        if (k < len) {
+          const size_t o = ((size_t)i * MMAX + k) * DP;
+          const int r = head + k < MMAX ? head + k : head + k - MMAX;
+          *reinterpret_cast<float4*>(P.hs + o) = hist_s[r][col];
+          *reinterpret_cast<float4*>(P.hy + o) = hist_y[r][col];
+          P.hrho[(size_t)i * MMAX + k] = rho[k];
+        }
+      }
+      P.f[i] = (float)(-F);
+      P.hlen[i] = len;
+    } else {
+      evals = grads = trials = fails = 0;
+    }
+  }
+  block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
+  block_add_u64<NT_OBJ>(trials, &P.cnt->ls_trials);
+  block_add_u64<NT_OBJ>(fails, &P.cnt->ls_fail);
 }
 
 // Phase 1 of every problem of a group in one launch (n_conv iterations each, fresh gradient).
@@ -697,6 +936,11 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
   if (rows <= 0) return cudaSuccess;
   switch (which) {
     case OKID_PHASE1:
+      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
+        k_phase1_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
+            P, S, arg < 0 ? -arg : arg, arg >= 0 ? 1 : 0, nullptr, nullptr);
+        break;
+      }
       k_phase1<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S, arg < 0 ? -arg : arg, arg >= 0 ? 1 : 0, nullptr,
                                                         nullptr);
       break;

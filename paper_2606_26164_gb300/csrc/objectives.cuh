@@ -791,6 +791,13 @@ __device__ __forceinline__ EvalT<GM> value_at(const ObjDev& O, const StepParams&
   return value_noisy<KIND, TE, V, LPS>(O, params_of<GM>(O), S, x, g);
 }
 
+// The stencil coordinates x_j +- h_j, each one rounded sum (never fused with the product that
+// forms h_j), so every kernel that forms them gets the same bits.
+__device__ __forceinline__ float stencil_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float stencil_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double stencil_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double stencil_sub(double a, double b) { return __dsub_rn(a, b); }
+
 // Central differences on the coordinates j < d: g_j = (f(x + h_j e_j) - f(x - h_j e_j)) / (x+_j - x-_j),
 // the stencil points regenerated one at a time in registers.
 template <int KIND, int GM, int V, int LPS>
@@ -811,7 +818,7 @@ __device__ __forceinline__ void fd_gradient(const ObjDev& O, const StepParams& S
       if (jl * V + v < d) {
         const TE xj = g.bcast(x[v], jl);
         const TE hj = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(xj)) : (TE)S.h;
-        const TE xp = xj + hj, xm = xj - hj;
+        const TE xp = stencil_add(xj, hj), xm = stencil_sub(xj, hj);
         const bool mine = (g.l == jl);
         TE y[V];
 #pragma unroll
