@@ -574,6 +574,81 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
   block_add_u64<NT_OBJ>(fails, &P.cnt->ls_fail);
 }
 
+// The gradients a scale pass needs, for samples of at most four coordinates with finite
+// differences, on P1_W lanes per sample (fd_gradient_wide): every unfrozen sample, or with
+// removed_only those Phase 4 reseeded (the others keep Phase 1's).  The scale pass then
+// reads them (reuse = 2) and sums in its own fixed order, so sigma and alpha are the one-
+// lane pass's bit for bit.
+template <int KIND, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_grad_wide(ProbDev P, StepParams S, int removed_only) {
+  constexpr int DP = 4, V = VL;
+  static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
+  const Grp<1> g;
+  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1);
+  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
+  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  unsigned long long evals = 0, grads = 0;
+  if (i < P.n && !bit_of(P.stuck, i) && (!removed_only || bit_of(P.removed, i))) {
+    float x[V], a[V];
+    ld_vec<V>(P.x + (size_t)i * DP, x);
+    fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, a, g, j, wmask);
+    if (j == 0) {
+      st_vec<V>(P.g + (size_t)i * DP, a);
+      evals = 2ull * P.d;
+      grads = 1;
+    }
+  }
+  block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
+}
+
+// Anti-convergence (Eq. 6) for samples of at most four coordinates with finite differences:
+// anti_body's steps with each step's gradient evaluated on P1_W lanes (fd_gradient_wide);
+// the lanes keep identical copies of the sample's position and velocity.
+template <int KIND, int GM>
+__global__ void __launch_bounds__(NT_OBJ) k_anti_wide(ProbDev P, StepParams S) {
+  constexpr int DP = 4, V = VL;
+  static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
+  const Grp<1> g;
+  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1);
+  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
+  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  unsigned long long evals = 0, grads = 0;
+  if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
+    const float alpha = P.cnt->sc_alpha, mu = S.mu;
+    float x[V], gr[V], vel[V], lo[V], hi[V];
+    ld_vec<V>(P.x + (size_t)i * DP, x);
+    ld_vec<V>(P.g + (size_t)i * DP, gr);
+    ld_vec<V>(P.lo, lo);
+    ld_vec<V>(P.hi, hi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) vel[v] = 0.f;
+    for (int t = 0; t < S.n_anti; ++t) {
+      if (t > 0) {
+        fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, gr, g, j, wmask);
+        evals += 2ull * P.d;
+        grads += 1;
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        vel[v] = mu * vel[v] - alpha * gr[v];
+        const float nx = x[v] + vel[v];
+        const float cx = clampf(nx, lo[v], hi[v]);
+        if (cx != nx) vel[v] = 0.f;
+        x[v] = cx;
+      }
+    }
+    if (j == 0) {
+      st_vec<V>(P.x + (size_t)i * DP, x);
+      P.hlen[i] = 0;
+    } else {
+      evals = grads = 0;
+    }
+  }
+  block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
+  block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
+}
+
 // Phase 1 of every problem of a group in one launch (n_conv iterations each, fresh gradient).
 template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase1_grp(GroupTab T) {
@@ -637,9 +712,10 @@ __device__ __forceinline__ void scales_body(const ProbDev& P, const StepParams& 
       ld_vec<V>(P.g + (size_t)i * DP + j0, a);          // computed by the batched evaluator
       ec.evals += 1;
       ec.grads += 1;
-    } else if (reuse && !bit_of(P.removed, i)) {
+    } else if (reuse == 2 || (reuse && !bit_of(P.removed, i))) {
       // Phase 1 left the gradient at this point in g and nothing has moved the sample
-      // since (only the reseeded slots, the removed ones, have): the same bits
+      // since (only the reseeded slots, the removed ones, have): the same bits.  With
+      // reuse = 2 a wide pre-pass (k_grad_wide) has just stored every gradient needed.
       ld_vec<V>(P.g + (size_t)i * DP + j0, a);
     } else {
       gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, x, a, g, ec);
@@ -951,6 +1027,11 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_direction<DP><<<blocks, NT_OBJ, 0, st>>>(P);
       break;
     case OKID_SCALES:
+      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
+        k_grad_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(P, S, arg);
+        k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, 2);
+        break;
+      }
       k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, arg);
       break;
     case OKID_HLC:
@@ -963,6 +1044,10 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_hlc<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
       break;
     case OKID_ANTI:
+      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
+        k_anti_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(P, S);
+        break;
+      }
       k_anti<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
       break;
     case OKID_EVAL:
