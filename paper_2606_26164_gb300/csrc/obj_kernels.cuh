@@ -850,32 +850,34 @@ __device__ __forceinline__ void hlc_body(const ProbDev& P, const StepParams& S, 
   block_add_u64<NT_OBJ>(ec.grads, &P.cnt->grads);
 }
 
-// Hands Like Clouds for samples of at most four coordinates (one lane each) with finite-
-// difference gradients: the gradient at each perturbed point is a serial chain of 2d + 1
-// evaluations, and one lane per sample would run the M chains of a step one after another.
-// Here HLC_W lanes share a sample: lane k draws perturbation k's normals and evaluates its
-// gradient (the same calls as the one-lane loop), and every lane adds the M gradients in
-// the order k = 0, 1, ... by shuffles, so the step is the one-lane kernel's bit for bit with
+// Hands Like Clouds for samples of at most sixteen coordinates (a group of DP / 4 lanes each)
+// with finite-difference gradients: the gradient at each perturbed point is a serial chain of
+// 2d evaluations, and one group per sample would run the M chains of a step one after another.
+// Here HLC_W groups share a sample: group k draws perturbation k's normals and evaluates its
+// gradient (the same calls as the one-group loop), and every group adds the M gradients in the
+// order k = 0, 1, ... by shuffles, so the step is the one-group kernel's bit for bit with
 // M-fold shorter chains and HLC_W times the warps.  Used when M <= HLC_W and the gradient
 // estimator is Eq. 5's (not the value-only variant).
 constexpr int HLC_W = 8;
-template <int KIND, int GM>
+template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_hlc_wide(ProbDev P, StepParams S) {
-  constexpr int DP = 4, V = VL, LPS = 1;
+  constexpr int V = VL, LPS = DP / V, SL = HLC_W * LPS;      // lanes per sample
   static_assert(GM != GRAD_ADJOINT, "exact gradients keep the paired and multi-point products of k_hlc");
-  const Grp<LPS> g;                                   // the objective sees each lane as one sample's lane
+  static_assert(SL <= 32, "a sample within one warp");
+  const Grp<LPS> g;                                         // this group's lanes (one copy of the sample)
   const int lane = threadIdx.x & 31;
-  const int k = lane & (HLC_W - 1);                  // this lane's perturbation
-  const unsigned wmask = ((1u << HLC_W) - 1u) << (lane & ~(HLC_W - 1));
-  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / HLC_W);
+  const int k = (lane / LPS) & (HLC_W - 1);                // this group's perturbation
+  const unsigned smask = SL == 32 ? 0xffffffffu : ((1u << SL) - 1u) << (lane & ~(SL - 1));
+  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / SL);
   EvalCount ec;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
+    const int j0 = V * g.l;
     const unsigned cyc = (unsigned)P.cnt->cycle + 1u;
     const float sigma = P.cnt->sc_sigma, alpha = P.cnt->sc_alpha;
     float x[V], lo[V], hi[V];
-    ld_vec<V>(P.x + (size_t)i * DP, x);
-    ld_vec<V>(P.lo, lo);
-    ld_vec<V>(P.hi, hi);
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
     const float invM = 1.0f / (float)S.M;
     for (int t = 0; t < S.n_cloud; ++t) {
       float a[V];
@@ -883,10 +885,10 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc_wide(ProbDev P, StepParams S) {
       for (int v = 0; v < V; ++v) a[v] = 0.f;
       if (k < S.M) {
         float z[V], xp[V];
-        normals_lane<V>(S, (unsigned)i, 0, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index, (unsigned)k,
+        normals_lane<V>(S, (unsigned)i, g.l, TAG_HLC, cyc, (unsigned)t, (unsigned)P.obj.prob_index, (unsigned)k,
                         z);
 #pragma unroll
-        for (int v = 0; v < V; ++v) xp[v] = (v < P.d) ? fmaf(sigma, z[v], x[v]) : x[v];
+        for (int v = 0; v < V; ++v) xp[v] = (j0 + v < P.d) ? fmaf(sigma, z[v], x[v]) : x[v];
         gradient_only<KIND, GM, V, LPS>(P.obj, S, P.d, xp, a, g, ec);
       }
       float acc[V];
@@ -896,15 +898,16 @@ __global__ void __launch_bounds__(NT_OBJ) k_hlc_wide(ProbDev P, StepParams S) {
       for (int q = 0; q < HLC_W; ++q)
         if (q < S.M) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] += __shfl_sync(wmask, a[v], q, HLC_W);
+          for (int v = 0; v < V; ++v) acc[v] += __shfl_sync(smask, a[v], q * LPS + g.l, SL);
         }
 #pragma unroll
       for (int v = 0; v < V; ++v) x[v] = clampf(fmaf(alpha, acc[v] * invM, x[v]), lo[v], hi[v]);
     }
     if (k == 0) {
-      st_vec<V>(P.x + (size_t)i * DP, x);
-      P.hlen[i] = 0;
+      st_vec<V>(P.x + (size_t)i * DP + j0, x);
+      if (g.l == 0) P.hlen[i] = 0;
     }
+    if (g.l != 0) ec.evals = ec.grads = 0;
   }
   block_add_u64<NT_OBJ>(ec.evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(ec.grads, &P.cnt->grads);
@@ -1035,9 +1038,10 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, arg);
       break;
     case OKID_HLC:
-      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
+      if constexpr (DP <= 16 && GM != GRAD_ADJOINT) {
         if (S.M <= HLC_W && !S.hlc_value_only) {
-          k_hlc_wide<KIND, GM><<<(unsigned)((rows * HLC_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(P, S);
+          k_hlc_wide<KIND, DP, GM><<<(unsigned)((rows * HLC_W * (DP / VL) + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
+              P, S);
           break;
         }
       }
