@@ -334,71 +334,97 @@ __global__ void __launch_bounds__(NT_OBJ, phase1_min_blocks<KIND, GM>()) k_phase
   phase1_body<KIND, DP, GM>(P, S, n_iter, fresh, rows, nrows, blockIdx.x);
 }
 
-// Phase 1 for samples of at most four coordinates (one lane each) with finite-difference
-// gradients.  There a sample's iteration is a serial chain of scalar evaluations: up to T_ls
-// Armijo trials (all of them at a mode, where no step decreases F) and the 2d stencil points
-// of the new gradient.  Here P1_W lanes share a sample and keep identical copies of its
-// state: a batch of P1_W trials is evaluated side by side (lane j trial t0 + j) and the
-// first that passes is taken, which is the step sequential backtracking takes, and the
-// stencil points are spread over the lanes (lane 2v: x + h e_v, lane 2v + 1: x - h e_v).
-// Every value is the one phase1_body computes, so the results (and the counters, which
-// count the trials and evaluations of the sequential search) are the same bit for bit.
+// Phase 1 for samples of at most sixteen coordinates (a group of DP / 4 lanes each) with
+// finite-difference gradients.  There a sample's iteration is a serial chain of evaluations:
+// up to T_ls Armijo trials (all of them at a mode, where no step decreases F) and the 2d
+// stencil points of the new gradient.  Here P1_W groups share a sample and keep identical
+// copies of its state: a batch of P1_W trials is evaluated side by side (group q trial t0 + q)
+// and the first that passes is taken, which is the step sequential backtracking takes, and the
+// stencil points are spread over the groups (fd_gradient_wide).  Every value is the one
+// phase1_body computes, so the results (and the counters, which count the trials and
+// evaluations of the sequential search) are the same bit for bit.
 constexpr int P1_W = 8;
 
-// Central differences with the 2d stencil values evaluated on the lanes of the group
-// (d <= 4), combined on every lane exactly as fd_gradient combines them.
-template <int KIND, int GM>
+// The lanes of one sample: P1_W groups of LPS lanes, aligned in the warp.
+template <int LPS>
+__device__ __forceinline__ unsigned wide_mask() {
+  constexpr int SL = P1_W * LPS;
+  const int lane = threadIdx.x & 31;
+  return SL == 32 ? 0xffffffffu : ((1u << SL) - 1u) << (lane & ~(SL - 1));
+}
+
+// Central differences with the 2d stencil values spread over the P1_W groups of a sample
+// (group q evaluates the points s = 8 r + q, r < LPS: coordinate s / 2, plus for even s,
+// minus for odd s), combined on every group exactly as fd_gradient combines them.  Lane l's
+// coordinates 4 l + v take their two values from round l of groups 2 v and 2 v + 1.
+template <int KIND, int GM, int LPS>
 __device__ __forceinline__ void fd_gradient_wide(const ObjDev& O, const StepParams& S, int d, const float (&xf)[4],
-                                                 float (&gr)[4], const Grp<1>& g, int j, unsigned wmask) {
+                                                 float (&gr)[4], const Grp<LPS>& g, int q, unsigned smask) {
   using TE = EvalT<GM>;
+  constexpr int SL = P1_W * LPS;
   const auto& o = params_of<GM>(O);
-  TE x[4], xs[4], hs[4];
+  TE x[4], hs[4], fr[LPS];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     x[v] = (TE)xf[v];
     gr[v] = 0.f;
     hs[v] = (GM == GRAD_FD32) ? (TE)S.h_rel * fmax((TE)1, fabs(x[v])) : (TE)S.h;
   }
-  // this lane's stencil point: coordinate j / 2, plus for even j, minus for odd j
-  const int v0 = j >> 1;
-  TE fv = TE(0);
-  if (v0 < d) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) xs[v] = x[v];
+  for (int r = 0; r < LPS; ++r) {
+    const int sp = P1_W * r + q, js = sp >> 1;
+    fr[r] = TE(0);
+    if (js < d) {
+      TE y[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if (v == v0) xs[v] = (j & 1) ? stencil_sub(x[v], hs[v]) : stencil_add(x[v], hs[v]);
-    fv = value_noisy<KIND, TE, 4, 1>(O, o, S, xs, g);
+      for (int v = 0; v < 4; ++v) {
+        y[v] = x[v];
+        if (g.l == (js >> 2) && v == (js & 3)) y[v] = (sp & 1) ? stencil_sub(x[v], hs[v]) : stencil_add(x[v], hs[v]);
+      }
+      fr[r] = value_noisy<KIND, TE, 4, LPS>(O, o, S, y, g);
+    }
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const TE fp = __shfl_sync(wmask, fv, 2 * v, P1_W), fm = __shfl_sync(wmask, fv, 2 * v + 1, P1_W);
-    if (v < d) {
+    TE fp = TE(0), fm = TE(0);
+#pragma unroll
+    for (int r = 0; r < LPS; ++r) {
+      const TE a = __shfl_sync(smask, fr[r], (2 * v) * LPS + g.l, SL);
+      const TE b = __shfl_sync(smask, fr[r], (2 * v + 1) * LPS + g.l, SL);
+      if (r == g.l) {
+        fp = a;
+        fm = b;
+      }
+    }
+    if (4 * g.l + v < d) {
       const TE xp = stencil_add(x[v], hs[v]), xm = stencil_sub(x[v], hs[v]);
       gr[v] = (float)((fp - fm) / (xp - xm));
     }
   }
 }
 
-template <int KIND, int GM>
+template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S, int n_iter, int fresh,
                                                         const int* __restrict__ rows, const int* __restrict__ nrows) {
-  constexpr int DP = 4, V = VL, LPS = 1, NS = NT_OBJ / P1_W;    // samples per block
+  constexpr int V = VL, LPS = DP / V, SL = P1_W * LPS, NC = NT_OBJ / P1_W;   // ring columns per block
   static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
+  static_assert(SL <= 32, "a sample within one warp");
   using TE = EvalT<GM>;
-  __shared__ float4 hist_s[MMAX][NS], hist_y[MMAX][NS];        // one ring per sample
+  __shared__ float4 hist_s[MMAX][NC], hist_y[MMAX][NC];        // one ring per sample, shared by its groups
   const Grp<LPS> g;
-  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1), col = (int)threadIdx.x / P1_W;
-  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
-  const int gi = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  const int lane = threadIdx.x & 31, q = (lane / LPS) & (P1_W - 1);
+  const int col = (int)(threadIdx.x / SL) * LPS + g.l;
+  const unsigned smask = wide_mask<LPS>();
+  const int gi = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / SL);
   const bool act = rows ? gi < *nrows : gi < P.n;
   const int i = rows ? (act ? rows[gi] : 0) : gi;
   unsigned long long evals = 0, grads = 0, trials = 0, fails = 0;
   if (act) {
+    const int j0 = V * g.l;
     float x[V], lo[V], hi[V];
-    ld_vec<V>(P.x + (size_t)i * DP, x);
-    ld_vec<V>(P.lo, lo);
-    ld_vec<V>(P.hi, hi);
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
     int len = P.hlen[i];
     float rho[MMAX], gam = 1.f;
     int head = 0;
@@ -406,15 +432,15 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
     for (int k = 0; k < MMAX; ++k) {
       rho[k] = 0.f;
       if (k < len) {
-        const size_t o = ((size_t)i * MMAX + k) * DP;
-        if (j == 0) {
+        const size_t o = ((size_t)i * MMAX + k) * DP + j0;
+        if (q == 0) {
           hist_s[k][col] = *reinterpret_cast<const float4*>(P.hs + o);
           hist_y[k][col] = *reinterpret_cast<const float4*>(P.hy + o);
         }
         rho[k] = P.hrho[(size_t)i * MMAX + k];
       }
     }
-    __syncwarp(wmask);
+    __syncwarp(smask);
     if (len > 0) {
       const float4 y4 = hist_y[0][col];
       const float y0[V] = {y4.x, y4.y, y4.z, y4.w};
@@ -428,14 +454,14 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
       for (int v = 0; v < V; ++v) xe[v] = (TE)x[v];
       F = -value_noisy<KIND, TE, V, LPS>(P.obj, params_of<GM>(P.obj), S, xe, g);
       float a[V];
-      fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, a, g, j, wmask);
+      fd_gradient_wide<KIND, GM, LPS>(P.obj, S, P.d, x, a, g, q, smask);
       evals += 1 + 2ull * P.d;
       grads += 1;
 #pragma unroll
       for (int v = 0; v < V; ++v) G[v] = -a[v];
     } else {
       F = -(TE)P.f[i];
-      ld_vec<V>(P.g + (size_t)i * DP, G);
+      ld_vec<V>(P.g + (size_t)i * DP + j0, G);
 #pragma unroll
       for (int v = 0; v < V; ++v) G[v] = -G[v];
     }
@@ -446,7 +472,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
       const float gn = g.maxf(gl);
       if (!(gn > 0.f)) break;                        // exactly stationary (or invalid): stays put
       float p[V];
-      two_loop_ring<LPS, NS>(hist_s, hist_y, head, rho, len, gam, G, p, g, col);
+      two_loop_ring<LPS, NC>(hist_s, hist_y, head, rho, len, gam, G, p, g, col);
       float a0 = len > 0 ? 1.f : fminf(1.f, 1.f / gn);
       const float gp = g.sum(dotv<V>(G, p));
       if (!(gp <= 0.f)) {
@@ -459,7 +485,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
       int tacc = -1;
       TE Ft = F;
       for (int t0 = 0; t0 < S.T_ls && tacc < 0; t0 += P1_W) {
-        const int t = t0 + j;
+        const int t = t0 + q;
         bool pass = false;
         TE ft = TE(0);
         if (t < S.T_ls) {
@@ -477,14 +503,17 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
           const TE dec = g.sum(dl);
           pass = -ft <= F + (TE)S.c1 * dec;
         }
-        const unsigned b = (__ballot_sync(wmask, pass) & wmask) >> (lane & ~(P1_W - 1));
+        const unsigned b = (__ballot_sync(smask, pass) & smask) >> (lane & ~(SL - 1));
+        unsigned gb = 0;                              // one bit per group (its lanes agree)
+#pragma unroll
+        for (int w = 0; w < P1_W; ++w) gb |= ((b >> (w * LPS)) & 1u) << w;
         const int nt = min(P1_W, S.T_ls - t0);
-        if (b) {
-          const int q = __ffs(b) - 1;
-          tacc = t0 + q;
-          Ft = -__shfl_sync(wmask, ft, q, P1_W);
-          trials += q + 1;
-          evals += q + 1;
+        if (gb) {
+          const int w = __ffs(gb) - 1;
+          tacc = t0 + w;
+          Ft = -__shfl_sync(smask, ft, w * LPS + g.l, SL);
+          trials += w + 1;
+          evals += w + 1;
         } else {
           trials += nt;
           evals += nt;
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
       }
       {
         float ag[V];
-        fd_gradient_wide<KIND, GM>(P.obj, S, P.d, xt, ag, g, j, wmask);
+        fd_gradient_wide<KIND, GM, LPS>(P.obj, S, P.d, xt, ag, g, q, smask);
         evals += 2ull * P.d;
         grads += 1;
 #pragma unroll
@@ -529,12 +558,12 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
 #pragma unroll
         for (int k = MMAX - 1; k > 0; --k) rho[k] = rho[k - 1];
         head = head == 0 ? MMAX - 1 : head - 1;
-        __syncwarp(wmask);                           // every lane has read the row it replaces
-        if (j == 0) {
+        __syncwarp(smask);                           // every lane has read the row it replaces
+        if (q == 0) {
           hist_s[head][col] = make_float4(sv[0], sv[1], sv[2], sv[3]);
           hist_y[head][col] = make_float4(yv[0], yv[1], yv[2], yv[3]);
         }
-        __syncwarp(wmask);
+        __syncwarp(smask);
         rho[0] = rsy;
         len = min(len + 1, S.m);
         gam = sy / yy;
@@ -546,27 +575,28 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
       }
       F = Ft;
     }
-    if (j == 0) {
+    if (q == 0) {
       float gout[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) gout[v] = -G[v];
-      st_vec<V>(P.x + (size_t)i * DP, x);
-      st_vec<V>(P.g + (size_t)i * DP, gout);
+      st_vec<V>(P.x + (size_t)i * DP + j0, x);
+      st_vec<V>(P.g + (size_t)i * DP + j0, gout);
 #pragma unroll
       for (int k = 0; k < MMAX; ++k) {
         if (k < len) {
-          const size_t o = ((size_t)i * MMAX + k) * DP;
+          const size_t o = ((size_t)i * MMAX + k) * DP + j0;
           const int r = head + k < MMAX ? head + k : head + k - MMAX;
           *reinterpret_cast<float4*>(P.hs + o) = hist_s[r][col];
           *reinterpret_cast<float4*>(P.hy + o) = hist_y[r][col];
-          P.hrho[(size_t)i * MMAX + k] = rho[k];
+          if (g.l == 0) P.hrho[(size_t)i * MMAX + k] = rho[k];
         }
       }
-      P.f[i] = (float)(-F);
-      P.hlen[i] = len;
-    } else {
-      evals = grads = trials = fails = 0;
+      if (g.l == 0) {
+        P.f[i] = (float)(-F);
+        P.hlen[i] = len;
+      }
     }
+    if (q != 0 || g.l != 0) evals = grads = trials = fails = 0;
   }
   block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
@@ -574,58 +604,62 @@ __global__ void __launch_bounds__(NT_OBJ) k_phase1_wide(ProbDev P, StepParams S,
   block_add_u64<NT_OBJ>(fails, &P.cnt->ls_fail);
 }
 
-// The gradients a scale pass needs, for samples of at most four coordinates with finite
-// differences, on P1_W lanes per sample (fd_gradient_wide): every unfrozen sample, or with
-// removed_only those Phase 4 reseeded (the others keep Phase 1's).  The scale pass then
-// reads them (reuse = 2) and sums in its own fixed order, so sigma and alpha are the one-
-// lane pass's bit for bit.
-template <int KIND, int GM>
+// The gradients a scale pass needs, for samples of at most sixteen coordinates with finite
+// differences, on P1_W groups per sample (fd_gradient_wide): every unfrozen sample, or with
+// removed_only those Phase 4 reseeded (the others keep Phase 1's).  The scale pass then reads
+// them (reuse = 2) and sums in its own fixed order, so sigma and alpha are the one-group
+// pass's bit for bit.
+template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_grad_wide(ProbDev P, StepParams S, int removed_only) {
-  constexpr int DP = 4, V = VL;
+  constexpr int V = VL, LPS = DP / V, SL = P1_W * LPS;
   static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
-  const Grp<1> g;
-  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1);
-  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
-  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  const Grp<LPS> g;
+  const int lane = threadIdx.x & 31, q = (lane / LPS) & (P1_W - 1);
+  const unsigned smask = wide_mask<LPS>();
+  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / SL);
   unsigned long long evals = 0, grads = 0;
   if (i < P.n && !bit_of(P.stuck, i) && (!removed_only || bit_of(P.removed, i))) {
+    const int j0 = V * g.l;
     float x[V], a[V];
-    ld_vec<V>(P.x + (size_t)i * DP, x);
-    fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, a, g, j, wmask);
-    if (j == 0) {
-      st_vec<V>(P.g + (size_t)i * DP, a);
-      evals = 2ull * P.d;
-      grads = 1;
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    fd_gradient_wide<KIND, GM, LPS>(P.obj, S, P.d, x, a, g, q, smask);
+    if (q == 0) {
+      st_vec<V>(P.g + (size_t)i * DP + j0, a);
+      if (g.l == 0) {
+        evals = 2ull * P.d;
+        grads = 1;
+      }
     }
   }
   block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
 }
 
-// Anti-convergence (Eq. 6) for samples of at most four coordinates with finite differences:
-// anti_body's steps with each step's gradient evaluated on P1_W lanes (fd_gradient_wide);
-// the lanes keep identical copies of the sample's position and velocity.
-template <int KIND, int GM>
+// Anti-convergence (Eq. 6) for samples of at most sixteen coordinates with finite
+// differences: anti_body's steps with each step's gradient evaluated on P1_W groups
+// (fd_gradient_wide); the groups keep identical copies of the sample's position and velocity.
+template <int KIND, int DP, int GM>
 __global__ void __launch_bounds__(NT_OBJ) k_anti_wide(ProbDev P, StepParams S) {
-  constexpr int DP = 4, V = VL;
+  constexpr int V = VL, LPS = DP / V, SL = P1_W * LPS;
   static_assert(GM != GRAD_ADJOINT, "finite-difference gradients");
-  const Grp<1> g;
-  const int lane = threadIdx.x & 31, j = lane & (P1_W - 1);
-  const unsigned wmask = ((1u << P1_W) - 1u) << (lane & ~(P1_W - 1));
-  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / P1_W);
+  const Grp<LPS> g;
+  const int lane = threadIdx.x & 31, q = (lane / LPS) & (P1_W - 1);
+  const unsigned smask = wide_mask<LPS>();
+  const int i = (int)(((size_t)blockIdx.x * NT_OBJ + threadIdx.x) / SL);
   unsigned long long evals = 0, grads = 0;
   if (i < P.n && !bit_of(P.stuck, i) && P.cnt->sc_count > 0) {
+    const int j0 = V * g.l;
     const float alpha = P.cnt->sc_alpha, mu = S.mu;
     float x[V], gr[V], vel[V], lo[V], hi[V];
-    ld_vec<V>(P.x + (size_t)i * DP, x);
-    ld_vec<V>(P.g + (size_t)i * DP, gr);
-    ld_vec<V>(P.lo, lo);
-    ld_vec<V>(P.hi, hi);
+    ld_vec<V>(P.x + (size_t)i * DP + j0, x);
+    ld_vec<V>(P.g + (size_t)i * DP + j0, gr);
+    ld_vec<V>(P.lo + j0, lo);
+    ld_vec<V>(P.hi + j0, hi);
 #pragma unroll
     for (int v = 0; v < V; ++v) vel[v] = 0.f;
     for (int t = 0; t < S.n_anti; ++t) {
       if (t > 0) {
-        fd_gradient_wide<KIND, GM>(P.obj, S, P.d, x, gr, g, j, wmask);
+        fd_gradient_wide<KIND, GM, LPS>(P.obj, S, P.d, x, gr, g, q, smask);
         evals += 2ull * P.d;
         grads += 1;
       }
@@ -638,12 +672,11 @@ __global__ void __launch_bounds__(NT_OBJ) k_anti_wide(ProbDev P, StepParams S) {
         x[v] = cx;
       }
     }
-    if (j == 0) {
-      st_vec<V>(P.x + (size_t)i * DP, x);
-      P.hlen[i] = 0;
-    } else {
-      evals = grads = 0;
+    if (q == 0) {
+      st_vec<V>(P.x + (size_t)i * DP + j0, x);
+      if (g.l == 0) P.hlen[i] = 0;
     }
+    if (q != 0 || g.l != 0) evals = grads = 0;
   }
   block_add_u64<NT_OBJ>(evals, &P.cnt->evals);
   block_add_u64<NT_OBJ>(grads, &P.cnt->grads);
@@ -1015,8 +1048,8 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
   if (rows <= 0) return cudaSuccess;
   switch (which) {
     case OKID_PHASE1:
-      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
-        k_phase1_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
+      if constexpr (DP <= 16 && GM != GRAD_ADJOINT) {
+        k_phase1_wide<KIND, DP, GM><<<(unsigned)((rows * P1_W * (DP / VL) + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
             P, S, arg < 0 ? -arg : arg, arg >= 0 ? 1 : 0, nullptr, nullptr);
         break;
       }
@@ -1030,8 +1063,9 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_direction<DP><<<blocks, NT_OBJ, 0, st>>>(P);
       break;
     case OKID_SCALES:
-      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
-        k_grad_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(P, S, arg);
+      if constexpr (DP <= 16 && GM != GRAD_ADJOINT) {
+        k_grad_wide<KIND, DP, GM><<<(unsigned)((rows * P1_W * (DP / VL) + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
+            P, S, arg);
         k_scales<KIND, DP, GM><<<(unsigned)scale_blocks(P), NT_SCALES, 0, st>>>(P, S, 2);
         break;
       }
@@ -1048,8 +1082,9 @@ cudaError_t launch_obj_dp_gm(int which, const ProbDev& P, const StepParams& S, i
       k_hlc<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
       break;
     case OKID_ANTI:
-      if constexpr (DP == 4 && GM != GRAD_ADJOINT) {
-        k_anti_wide<KIND, GM><<<(unsigned)((rows * P1_W + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(P, S);
+      if constexpr (DP <= 16 && GM != GRAD_ADJOINT) {
+        k_anti_wide<KIND, DP, GM><<<(unsigned)((rows * P1_W * (DP / VL) + NT_OBJ - 1) / NT_OBJ), NT_OBJ, 0, st>>>(
+            P, S);
         break;
       }
       k_anti<KIND, DP, GM><<<blocks, NT_OBJ, 0, st>>>(P, S);
