@@ -61,6 +61,41 @@ def test_line_search_backtracks_to_first_passing_step():
     assert Xn[0, 0] == -0.5 and Fn[0] == 0.125
 
 
+def test_line_search_equals_trials_taken_in_batches():
+    """Reading 23: the trials of a search do not depend on one another, so evaluating them
+    in batches side by side and taking the first that passes (as the batched evaluator and
+    the small-sample device kernels do) gives the sequential search's step, value and trial
+    count.  Checked on a noisy mixture with one-trial-at-a-time, batches of 3 and batches of
+    8, including searches that fail and samples already at a mode."""
+    prob = I.small_mixture(3, 4, 200, seed=9, noise_sigma=0.05)
+    P = M.Params(m=5, grad_mode=M.GRAD_ADJOINT, T_ls=11)
+    rng = np.random.default_rng(9)
+    X = prob.x0.astype(np.float64)
+    F = -M.evaluate(prob, X)
+    G = -M.gradient(prob, X, P)
+    Pd = -G + rng.normal(0, 1.0, G.shape) * np.abs(G).max(axis=1, keepdims=True)   # some ascent steps
+    alpha0 = np.minimum(1.0, 1.0 / np.abs(G).max(axis=1))
+    acc, Xn, Fn, trials = M.line_search(prob, X, F, G, Pd, alpha0, P)
+    assert 0 < acc.sum() < prob.n
+    for B in (1, 3, 8):
+        for i in range(prob.n):
+            got = None
+            for t0 in range(0, P.T_ls, B):
+                ts = np.arange(t0, min(t0 + B, P.T_ls))
+                Xt = np.clip(X[i] + (alpha0[i] * 2.0 ** (-ts))[:, None] * Pd[i], prob.lo, prob.hi)
+                Ft = -M.evaluate(prob, Xt)
+                ok = Ft <= F[i] + P.c1 * (Xt - X[i]) @ G[i]
+                if ok.any():
+                    k = int(np.argmax(ok))
+                    got = (True, Xt[k], Ft[k], int(ts[k]) + 1)
+                    break
+            if got is None:
+                got = (False, X[i], F[i], P.T_ls)
+            assert got[0] == acc[i] and got[3] == trials[i]
+            np.testing.assert_array_equal(got[1], Xn[i])
+            assert got[2] == Fn[i]
+
+
 def test_line_search_projects_onto_box():
     obj = I.Objective(3, 1, {"center": np.array([5.0]), "Q": np.eye(1), "lam": np.array([1.0])})
     prob = I.Problem(1, 1, np.array([-1.0]), np.array([1.0]), obj, np.zeros((1, 1), np.float32), 1e-6, 1.0)
